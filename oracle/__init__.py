@@ -1,0 +1,224 @@
+"""FP64 CPU oracle for noise-aware multi-sensor LPA reconstruction (test infrastructure).
+
+Only `tests/`, `__graft_entry__.smoke()` and `bench.py`'s CPU-baseline leg may
+import this package. The product path (the CUDA library and its binding) never
+does; the two share no code. Two independent routes live here:
+
+* `lpa_oracle.c` (loaded through ctypes): the definition per output pixel in
+  double precision - bounding-box gather, normal equations, Jacobi
+  equilibration, LDL^T, scale choice by intersection of confidence intervals,
+  order fallback (see its header for the passages followed and the readings).
+* `bruteforce.py`: every sample of every sensor, weighted least squares by
+  Householder QR (numpy), for tiny rigs - an independent check of the C route.
+
+Parity of `lpa_oracle.c` with the paper is pinned by `tests/test_oracle_*.py`
+against closed forms, invariants and brute force (the paper prints no numeric
+results). The paper's own code is not available, so parity with that code is
+unpinned (noise-weight exponent and window truncation are readings).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lpa_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liblpa_oracle.so")
+
+MAX_SCALES = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (-O2, OpenMP); returns the library path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Sensor(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("raw", ctypes.c_void_p), ("value_f", ctypes.c_void_p), ("value_var", ctypes.c_void_p),
+                ("gain", ctypes.c_double), ("exposure", ctypes.c_double), ("nd", ctypes.c_double),
+                ("read_var", ctypes.c_double), ("black", ctypes.c_double), ("sat", ctypes.c_double),
+                ("bias_px", ctypes.c_void_p), ("prnu_px", ctypes.c_void_p),
+                ("read_var_px", ctypes.c_void_p), ("sat_px", ctypes.c_void_p),
+                ("affine", ctypes.c_double * 6)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("n_scales", ctypes.c_int32),
+                ("sigma", ctypes.c_double * MAX_SCALES), ("green_ratio", ctypes.c_double),
+                ("trunc_k", ctypes.c_double), ("ici_gamma", ctypes.c_double),
+                ("min_pivot", ctypes.c_double), ("out_affine", ctypes.c_double * 6),
+                ("weight_mode", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.orc_reconstruct.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_reconstruct.restype = ctypes.c_int
+        lib.orc_radiometry.argtypes = [ctypes.c_double] * 8 + [P, P]
+        lib.orc_radiometry.restype = ctypes.c_int
+        lib.orc_ici.argtypes = [ctypes.c_int, P, P, P, ctypes.c_double, P]
+        lib.orc_ici.restype = ctypes.c_int
+        lib.orc_equivalent_kernel.argtypes = [P, ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_int32, ctypes.c_int32] + [P] * 7
+        lib.orc_equivalent_kernel.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a) -> Optional[np.ndarray]:
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _Marshal:
+    """Keeps the numpy buffers alive while the C structs point at them."""
+
+    def __init__(self, sensors, params):
+        self.keep: List[np.ndarray] = []
+        n = len(sensors)
+        self.arr = (_Sensor * max(n, 1))()
+        for i, s in enumerate(sensors):
+            d = self.arr[i]
+            d.width, d.height = int(s.width), int(s.height)
+            vf = getattr(s, "value_f", None)
+            if vf is not None:
+                f = _f64(vf)
+                v = _f64(s.value_var)
+                self.keep += [f, v]
+                d.value_f, d.value_var = _ptr(f), _ptr(v)
+                d.pitch = int(s.width)
+                d.raw = None
+            else:
+                raw = np.ascontiguousarray(s.raw, dtype=np.uint16)
+                self.keep.append(raw)
+                d.raw = _ptr(raw)
+                d.pitch = int(raw.shape[1])
+            d.gain, d.exposure, d.nd = float(s.gain), float(s.exposure), float(s.nd)
+            d.read_var, d.black, d.sat = float(s.read_var), float(s.black), float(s.sat)
+            for name, field in (("bias_frame", "bias_px"), ("prnu_frame", "prnu_px"),
+                                ("read_var_frame", "read_var_px"), ("sat_frame", "sat_px")):
+                fr = getattr(s, name, None)
+                if fr is not None:
+                    fr = _f64(fr)
+                    self.keep.append(fr)
+                setattr(d, field, _ptr(fr))
+            d.affine[:] = [float(x) for x in np.asarray(s.affine, dtype=np.float64).reshape(6)]
+        self.n = n
+        p = _Params()
+        p.order = int(params.order)
+        p.n_scales = len(params.sigmas)
+        for j, sg in enumerate(params.sigmas):
+            p.sigma[j] = float(sg)
+        p.green_ratio = float(params.green_ratio)
+        p.trunc_k = float(params.trunc_k)
+        p.ici_gamma = float(params.ici_gamma)
+        p.min_pivot = float(params.min_pivot)
+        p.out_affine[:] = [float(x) for x in np.asarray(params.out_affine, dtype=np.float64).reshape(6)]
+        p.weight_mode = int(getattr(params, "weight_mode", 0))
+        self.params = p
+
+
+def n_levels(params) -> int:
+    return len(params.sigmas) + int(params.order)
+
+
+def reconstruct(sensors: Sequence, params, pixels: Optional[np.ndarray] = None,
+                levels: bool = False, kappa: bool = False) -> Dict[str, np.ndarray]:
+    """Run the oracle on output pixels `pixels` ([n, 2] of (u, v); default: the whole output grid).
+
+    Returns a dict with `out` [n, 3] (or [3, H, W] for the whole grid), `choice`, `margin` and, when
+    `levels`, the per-level arrays `c0`, `var`, `pivot`, `count`, `valid` ([n, 3, J+M]) and `kappa`.
+    """
+    lib = _load()
+    grid = pixels is None
+    if grid:
+        vv, uu = np.mgrid[0:params.out_h, 0:params.out_w]
+        pixels = np.stack([uu.ravel(), vv.ravel()], axis=1)
+    pixels = np.asarray(pixels, dtype=np.int64)
+    n = pixels.shape[0]
+    pu = np.ascontiguousarray(pixels[:, 0], dtype=np.int32)
+    pv = np.ascontiguousarray(pixels[:, 1], dtype=np.int32)
+    m = _Marshal(sensors, params)
+    NL = n_levels(params)
+    out = np.empty((n, 3))
+    choice = np.empty((n, 3), dtype=np.int32)
+    margin = np.empty((n, 3))
+    lv = {}
+    if levels or kappa:
+        lv = dict(c0=np.empty((n, 3, NL)), var=np.empty((n, 3, NL)), pivot=np.empty((n, 3, NL)),
+                  count=np.empty((n, 3, NL), dtype=np.int32), valid=np.empty((n, 3, NL), dtype=np.int32))
+        if kappa:
+            lv["kappa"] = np.empty((n, 3, NL))
+    rc = lib.orc_reconstruct(ctypes.byref(m.arr), m.n, ctypes.byref(m.params), n, _ptr(pu), _ptr(pv),
+                             _ptr(out), _ptr(choice), _ptr(margin), _ptr(lv.get("c0")), _ptr(lv.get("var")),
+                             _ptr(lv.get("pivot")), _ptr(lv.get("kappa")), _ptr(lv.get("count")),
+                             _ptr(lv.get("valid")))
+    if rc != 0:
+        raise ValueError(f"orc_reconstruct rejected its arguments (code {rc})")
+    res = dict(out=out, choice=choice, margin=margin, **lv)
+    if grid:
+        H, W = params.out_h, params.out_w
+        res["out"] = out.reshape(H, W, 3).transpose(2, 0, 1).copy()
+        res["choice"] = choice.reshape(H, W, 3).transpose(2, 0, 1).copy()
+        res["margin"] = margin.reshape(H, W, 3).transpose(2, 0, 1).copy()
+    res["pixels"] = pixels
+    return res
+
+
+def radiometry(y, b, g, t, a, n, read_var, sat):
+    """Eqs. 18 and 20 for one digital value; returns (excluded, f, s2)."""
+    lib = _load()
+    f = ctypes.c_double()
+    s2 = ctypes.c_double()
+    ex = lib.orc_radiometry(float(y), float(b), float(g), float(t), float(a), float(n), float(read_var),
+                            float(sat), ctypes.addressof(f), ctypes.addressof(s2))
+    return bool(ex), f.value, s2.value
+
+
+def ici(c0: Sequence[float], var: Sequence[float], valid: Sequence[int], gamma: float):
+    """The scale-choice rule on given intervals; returns (chosen index or -1, margin)."""
+    lib = _load()
+    c0 = np.ascontiguousarray(c0, dtype=np.float64)
+    var = np.ascontiguousarray(var, dtype=np.float64)
+    valid = np.ascontiguousarray(valid, dtype=np.int32)
+    mg = ctypes.c_double()
+    ch = lib.orc_ici(len(c0), _ptr(c0), _ptr(var), _ptr(valid), float(gamma), ctypes.addressof(mg))
+    return ch, mg.value
+
+
+def equivalent_kernel(sensors, params, u: int, v: int, c: int, sigma: float, order: int, cap: int = 4096):
+    """Equivalent kernel of one fit: dict of per-sample arrays, or None if the fit is not usable."""
+    lib = _load()
+    m = _Marshal(sensors, params)
+    bufs = dict(sensor=np.zeros(cap, np.int32), x=np.zeros(cap, np.int32), y=np.zeros(cap, np.int32),
+                dx=np.zeros(cap), dy=np.zeros(cap), f=np.zeros(cap), ell=np.zeros(cap))
+    k = lib.orc_equivalent_kernel(ctypes.byref(m.arr), m.n, ctypes.byref(m.params), int(u), int(v), int(c),
+                                  float(sigma), int(order), cap, *(_ptr(bufs[x]) for x in
+                                                                   ("sensor", "x", "y", "dx", "dy", "f", "ell")))
+    if k == -1:
+        return None
+    if k < 0:
+        raise ValueError(f"orc_equivalent_kernel rejected its arguments (code {k})")
+    k = min(k, cap)
+    return {key: val[:k] for key, val in bufs.items()}
