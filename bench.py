@@ -1,0 +1,326 @@
+"""Benchmark: multi-sensor HDR reconstruction throughput on GB300.
+
+Workload (one "step" = one frame through the whole hot path, one kernel launch):
+3 sensors of 2048x2048 12-bit RGGB raw (ND 1, 1/16, 1/256; affine misalignment),
+seeded synthetic scene, LPA order 2 with the scale chosen among 4 scales
+(0.5, 0.8, 1.2, 1.8 px) by intersection of confidence intervals, 2048x2048
+float32 RGB output. Inputs are resident in HBM when timing starts; L2 is flushed
+(a 256 MiB write) between timed steps. One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the slow program the CUDA path is checked against).
+N > 1 (torchrun): independent replicas, one frame stream per GPU, no collective
+on the data path; the barrier and the max-over-ranks time use the process group.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HDR output Mpixel/s (3x4Mpx, LPA M=2 adaptive); p50/p99 frame latency, mixed"
+WORKLOAD = "paper-scale: 3 x 2048x2048 RGGB 12-bit -> 2048x2048 fp32 RGB, LPA M=2, ICI over sigma {0.5,0.8,1.2,1.8}"
+FLOPS_PER_PAIR = {0: 11, 1: 41, 2: 92}   # algorithmic FP32 flops per (sample, scale) pair; FMA = 2
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(pk) -> float:
+    """FP32 FMA peak of the GB300: 152 SMs x 128 lanes x 2 flop x max SM clock."""
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def expected_pairs(params, sensors):
+    """Expected (sample, scale) pairs per output pixel and channel at each scale: sample density
+    of the channel in sensor px (R, B 1/4, G 1/2) x reference-disc area / |det T_s|."""
+    k = params.trunc_k
+    out = np.zeros((3, len(params.sigmas)))
+    for s in sensors:
+        det = abs(s.affine[0, 0] * s.affine[1, 1] - s.affine[0, 1] * s.affine[1, 0])
+        for j, sg in enumerate(params.sigmas):
+            for c, dens in ((0, 0.25), (1, 0.5), (2, 0.25)):
+                sc = sg * (params.green_ratio if c == 1 else 1.0)
+                out[c, j] += dens * math.pi * (k * sc) ** 2 / det
+    return out
+
+
+def algorithmic_flops(params, sensors, choice: np.ndarray) -> float:
+    """FP32 flops the method needs for one frame: per pixel and channel every scale up to the
+    one at which the confidence-interval rule stops (the chosen scale and the next), times the
+    per-pair count of the order (moment FMAs, monomials, weights)."""
+    J = len(params.sigmas)
+    pairs = expected_pairs(params, sensors)             # [3, J]
+    cum = np.cumsum(pairs, axis=1)                      # pairs up to scale j
+    total = 0.0
+    for c in range(3):
+        ch = choice[c].astype(np.int64).ravel()
+        stop = np.where((ch >= 0) & (ch < J - 1), ch + 1, J - 1)   # scale index reached
+        total += cum[c][stop].sum()
+    return total * FLOPS_PER_PAIR[params.order]
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 4 + i and s[4 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples),
+                "power_w_max": max(float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit())
+                if any(s[2].replace(".", "").isdigit() for s in self.samples) else None}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, value: float, device=None) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=f"cuda:{device}" if device is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_rate(frame, n_pix: int, seed: int = 0):
+    """Time the oracle on n_pix random output pixels of the frame; returns (Mpx/s, seconds, threads)."""
+    import oracle
+    r = np.random.default_rng(seed)
+    pix = np.stack([r.integers(0, frame.params.out_w, n_pix), r.integers(0, frame.params.out_h, n_pix)], axis=1)
+    t0 = time.perf_counter()
+    oracle.reconstruct(frame.sensors, frame.params, pix)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n_pix / dt / 1e6, dt, threads
+
+
+def cpu_baseline(frame, budget_s: float = 12.0):
+    import oracle
+    oracle.build()
+    rate, dt, thr = oracle_rate(frame, 8192, seed=1)
+    n = int(min(max(budget_s * rate * 1e6, 8192), 4_000_000))
+    rate, dt, thr = oracle_rate(frame, n, seed=2)
+    return {"value": round(rate, 4), "unit": "Mpixel/s", "cores": thr, "kind": "oracle",
+            "sample": f"{n} random output pixels of the same 2048x2048 frame ({dt:.1f} s, FP64, OpenMP over pixels)"}
+
+
+def run_reference(args, world, rank, pg):
+    """The reference arm: the FP64 oracle on the host cores, each step a bounded pixel sample."""
+    if rank != 0:
+        return
+    from paper_1308_4908_gb300 import synth
+    import oracle
+    oracle.build()
+    frame = synth.paper_scale()
+    rate, dt, thr = oracle_rate(frame, 4096, seed=1)
+    n = int(min(max(3.0 * rate * 1e6, 4096), 1_000_000))   # about 3 s per step
+    for w in range(args.warmup if args.warmup < 1 else 1):
+        oracle_rate(frame, min(n, 4096), seed=100 + w)
+    times = []
+    for k in range(args.steps):
+        _, dt, thr = oracle_rate(frame, n, seed=200 + k)
+        times.append(dt)
+    tot = sum(times)
+    value = n * args.steps / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Mpixel/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_pixels_per_step": n},
+            "cpu_baseline": {"value": round(value, 5), "unit": "Mpixel/s", "cores": thr, "kind": "oracle",
+                             "sample": f"{n} random output pixels per step of the 2048x2048 frame"},
+            "e2e": {"value": round(value, 5), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    from paper_1308_4908_gb300 import hdr, synth
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    frame = synth.paper_scale()
+    p = frame.params
+    ctx = hdr.Context(local)
+    ctx.set_rig(0, frame.sensors)
+    hp = hdr.params_struct(p)
+    raws = [torch.from_numpy(s.raw).to(dev) for s in frame.sensors]
+    out = torch.empty((3, p.out_h, p.out_w), dtype=torch.float32, device=dev)
+    choice = torch.empty((3, p.out_h, p.out_w), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    ptrs = [int(r.data_ptr()) for r in raws]
+
+    def step(with_choice=False):
+        hdr.hdr_reconstruct(ctx.handle, 0, hp, ptrs, out.data_ptr(), choice.data_ptr() if with_choice else None, sp)
+
+    # one untimed pass with the choice map (for the algorithmic work count), then warm-up
+    with torch.cuda.stream(stream):
+        step(True)
+    ctx.check(stream)
+    ch = choice.cpu().numpy().astype(np.int16)
+    ch[ch == 255] = -1
+    flops = algorithmic_flops(p, frame.sensors, ch)
+    for _ in range(max(args.warmup, 0)):
+        with torch.cuda.stream(stream):
+            step()
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(pg, local)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)                 # evict L2 between timed steps
+                evs[k][0].record(stream)
+                step()
+                evs[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall0
+    barrier(pg, local)
+    ctx.check(stream)
+    kern_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = float(np.mean(kern_ms))
+    ms_max = max_over_ranks(pg, ms, local)
+    px = p.out_w * p.out_h
+    value = px * world / (ms_max * 1e-3) / 1e6
+
+    # end to end through the host-buffer entry point (pinned host memory, copies timed)
+    raw_host = [torch.from_numpy(s.raw).pin_memory() for s in frame.sensors]
+    out_host = torch.empty((3, p.out_h, p.out_w), dtype=torch.float32).pin_memory()
+    raw_np = [r.numpy() for r in raw_host]
+    out_np = out_host.numpy()
+    e2e_steps = max(3, min(args.steps, 10))
+    ctx.reconstruct_host(0, hp, raw_np, out_np, stream=stream)   # grow staging once
+    barrier(pg, local)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.reconstruct_host(0, hp, raw_np, out_np, stream=stream)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks(pg, e2e_s, local)
+    h2d = sum(int(r.numel()) * 2 for r in raw_host)
+    d2h = int(out_host.numel()) * 4
+    ctx.check(stream)
+
+    if rank == 0:
+        pk = peaks()
+        peak = fp32_peak_tflops(pk)
+        achieved = flops / (ms * 1e-3) / 1e12
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": 1, "output_px": px,
+                       "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz of MEASURED_PEAKS.json",
+                         "algorithmic_gflop_per_launch": round(flops / 1e9, 3)},
+            "e2e": {"value": round(px * world / e2e_s / 1e6, 2), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3, 3),
+                    "api": "hdr_reconstruct_host (pinned host buffers, copies and kernel on one stream)"},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "kernel_ms": {"mean": round(ms, 4), "min": round(min(kern_ms), 4), "max": round(max(kern_ms), 4)},
+            "wall_s_timed_region": round(t_wall, 4),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(frame)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank, pg)
+        else:
+            run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,148 @@
+/*
+ * hdr_lpa.h - C ABI of the GB300 (sm_103a) multi-sensor HDR reconstruction library.
+ *
+ * Method: Kronander, Gustavson, Bonnet, Ynnerman, Unger, "A Unified Framework
+ * for Multi-Sensor HDR Video Reconstruction". For every output pixel the
+ * library gathers the raw Bayer samples of all sensors around the pixel's
+ * point in the reference frame (Section 4.2), converts them to radiant power
+ * with their plug-in variance (Section 6, Eqs. 18 and 20; saturated samples
+ * excluded, Section 6.1), fits a weighted local polynomial of order M <= 2 per
+ * colour channel with a truncated Gaussian window times the inverse variance
+ * (Sections 5.1-5.3, Eq. 6, Eq. 8) and returns the fit's constant term C_0.
+ * With several window scales it keeps, per channel, the last scale whose
+ * running intersection of confidence intervals C_0 +- gamma*sqrt(Var C_0)
+ * (ascending scales) is non-empty; with no usable scale it lowers the order at
+ * the largest scale; with no sample at all the output is NaN.
+ *
+ * Conventions for every entry point:
+ *  - Status codes only; no exception crosses the ABI. hdr_last_error() returns
+ *    a message for the calling thread's last failed call.
+ *  - Argument errors are reported synchronously. Device-side errors (a
+ *    bounded wait that ran out, a staging-window overrun) are recorded in a
+ *    per-context status word and reported by hdr_check().
+ *  - Pointers named *_dev are device pointers owned by the caller; they must
+ *    stay valid until the work queued on the given stream has finished.
+ *    Pointers named *_host are host pointers, read or written before the call
+ *    returns.
+ *  - One hdr_ctx may be used by one thread at a time.
+ *  - Colour planes are ordered R, G, B. RGGB Bayer layout: sensor pixel
+ *    (x even, y even) is R, (x odd, y odd) is B, the others are G.
+ */
+#ifndef HDR_LPA_H
+#define HDR_LPA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HDR_MAX_SENSORS 8
+#define HDR_MAX_SCALES 8
+
+typedef enum {
+  HDR_OK = 0,
+  HDR_E_INVALID = 1,     /* bad argument (reported before any GPU work)          */
+  HDR_E_NOMEM = 2,       /* device or host allocation failed                     */
+  HDR_E_CUDA = 3,        /* a CUDA runtime/driver call failed                    */
+  HDR_E_BUSY = 4,        /* resource in use                                      */
+  HDR_E_TIMEOUT = 5,     /* a bounded device-side wait ran out                   */
+  HDR_E_UNSUPPORTED = 6, /* valid but outside what this build implements         */
+  HDR_E_INTERNAL = 7     /* a device-side consistency check failed               */
+} hdr_status;
+
+typedef struct hdr_ctx hdr_ctx;
+
+/* One sensor s of a rig (Sections 3, 4 and 6). */
+typedef struct {
+  int32_t width, height;      /* raw frame size in pixels                                  */
+  int32_t pitch_elems;        /* row pitch in uint16 elements; pitch_elems*2 % 16 == 0     */
+  int32_t cfa;                /* Bayer layout; only 0 = RGGB is implemented                */
+  double gain;                /* g_s, digital values per electron (Section 6, Eq. 17)      */
+  double exposure;            /* t_s (Section 6, Eq. 16)                                   */
+  double nd;                  /* exposure scaling n_s (Section 3)                          */
+  double read_var;            /* Var r_s in DN^2, > 0 (Section 6.1, Eq. 20)                */
+  double black;               /* bias b_s in DN (Section 6, Eq. 18)                        */
+  double sat;                 /* saturation level in DN: y >= sat is excluded (Sec. 6.1)   */
+  double affine[6];           /* T_s: sensor px -> reference px, row-major 2x3 (Sec. 4.2)  */
+  /* Optional per-pixel calibration, HOST pointers to [height][width] arrays, NULL = use
+   * the scalar above. Copied to the device by hdr_set_rig. */
+  const float *bias_frame;    /* b_{s,i}                                                   */
+  const float *prnu_frame;    /* a_{s,i}, > 0 (Section 6, Eq. 16)                          */
+  const float *read_var_frame;/* Var r_{s,i}, > 0                                          */
+  const uint16_t *sat_frame;  /* saturation frame (Section 6.1)                            */
+} hdr_sensor_desc;
+
+/* Reconstruction parameters (Sections 5.3 and 5.3.1). */
+typedef struct {
+  int32_t order;              /* polynomial order M in {0, 1, 2}                           */
+  int32_t n_scales;           /* J in [1, HDR_MAX_SCALES]; 1 = a single window scale       */
+  double sigma[HDR_MAX_SCALES]; /* R/B Gaussian scales in reference px, strictly ascending   */
+  double green_ratio;         /* sigma_G / sigma_RB (Section 5.3.1: 1/sqrt(2))             */
+  double trunc_k;             /* window radius k*sigma; the window is lowered by exp(-k^2/2) */
+  double ici_gamma;           /* confidence-interval half-width in standard deviations     */
+  double min_pivot;           /* a fit is usable only if every pivot of its equilibrated
+                                 normal matrix exceeds this and it has >= (M+1)(M+2)/2 samples */
+  double cond_fallback;       /* redo a solve in FP64 when the FP32 condition estimate exceeds
+                                 this; <= 0 disables the fallback                           */
+  int32_t out_w, out_h;       /* output size in pixels                                     */
+  double out_affine[6];       /* output px -> reference px, row-major 2x3 (Section 4.2)    */
+  int32_t out_dtype;          /* 0 = float32, 1 = float16; planar [3][out_h][out_w]        */
+  int32_t accum;              /* 0 = plain FP32 moment sums, 1 = compensated (two-sum)     */
+} hdr_params;
+
+/* Fill *p with the defaults: order 2, scales {0.5, 0.8, 1.2, 1.8}, green_ratio 1/sqrt(2),
+ * trunc_k 3, ici_gamma 2, min_pivot 1e-3, cond_fallback 1e6, identity output mapping,
+ * float32 output, plain accumulation. out_w/out_h are set to 0 and must be filled. */
+void hdr_params_default(hdr_params *p);
+
+/* Create a context on CUDA device `device` (allocates its status word). */
+hdr_status hdr_create(int device, hdr_ctx **out);
+
+/* Destroy a context and every rig it holds. NULL is a no-op. */
+void hdr_destroy(hdr_ctx *ctx);
+
+/* Define (or replace) rig `rig_id` (0 <= rig_id < 64) of `n_sensors` (1..HDR_MAX_SENSORS)
+ * sensors. Calibration and any per-pixel frames are copied to the device; the host
+ * descriptors may be freed after the call. Replacing a rig waits for the device. */
+hdr_status hdr_set_rig(hdr_ctx *ctx, int32_t rig_id, int32_t n_sensors, const hdr_sensor_desc *sensors);
+
+/* Reconstruct one frame on `cuda_stream` (a cudaStream_t, NULL = the legacy default stream).
+ *   raw_dev[s]  device pointer to sensor s's raw frame, [height][pitch_elems] uint16,
+ *               16-byte aligned;
+ *   out_dev     device pointer to the planar output [3][out_h][out_w] of out_dtype;
+ *   choice_dev  optional device pointer [3][out_h][out_w] uint8: per channel the level
+ *               used - 0..J-1 = order M at scale j, J+i = order M-1-i at the largest scale,
+ *               255 = no sample (NaN output). NULL = not written.
+ * Asynchronous: returns after queueing one kernel launch. */
+hdr_status hdr_reconstruct(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                           const uint16_t *const *raw_dev, void *out_dev, uint8_t *choice_dev,
+                           void *cuda_stream);
+
+/* Diagnostic variant of hdr_reconstruct: computes every level (no early exit) and also
+ * writes levels_dev [3][J+M][out_h][out_w][2] float32 = (C_0, Var C_0) per level, NaN for
+ * an unusable level. Slower; for parity and precision studies. */
+hdr_status hdr_reconstruct_levels(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                                  const uint16_t *const *raw_dev, void *out_dev, uint8_t *choice_dev,
+                                  float *levels_dev, void *cuda_stream);
+
+/* End-to-end variant with HOST buffers: copies raw_host[s] ([height][pitch_elems]) to
+ * device staging owned by the context, reconstructs, copies the output back to out_host
+ * (and choice to choice_host when non-NULL) and waits. Staging grows on demand. */
+hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                                const uint16_t *const *raw_host, void *out_host, uint8_t *choice_host,
+                                void *cuda_stream);
+
+/* Wait for `cuda_stream`, then read and clear the context's device status word.
+ * Returns HDR_E_TIMEOUT or HDR_E_INTERNAL if a kernel recorded one, HDR_E_CUDA on a
+ * CUDA error, else HDR_OK. */
+hdr_status hdr_check(hdr_ctx *ctx, void *cuda_stream);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *hdr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDR_LPA_H */

@@ -70,7 +70,7 @@ def _load():
     if _lib is None:
         lib = ctypes.CDLL(build())
         P = ctypes.c_void_p
-        lib.orc_reconstruct.argtypes = [P, ctypes.c_int, P, ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_reconstruct.argtypes = [P, ctypes.c_int, P, ctypes.c_int64] + [P] * 13
         lib.orc_reconstruct.restype = ctypes.c_int
         lib.orc_radiometry.argtypes = [ctypes.c_double] * 8 + [P, P]
         lib.orc_radiometry.restype = ctypes.c_int
@@ -148,7 +148,8 @@ def reconstruct(sensors: Sequence, params, pixels: Optional[np.ndarray] = None,
     """Run the oracle on output pixels `pixels` ([n, 2] of (u, v); default: the whole output grid).
 
     Returns a dict with `out` [n, 3] (or [3, H, W] for the whole grid), `choice`, `margin` and, when
-    `levels`, the per-level arrays `c0`, `var`, `pivot`, `count`, `valid` ([n, 3, J+M]) and `kappa`.
+    `levels`, the per-level arrays `c0`, `var`, `pivot`, `count`, `valid` ([n, 3, J+M]), the
+    rounding scales `efit` and `ew` (see lpa_oracle.c) and, with `kappa`, the condition numbers.
     """
     lib = _load()
     grid = pixels is None
@@ -167,13 +168,14 @@ def reconstruct(sensors: Sequence, params, pixels: Optional[np.ndarray] = None,
     lv = {}
     if levels or kappa:
         lv = dict(c0=np.empty((n, 3, NL)), var=np.empty((n, 3, NL)), pivot=np.empty((n, 3, NL)),
-                  count=np.empty((n, 3, NL), dtype=np.int32), valid=np.empty((n, 3, NL), dtype=np.int32))
+                  count=np.empty((n, 3, NL), dtype=np.int32), valid=np.empty((n, 3, NL), dtype=np.int32),
+                  efit=np.empty((n, 3, NL)), ew=np.empty((n, 3, NL)))
         if kappa:
             lv["kappa"] = np.empty((n, 3, NL))
     rc = lib.orc_reconstruct(ctypes.byref(m.arr), m.n, ctypes.byref(m.params), n, _ptr(pu), _ptr(pv),
                              _ptr(out), _ptr(choice), _ptr(margin), _ptr(lv.get("c0")), _ptr(lv.get("var")),
                              _ptr(lv.get("pivot")), _ptr(lv.get("kappa")), _ptr(lv.get("count")),
-                             _ptr(lv.get("valid")))
+                             _ptr(lv.get("valid")), _ptr(lv.get("efit")), _ptr(lv.get("ew")))
     if rc != 0:
         raise ValueError(f"orc_reconstruct rejected its arguments (code {rc})")
     res = dict(out=out, choice=choice, margin=margin, **lv)

@@ -228,6 +228,13 @@ typedef struct {
   double var;        /* Var C_0 */
   double min_pivot;  /* smallest pivot of the equilibrated normal matrix */
   double kappa;      /* its 2-norm condition number */
+  /* Rounding scales of C_0 (diagnostics only; they do not enter the result). With
+   * L1_k = sum_m |l_m phi_m(d_k)|, F1_k = sum_m |c_m phi_m(d_k)| and c = A^{-1} b the fitted
+   * coefficients, a first-order perturbation of the moment sums and of the solve moves C_0 by at
+   * most (relative rounding) x err_fit, and a relative perturbation of the window at each sample
+   * (its evaluation and the rounding of the sample position) by at most that x err_w. */
+  double err_fit;    /* sum_k w_k L1_k (|f_k| + F1_k) */
+  double err_w;      /* sum_k (G_k (1 + r_k^2 / sigma^2) / s2_k) L1_k |f_k - phi(d_k)^T c|, G the Gaussian */
 } orc_fit;
 
 /* Section 5.2, Eq. 6 for one channel at one scale and order, with the
@@ -235,7 +242,7 @@ typedef struct {
  * equivalent kernel l_k = w_k e_0^T A^{-1} phi_k per sample (Section 5.2). */
 static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int order,
                    const orc_params *prm, int want_kappa, double *ell) {
-  orc_fit r = {0, 0, NAN, NAN, 0.0, INFINITY};
+  orc_fit r = {0, 0, NAN, NAN, 0.0, INFINITY, NAN, NAN};
   int P = n_unknowns(order);
   double k = prm->trunc_k;
   double R2 = (k * sigma_c) * (k * sigma_c);
@@ -285,21 +292,27 @@ static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int 
   r.min_pivot = minp;
   if (want_kappa) r.kappa = jacobi_condition(At, P);
   r.valid = (r.count >= P) && (minp > prm->min_pivot);
-  if (!r.valid) return r;
-  /* l = A^{-1} e_0 = D (D A D)^{-1} D e_0: solve L z = D e_0, z /= d, L^T x = z. */
-  double z[ORC_MAX_P], x[ORC_MAX_P], l[ORC_MAX_P];
-  for (int i = 0; i < P; i++) {
-    double s = (i == 0) ? D[0] : 0.0;
-    for (int m = 0; m < i; m++) s -= L[i * P + m] * z[m];
-    z[i] = s;
+  /* C_0 and its variance are also reported for factorable fits below the threshold (a
+   * diagnostic for decisions taken near it); the scale choice uses only usable fits. */
+  if (!(minp > 0.0)) return r;
+  /* l = A^{-1} e_0 = D (D A D)^{-1} D e_0 (and c = A^{-1} b the same way):
+   * solve L z = D rhs, z /= d, L^T x = z, result D x. */
+  double l[ORC_MAX_P], cf[ORC_MAX_P];
+  for (int which = 0; which < 2; which++) {
+    double z[ORC_MAX_P], x[ORC_MAX_P];
+    for (int i = 0; i < P; i++) {
+      double s = D[i] * (which == 0 ? (i == 0 ? 1.0 : 0.0) : bvec[i]);
+      for (int m = 0; m < i; m++) s -= L[i * P + m] * z[m];
+      z[i] = s;
+    }
+    for (int i = 0; i < P; i++) z[i] /= d[i];
+    for (int i = P - 1; i >= 0; i--) {
+      double s = z[i];
+      for (int m = i + 1; m < P; m++) s -= L[m * P + i] * x[m];
+      x[i] = s;
+    }
+    for (int i = 0; i < P; i++) (which == 0 ? l : cf)[i] = D[i] * x[i];
   }
-  for (int i = 0; i < P; i++) z[i] /= d[i];
-  for (int i = P - 1; i >= 0; i--) {
-    double s = z[i];
-    for (int m = i + 1; m < P; m++) s -= L[m * P + i] * x[m];
-    x[i] = s;
-  }
-  for (int i = 0; i < P; i++) l[i] = D[i] * x[i];
   double c0 = 0.0, v = 0.0;
   for (int a = 0; a < P; a++) {
     c0 += l[a] * bvec[a];
@@ -307,6 +320,25 @@ static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int 
   }
   r.c0 = c0;
   r.var = v;
+  r.err_fit = 0.0;
+  r.err_w = 0.0;
+  for (int i = 0; i < n; i++) {
+    const orc_sample *o = &smp[i];
+    if (o->color != color) continue;
+    double r2 = o->dx * o->dx + o->dy * o->dy;
+    if (!(r2 < R2)) continue;
+    double G = exp(-r2 / (2.0 * sigma_c * sigma_c));
+    double nw = prm->weight_mode == 1 ? 1.0 / sqrt(o->s2) : 1.0 / o->s2;
+    double phi[ORC_MAX_P], l1 = 0.0, f1 = 0.0, fit_k = 0.0;
+    basis(o->dx, o->dy, P, phi);
+    for (int a = 0; a < P; a++) {
+      l1 += fabs(l[a] * phi[a]);
+      f1 += fabs(cf[a] * phi[a]);
+      fit_k += cf[a] * phi[a];
+    }
+    r.err_fit += (G - floor_w) * nw * l1 * (fabs(o->f) + f1);
+    r.err_w += G * (1.0 + r2 / (sigma_c * sigma_c)) * nw * l1 * fabs(o->f - fit_k);
+  }
   if (ell) {
     for (int i = 0; i < n; i++) {
       const orc_sample *o = &smp[i];
@@ -380,13 +412,14 @@ static int check_params(const orc_sensor *sens, int n_sensors, const orc_params 
  *   out           [n_pix][3] chosen C_0 per channel R, G, B (NaN: no sample)
  *   choice        [n_pix][3] chosen level (see n_levels) or -1        (optional)
  *   margin        [n_pix][3] ICI margin |upper - lower| minimum        (optional)
- *   lv_c0, lv_var, lv_pivot, lv_kappa [n_pix][3][J+M], lv_count, lv_valid  (optional)
+ *   lv_c0, lv_var, lv_pivot, lv_kappa, lv_efit, lv_ew [n_pix][3][J+M], lv_count, lv_valid
+ *                 (optional; lv_efit / lv_ew are the rounding scales err_fit / err_w of orc_fit)
  * Returns 0, or a negative code for invalid arguments.
  */
 int orc_reconstruct(const orc_sensor *sens, int n_sensors, const orc_params *p, int64_t n_pix,
                     const int32_t *pu, const int32_t *pv, double *out, int32_t *choice, double *margin,
                     double *lv_c0, double *lv_var, double *lv_pivot, double *lv_kappa,
-                    int32_t *lv_count, int32_t *lv_valid) {
+                    int32_t *lv_count, int32_t *lv_valid, double *lv_efit, double *lv_ew) {
   int rc = check_params(sens, n_sensors, p);
   if (rc) return rc;
   if (n_pix < 0 || (n_pix > 0 && (!pu || !pv || !out))) return -1;
@@ -432,6 +465,8 @@ int orc_reconstruct(const orc_sensor *sens, int n_sensors, const orc_params *p, 
           if (lv_kappa) lv_kappa[o] = lv[l].kappa;
           if (lv_count) lv_count[o] = lv[l].count;
           if (lv_valid) lv_valid[o] = lv[l].valid;
+          if (lv_efit) lv_efit[o] = lv[l].err_fit;
+          if (lv_ew) lv_ew[o] = lv[l].err_w;
         }
       }
     }

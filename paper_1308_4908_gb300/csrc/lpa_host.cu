@@ -1,0 +1,469 @@
+// Host side of the C ABI declared in include/hdr_lpa.h: contexts, device-resident
+// rigs, launch planning (staging footprints, tensor maps) and the kernel launch.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/hdr_lpa.h"
+#include "lpa_dispatch.h"
+#include "lpa_launch.h"
+
+static_assert(HDR_MAX_SENSORS == LPA_MAX_SENSORS, "sensor limits differ");
+static_assert(HDR_MAX_SCALES == LPA_MAX_SCALES, "scale limits differ");
+
+namespace {
+
+thread_local std::string g_err;
+
+hdr_status fail(hdr_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(e_ == cudaErrorMemoryAllocation ? HDR_E_NOMEM : HDR_E_CUDA, "%s: %s (%s:%d)", \
+                  #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+  } while (0)
+
+constexpr int kMaxRigs = 64;
+
+struct RigSensor {
+  hdr_sensor_desc d;   // host copy; frame pointers below replace the caller's
+  float *bias = nullptr, *prnu = nullptr, *rvar = nullptr;
+  uint16_t *satf = nullptr;
+};
+
+struct Rig {
+  int n = 0;
+  RigSensor s[HDR_MAX_SENSORS];
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+}  // namespace
+
+struct hdr_ctx {
+  int device = 0;
+  unsigned int *status = nullptr;
+  Rig rigs[kMaxRigs];
+  EncodeTiledFn encode = nullptr;
+  // staging for the host-buffer entry point
+  uint16_t *raw_stage[HDR_MAX_SENSORS] = {};
+  size_t raw_cap[HDR_MAX_SENSORS] = {};
+  void *out_stage = nullptr;
+  size_t out_cap = 0;
+  uint8_t *choice_stage = nullptr;
+  size_t choice_cap = 0;
+};
+
+namespace {
+
+void free_rig(Rig &r) {
+  for (int i = 0; i < r.n; i++) {
+    cudaFree(r.s[i].bias);
+    cudaFree(r.s[i].prnu);
+    cudaFree(r.s[i].rvar);
+    cudaFree(r.s[i].satf);
+    r.s[i] = RigSensor();
+  }
+  r.n = 0;
+}
+
+bool finite6(const double *a) {
+  for (int i = 0; i < 6; i++)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+// 2x3 affine inverse (FP64).
+void invert_affine(const double m[6], double inv[6]) {
+  double det = m[0] * m[4] - m[1] * m[3];
+  inv[0] = m[4] / det;
+  inv[1] = -m[1] / det;
+  inv[3] = -m[3] / det;
+  inv[4] = m[0] / det;
+  inv[2] = -(inv[0] * m[2] + inv[1] * m[5]);
+  inv[5] = -(inv[3] * m[2] + inv[4] * m[5]);
+}
+
+// c = a o b (apply b first).
+void compose_affine(const double a[6], const double b[6], double c[6]) {
+  c[0] = a[0] * b[0] + a[1] * b[3];
+  c[1] = a[0] * b[1] + a[1] * b[4];
+  c[2] = a[0] * b[2] + a[1] * b[5] + a[2];
+  c[3] = a[3] * b[0] + a[4] * b[3];
+  c[4] = a[3] * b[1] + a[4] * b[4];
+  c[5] = a[3] * b[2] + a[4] * b[5] + a[5];
+}
+
+hdr_status check_params(const hdr_params *p) {
+  if (!p) return fail(HDR_E_INVALID, "params is NULL");
+  if (p->order < 0 || p->order > 2) return fail(HDR_E_INVALID, "order %d not in {0,1,2}", p->order);
+  if (p->n_scales < 1 || p->n_scales > HDR_MAX_SCALES)
+    return fail(HDR_E_INVALID, "n_scales %d not in [1,%d]", p->n_scales, HDR_MAX_SCALES);
+  for (int j = 0; j < p->n_scales; j++) {
+    if (!(p->sigma[j] > 0.0) || !std::isfinite(p->sigma[j])) return fail(HDR_E_INVALID, "sigma[%d] must be > 0", j);
+    if (j > 0 && !(p->sigma[j] > p->sigma[j - 1])) return fail(HDR_E_INVALID, "sigma must be strictly ascending");
+  }
+  if (!(p->green_ratio > 0.0) || !(p->trunc_k > 0.0) || !(p->ici_gamma >= 0.0) || !(p->min_pivot >= 0.0) ||
+      !std::isfinite(p->green_ratio) || !std::isfinite(p->trunc_k) || !std::isfinite(p->ici_gamma))
+    return fail(HDR_E_INVALID, "green_ratio, trunc_k > 0 and ici_gamma, min_pivot >= 0 required");
+  if (p->out_w < 0 || p->out_h < 0) return fail(HDR_E_INVALID, "negative output size");
+  if ((long long)p->out_w * p->out_h > (1LL << 31) / 4)
+    return fail(HDR_E_UNSUPPORTED, "output of %dx%d exceeds this build's size limit", p->out_w, p->out_h);
+  if (!finite6(p->out_affine)) return fail(HDR_E_INVALID, "out_affine not finite");
+  if (p->out_dtype != 0 && p->out_dtype != 1) return fail(HDR_E_INVALID, "out_dtype must be 0 or 1");
+  if (p->accum != 0 && p->accum != 1) return fail(HDR_E_INVALID, "accum must be 0 or 1");
+  return HDR_OK;
+}
+
+// Fill the launch descriptor for one frame. raw: device pointers per sensor.
+hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L) {
+  memset(&L, 0, sizeof(L));
+  L.n_sensors = rig.n;
+  L.order = p->order;
+  L.n_scales = p->n_scales;
+  for (int j = 0; j < p->n_scales; j++) L.sigma[j] = (float)p->sigma[j];
+  L.green_ratio = (float)p->green_ratio;
+  L.trunc_k = (float)p->trunc_k;
+  L.ici_gamma = (float)p->ici_gamma;
+  L.min_pivot = (float)p->min_pivot;
+  L.cond_fallback = (float)p->cond_fallback;
+  L.taper = (float)std::exp(-0.5 * p->trunc_k * p->trunc_k);
+  L.out_w = p->out_w;
+  L.out_h = p->out_h;
+  L.tiles_x = (p->out_w + LPA_TILE - 1) / LPA_TILE;
+  L.tiles_y = (p->out_h + LPA_TILE - 1) / LPA_TILE;
+  L.out_half = p->out_dtype;
+  L.status = ctx->status;
+  const double rmax = p->trunc_k * p->sigma[p->n_scales - 1] * std::fmax(1.0, p->green_ratio);
+  uint32_t off = 0, tx = 0;
+  for (int s = 0; s < rig.n; s++) {
+    const hdr_sensor_desc &d = rig.s[s].d;
+    LpaSensorK &K = L.s[s];
+    if (!raw[s]) return fail(HDR_E_INVALID, "raw pointer of sensor %d is NULL", s);
+    if (reinterpret_cast<uintptr_t>(raw[s]) % 16) return fail(HDR_E_INVALID, "raw pointer of sensor %d not 16-byte aligned", s);
+    double tinv[6];
+    invert_affine(d.affine, tinv);
+    compose_affine(tinv, p->out_affine, K.G);
+    for (int i = 0; i < 4; i++) K.Gf[i] = (float)K.G[i < 2 ? i : i + 1];
+    K.A[0] = (float)d.affine[0];
+    K.A[1] = (float)d.affine[1];
+    K.A[2] = (float)d.affine[3];
+    K.A[3] = (float)d.affine[4];
+    const double hxu = std::sqrt(tinv[0] * tinv[0] + tinv[1] * tinv[1]);
+    const double hyu = std::sqrt(tinv[3] * tinv[3] + tinv[4] * tinv[4]);
+    K.hx_unit = (float)hxu;
+    K.hy_unit = (float)hyu;
+    const double gtn = d.gain * d.exposure * d.nd;
+    K.inv_gtn = (float)(1.0 / gtn);
+    K.gtn2 = (float)(gtn * gtn);
+    K.gain = (float)d.gain;
+    K.read_var = (float)d.read_var;
+    K.black = (float)d.black;
+    K.sat = (float)d.sat;
+    K.width = d.width;
+    K.height = d.height;
+    K.bias = rig.s[s].bias;
+    K.prnu = rig.s[s].prnu;
+    K.rvar = rig.s[s].rvar;
+    K.satf = rig.s[s].satf;
+    // staging box: the tile's pixel points span |G_lin| * (TILE-1) in sensor space; add the
+    // largest window's half extent plus margin on both sides, the floor of the origin and
+    // the alignment of the origin (x to 8 elements = 16 bytes, y to 2)
+    K.ext_x = (float)(rmax * hxu + LPA_MARGIN);
+    K.ext_y = (float)(rmax * hyu + LPA_MARGIN);
+    const double span_x = (std::fabs(K.G[0]) + std::fabs(K.G[1])) * (LPA_TILE - 1);
+    const double span_y = (std::fabs(K.G[3]) + std::fabs(K.G[4])) * (LPA_TILE - 1);
+    int bw = (int)std::ceil(span_x + 2.0 * K.ext_x) + 9;
+    int bh = (int)std::ceil(span_y + 2.0 * K.ext_y) + 3;
+    bw = (bw + 7) / 8 * 8;
+    bh = (bh + 1) / 2 * 2;
+    if (bw > 256 || bh > 256)
+      return fail(HDR_E_UNSUPPORTED, "sensor %d staging box %dx%d exceeds 256 (window or output scale too large)", s, bw, bh);
+    K.box_w = bw;
+    K.box_h = bh;
+    off = (off + 127) / 128 * 128;
+    K.off_raw = off;
+    off += (uint32_t)(bw * bh * 2);
+    tx += (uint32_t)(bw * bh * 2);
+    off = (off + 127) / 128 * 128;
+    K.off_planes = off;
+    off += (uint32_t)(bw * bh * 8);
+    // tensor map of the raw frame
+    cuuint64_t gdim[2] = {(cuuint64_t)d.width, (cuuint64_t)d.height};
+    cuuint64_t gstride[1] = {(cuuint64_t)d.pitch_elems * 2};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = ctx->encode(&K.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t *>(raw[s]), gdim, gstride,
+                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled failed for sensor %d (code %d)", s, (int)cr);
+  }
+  L.tx_bytes = tx;
+  L.smem_bytes = off;
+  int max_smem = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  if ((int)off > max_smem - 1024)
+    return fail(HDR_E_UNSUPPORTED, "staging needs %u bytes of shared memory (limit %d)", off, max_smem - 1024);
+  return HDR_OK;
+}
+
+hdr_status launch(const LpaLaunch &L, int accum, bool diag, cudaStream_t st) {
+  if (L.tiles_x == 0 || L.tiles_y == 0) return HDR_OK;
+  cudaError_t e;
+  switch (L.order) {
+    case 0: e = lpa_launch_order0(L, accum != 0, diag, st); break;
+    case 1: e = lpa_launch_order1(L, accum != 0, diag, st); break;
+    default: e = lpa_launch_order2(L, accum != 0, diag, st); break;
+  }
+  if (e != cudaSuccess) return fail(HDR_E_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  return HDR_OK;
+}
+
+hdr_status common_checks(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const void *raw, const void *out) {
+  if (!ctx) return fail(HDR_E_INVALID, "ctx is NULL");
+  if (rig_id < 0 || rig_id >= kMaxRigs || ctx->rigs[rig_id].n == 0)
+    return fail(HDR_E_INVALID, "rig %d is not defined", rig_id);
+  hdr_status st = check_params(params);
+  if (st) return st;
+  if (!raw) return fail(HDR_E_INVALID, "raw pointer array is NULL");
+  if (!out && (long long)params->out_w * params->out_h > 0) return fail(HDR_E_INVALID, "output pointer is NULL");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  return HDR_OK;
+}
+
+hdr_status reconstruct_impl(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_dev,
+                            void *out_dev, uint8_t *choice_dev, float *levels_dev, void *stream) {
+  hdr_status st = common_checks(ctx, rig_id, params, raw_dev, out_dev);
+  if (st) return st;
+  LpaLaunch L;
+  st = plan(ctx, ctx->rigs[rig_id], params, raw_dev, L);
+  if (st) return st;
+  L.out = out_dev;
+  L.choice = choice_dev;
+  L.levels = levels_dev;
+  return launch(L, params->accum, levels_dev != nullptr, (cudaStream_t)stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void hdr_params_default(hdr_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->order = 2;
+  p->n_scales = 4;
+  p->sigma[0] = 0.5;
+  p->sigma[1] = 0.8;
+  p->sigma[2] = 1.2;
+  p->sigma[3] = 1.8;
+  p->green_ratio = 1.0 / std::sqrt(2.0);
+  p->trunc_k = 3.0;
+  p->ici_gamma = 2.0;
+  p->min_pivot = 1e-3;
+  p->cond_fallback = 1e6;
+  p->out_affine[0] = 1.0;
+  p->out_affine[4] = 1.0;
+  p->out_dtype = 0;
+  p->accum = 0;
+}
+
+hdr_status hdr_create(int device, hdr_ctx **out) {
+  if (!out) return fail(HDR_E_INVALID, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(HDR_E_INVALID, "device %d not present (%d devices)", device, n);
+  CUDA_TRY(cudaSetDevice(device));
+  hdr_ctx *c = new (std::nothrow) hdr_ctx();
+  if (!c) return fail(HDR_E_NOMEM, "host allocation failed");
+  c->device = device;
+  cudaDriverEntryPointQueryResult q;
+  void *fn = nullptr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    delete c;
+    return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
+  }
+  c->encode = reinterpret_cast<EncodeTiledFn>(fn);
+  e = cudaMalloc(&c->status, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    cudaFree(c->status);
+    delete c;
+    return fail(HDR_E_NOMEM, "status word allocation failed: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return HDR_OK;
+}
+
+void hdr_destroy(hdr_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (int r = 0; r < kMaxRigs; r++) free_rig(ctx->rigs[r]);
+  for (int s = 0; s < HDR_MAX_SENSORS; s++) cudaFree(ctx->raw_stage[s]);
+  cudaFree(ctx->out_stage);
+  cudaFree(ctx->choice_stage);
+  cudaFree(ctx->status);
+  delete ctx;
+}
+
+hdr_status hdr_set_rig(hdr_ctx *ctx, int32_t rig_id, int32_t n_sensors, const hdr_sensor_desc *sensors) {
+  if (!ctx) return fail(HDR_E_INVALID, "ctx is NULL");
+  if (rig_id < 0 || rig_id >= kMaxRigs) return fail(HDR_E_INVALID, "rig_id %d not in [0,%d)", rig_id, kMaxRigs);
+  if (n_sensors < 1 || n_sensors > HDR_MAX_SENSORS)
+    return fail(HDR_E_INVALID, "n_sensors %d not in [1,%d]", n_sensors, HDR_MAX_SENSORS);
+  if (!sensors) return fail(HDR_E_INVALID, "sensors is NULL");
+  for (int s = 0; s < n_sensors; s++) {
+    const hdr_sensor_desc &d = sensors[s];
+    if (d.width < 1 || d.height < 1 || d.pitch_elems < d.width || (d.pitch_elems * 2) % 16)
+      return fail(HDR_E_INVALID, "sensor %d: bad size %dx%d / pitch %d (pitch*2 must be a multiple of 16)", s,
+                  d.width, d.height, d.pitch_elems);
+    if (d.width > (1 << 20) || d.height > (1 << 20)) return fail(HDR_E_UNSUPPORTED, "sensor %d too large", s);
+    if (d.cfa != 0) return fail(HDR_E_UNSUPPORTED, "sensor %d: only the RGGB layout (cfa 0) is implemented", s);
+    if (!(d.gain > 0) || !(d.exposure > 0) || !(d.nd > 0) || !std::isfinite(d.gain * d.exposure * d.nd))
+      return fail(HDR_E_INVALID, "sensor %d: gain, exposure and nd must be finite and > 0", s);
+    if (!d.read_var_frame && !(d.read_var > 0)) return fail(HDR_E_INVALID, "sensor %d: read_var must be > 0", s);
+    if (!std::isfinite(d.black) || !std::isfinite(d.sat)) return fail(HDR_E_INVALID, "sensor %d: black/sat not finite", s);
+    if (!finite6(d.affine)) return fail(HDR_E_INVALID, "sensor %d: affine not finite", s);
+    const double det = d.affine[0] * d.affine[4] - d.affine[1] * d.affine[3];
+    if (!(std::fabs(det) > 1e-12)) return fail(HDR_E_INVALID, "sensor %d: affine is singular", s);
+    const size_t npx = (size_t)d.width * d.height;
+    for (size_t i = 0; d.prnu_frame && i < npx; i++)
+      if (!(d.prnu_frame[i] > 0.f) || !std::isfinite(d.prnu_frame[i]))
+        return fail(HDR_E_INVALID, "sensor %d: prnu_frame must be finite and > 0", s);
+    for (size_t i = 0; d.read_var_frame && i < npx; i++)
+      if (!(d.read_var_frame[i] > 0.f) || !std::isfinite(d.read_var_frame[i]))
+        return fail(HDR_E_INVALID, "sensor %d: read_var_frame must be finite and > 0", s);
+  }
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  Rig &rig = ctx->rigs[rig_id];
+  if (rig.n) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    free_rig(rig);
+  }
+  Rig fresh;
+  fresh.n = n_sensors;
+  for (int s = 0; s < n_sensors; s++) {
+    RigSensor &rs = fresh.s[s];
+    rs.d = sensors[s];
+    const size_t npx = (size_t)rs.d.width * rs.d.height;
+    auto up = [&](const void *src, size_t bytes, void **dst) -> cudaError_t {
+      if (!src) return cudaSuccess;
+      cudaError_t e = cudaMalloc(dst, bytes);
+      if (e != cudaSuccess) return e;
+      return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = up(rs.d.bias_frame, npx * 4, (void **)&rs.bias);
+    if (e == cudaSuccess) e = up(rs.d.prnu_frame, npx * 4, (void **)&rs.prnu);
+    if (e == cudaSuccess) e = up(rs.d.read_var_frame, npx * 4, (void **)&rs.rvar);
+    if (e == cudaSuccess) e = up(rs.d.sat_frame, npx * 2, (void **)&rs.satf);
+    rs.d.bias_frame = rs.d.prnu_frame = rs.d.read_var_frame = nullptr;
+    rs.d.sat_frame = nullptr;
+    if (e != cudaSuccess) {
+      free_rig(fresh);
+      return fail(e == cudaErrorMemoryAllocation ? HDR_E_NOMEM : HDR_E_CUDA, "rig upload failed: %s",
+                  cudaGetErrorString(e));
+    }
+  }
+  rig = fresh;
+  for (int s = 0; s < n_sensors; s++) fresh.s[s] = RigSensor();   // ownership moved
+  fresh.n = 0;
+  return HDR_OK;
+}
+
+hdr_status hdr_reconstruct(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_dev,
+                           void *out_dev, uint8_t *choice_dev, void *cuda_stream) {
+  return reconstruct_impl(ctx, rig_id, params, raw_dev, out_dev, choice_dev, nullptr, cuda_stream);
+}
+
+hdr_status hdr_reconstruct_levels(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                                  const uint16_t *const *raw_dev, void *out_dev, uint8_t *choice_dev,
+                                  float *levels_dev, void *cuda_stream) {
+  if (!levels_dev && (long long)params->out_w * params->out_h > 0) return fail(HDR_E_INVALID, "levels_dev is NULL");
+  return reconstruct_impl(ctx, rig_id, params, raw_dev, out_dev, choice_dev, levels_dev, cuda_stream);
+}
+
+hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_host,
+                                void *out_host, uint8_t *choice_host, void *cuda_stream) {
+  hdr_status st = common_checks(ctx, rig_id, params, raw_host, out_host);
+  if (st) return st;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const Rig &rig = ctx->rigs[rig_id];
+  const uint16_t *raw_dev[HDR_MAX_SENSORS];
+  for (int s = 0; s < rig.n; s++) {
+    if (!raw_host[s]) return fail(HDR_E_INVALID, "raw_host[%d] is NULL", s);
+    const size_t bytes = (size_t)rig.s[s].d.pitch_elems * rig.s[s].d.height * 2;
+    if (ctx->raw_cap[s] < bytes) {
+      CUDA_TRY(cudaStreamSynchronize(stream));
+      cudaFree(ctx->raw_stage[s]);
+      ctx->raw_stage[s] = nullptr;
+      ctx->raw_cap[s] = 0;
+      CUDA_TRY(cudaMalloc(&ctx->raw_stage[s], bytes));
+      ctx->raw_cap[s] = bytes;
+    }
+    CUDA_TRY(cudaMemcpyAsync(ctx->raw_stage[s], raw_host[s], bytes, cudaMemcpyHostToDevice, stream));
+    raw_dev[s] = ctx->raw_stage[s];
+  }
+  const size_t npx = (size_t)params->out_w * params->out_h * 3;
+  const size_t obytes = npx * (params->out_dtype ? 2 : 4);
+  if (ctx->out_cap < obytes) {
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    cudaFree(ctx->out_stage);
+    ctx->out_stage = nullptr;
+    ctx->out_cap = 0;
+    CUDA_TRY(cudaMalloc(&ctx->out_stage, obytes));
+    ctx->out_cap = obytes;
+  }
+  if (choice_host && ctx->choice_cap < npx) {
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    cudaFree(ctx->choice_stage);
+    ctx->choice_stage = nullptr;
+    ctx->choice_cap = 0;
+    CUDA_TRY(cudaMalloc(&ctx->choice_stage, npx));
+    ctx->choice_cap = npx;
+  }
+  st = reconstruct_impl(ctx, rig_id, params, raw_dev, ctx->out_stage, choice_host ? ctx->choice_stage : nullptr,
+                        nullptr, cuda_stream);
+  if (st) return st;
+  if (obytes) CUDA_TRY(cudaMemcpyAsync(out_host, ctx->out_stage, obytes, cudaMemcpyDeviceToHost, stream));
+  if (choice_host && npx) CUDA_TRY(cudaMemcpyAsync(choice_host, ctx->choice_stage, npx, cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  return HDR_OK;
+}
+
+hdr_status hdr_check(hdr_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return fail(HDR_E_INVALID, "ctx is NULL");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+  CUDA_TRY(cudaGetLastError());
+  unsigned int word = 0;
+  CUDA_TRY(cudaMemcpy(&word, ctx->status, sizeof(word), cudaMemcpyDeviceToHost));
+  if (word) CUDA_TRY(cudaMemset(ctx->status, 0, sizeof(word)));
+  if (word & LPA_ERR_TIMEOUT) return fail(HDR_E_TIMEOUT, "a bounded device wait ran out (status 0x%x)", word);
+  if (word & LPA_ERR_BOUNDS) return fail(HDR_E_INTERNAL, "a window left the staged footprint (status 0x%x)", word);
+  return HDR_OK;
+}
+
+const char *hdr_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,560 @@
+// Fused multi-sensor HDR reconstruction kernel for sm_103a.
+//
+// One CTA reconstructs one 16x16 tile of output pixels, one thread per pixel.
+//   1. Stage: the raw uint16 footprint of the tile in every sensor is fetched
+//      by one bulk tensor copy per sensor (cp.async.bulk.tensor, completion on
+//      an mbarrier with a bounded wait), then converted once per sample to
+//      radiant power and inverse variance (Section 6, Eqs. 18 and 20;
+//      saturated and out-of-sensor samples get inverse variance 0 = excluded)
+//      into four colour-phase planes of float2 in shared memory.
+//   2. Fit: per channel and window scale the thread walks the samples of its
+//      window in sensor space (the bounding box of the pre-image of the
+//      reference-space disc), computes the reference-frame offset d = X - P_j
+//      from small sensor-space offsets (Section 4.2), and accumulates the
+//      distinct moments sum w d^a d^b (a+b <= 2M), sum w f phi and
+//      sum w K d^a d^b in registers (w = K / s2, K the tapered Gaussian window
+//      of Eq. 8). The normal equations of Eq. 6 are then equilibrated and
+//      factored (LDL^T, FP32; FP64 when the condition estimate is large),
+//      giving C_0 and Var C_0.
+//   3. Scale choice: intersection of confidence intervals over the scales in
+//      ascending order, with a warp-wide early exit once every lane's
+//      intersection is empty; order fallback at the largest scale; NaN when
+//      nothing is usable.
+// Warps hold pixels of one output parity class (16x8 pixels, stride 2), so on
+// rigs close to a translation at 1x output every lane sees the same sample
+// layout and the window loops run without divergence.
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lpa_launch.h"
+
+namespace lpa {
+
+#define LPA_FULL 0xffffffffu
+
+__host__ __device__ constexpr int mono_index(int a, int b) { return (a + b) * (a + b + 1) / 2 + b; }
+__host__ __device__ constexpr int n_unknowns(int order) { return order == 0 ? 1 : (order == 1 ? 3 : 6); }
+__host__ __device__ constexpr int n_monos(int order) { return order == 0 ? 1 : (order == 1 ? 6 : 15); }
+// exponents of the basis [1, dx, dy, dx^2, dx dy, dy^2] (Section 5.1, tril order)
+__host__ __device__ constexpr int ex(int m) { return (m == 1 || m == 4) ? 1 : (m == 3 ? 2 : 0); }
+__host__ __device__ constexpr int ey(int m) { return (m == 2 || m == 4) ? 1 : (m == 5 ? 2 : 0); }
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after `limit` polls (each poll may
+// suspend the thread for a hardware-defined interval).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------- moments
+
+// Error-free sum of two floats (Knuth's two-sum) and product (FMA residual).
+__device__ __forceinline__ void comp_add(float &hi, float &lo, float a, float b) {
+  float p = __fmul_rn(a, b);
+  float pe = __fmaf_rn(a, b, -p);
+  float s = __fadd_rn(hi, p);
+  float bb = __fsub_rn(s, hi);
+  float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+template <int ORDER, bool COMP>
+struct Moments {
+  static constexpr int NA = n_monos(ORDER);     // sum w d^a d^b, a+b <= 2M
+  static constexpr int NB = n_unknowns(ORDER);  // sum w f phi
+  float a[NA], b[NB], k[NA];                    // k: sum w K d^a d^b (variance of C_0)
+  float al[COMP ? NA : 1], bl[COMP ? NB : 1], kl[COMP ? NA : 1];
+  float cnt;
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NA; i++) a[i] = k[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < NB; i++) b[i] = 0.f;
+    if (COMP) {
+#pragma unroll
+      for (int i = 0; i < NA; i++) al[i] = kl[i] = 0.f;
+#pragma unroll
+      for (int i = 0; i < NB; i++) bl[i] = 0.f;
+    }
+    cnt = 0.f;
+  }
+
+  __device__ __forceinline__ void add(float dx, float dy, float w, float wf, float wk) {
+    float m[15];
+    m[0] = 1.f;
+    if (NA > 1) {
+      m[1] = dx;
+      m[2] = dy;
+      m[3] = dx * dx;
+      m[4] = dx * dy;
+      m[5] = dy * dy;
+    }
+    if (NA > 6) {
+      m[6] = m[3] * dx;
+      m[7] = m[3] * dy;
+      m[8] = m[4] * dy;
+      m[9] = m[5] * dy;
+      m[10] = m[3] * m[3];
+      m[11] = m[3] * m[4];
+      m[12] = m[3] * m[5];
+      m[13] = m[4] * m[5];
+      m[14] = m[5] * m[5];
+    }
+    if (COMP) {
+#pragma unroll
+      for (int i = 0; i < NA; i++) {
+        comp_add(a[i], al[i], w, m[i]);
+        comp_add(k[i], kl[i], wk, m[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < NB; i++) comp_add(b[i], bl[i], wf, m[i]);
+    } else {
+      a[0] += w;
+      k[0] += wk;
+      b[0] += wf;
+#pragma unroll
+      for (int i = 1; i < NA; i++) {
+        a[i] = fmaf(w, m[i], a[i]);
+        k[i] = fmaf(wk, m[i], k[i]);
+      }
+#pragma unroll
+      for (int i = 1; i < NB; i++) b[i] = fmaf(wf, m[i], b[i]);
+    }
+    cnt += 1.f;
+  }
+
+  template <typename T>
+  __device__ __forceinline__ T A(int i) const { return COMP ? (T)a[i] + (T)al[i] : (T)a[i]; }
+  template <typename T>
+  __device__ __forceinline__ T B(int i) const { return COMP ? (T)b[i] + (T)bl[i] : (T)b[i]; }
+  template <typename T>
+  __device__ __forceinline__ T Kv(int i) const { return COMP ? (T)k[i] + (T)kl[i] : (T)k[i]; }
+};
+
+// ---------------------------------------------------------------- solve
+
+struct FitOut {
+  float c0, var;
+  float dmin, dmax;  // extreme pivots of the equilibrated LDL^T
+  bool valid;
+};
+
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
+
+// Eq. 6 for the first P basis functions: A = Phi^T W Phi is Jacobi-equilibrated
+// (D A D, D = diag(A)^{-1/2}) and factored LDL^T; l = A^{-1} e_0, C_0 = l^T b,
+// Var C_0 = l^T (Phi^T W S W Phi) l with S the sample variances.
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
+
+template <typename T, int P, class MOM>
+__device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
+  FitOut r;
+  T s[P];
+  bool pos = true;
+#pragma unroll
+  for (int i = 0; i < P; i++) {
+    T d = m.template A<T>(mono_index(2 * ex(i), 2 * ey(i)));
+    pos = pos && (d > T(0));
+    s[i] = d > T(0) ? rsqrt_t(d) : T(0);
+  }
+  // equilibrated matrix, lower triangle, overwritten by L (below the diagonal) and D
+  T a[P * (P + 1) / 2];
+#pragma unroll
+  for (int i = 0; i < P; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++) a[tri(i, j)] = m.template A<T>(mono_index(ex(i) + ex(j), ey(i) + ey(j))) * s[i] * s[j];
+  // triangular loops are written with fixed trip counts and guards so that they unroll fully
+  T dinv[P];
+  T dmin = T(1e30), dmax = T(0);
+#pragma unroll
+  for (int j = 0; j < P; j++) {
+    T dj = a[tri(j, j)];
+#pragma unroll
+    for (int q = 0; q < P; q++)
+      if (q < j) dj -= a[tri(j, q)] * a[tri(j, q)] * a[tri(q, q)];
+    a[tri(j, j)] = dj;
+    dmin = dj < dmin ? dj : dmin;
+    dmax = dj > dmax ? dj : dmax;
+    dinv[j] = dj > T(0) ? rcp_t(dj) : T(0);
+#pragma unroll
+    for (int i = 0; i < P; i++) {
+      if (i > j) {
+        T t = a[tri(i, j)];
+#pragma unroll
+        for (int q = 0; q < P; q++)
+          if (q < j) t -= a[tri(i, q)] * a[tri(j, q)] * a[tri(q, q)];
+        a[tri(i, j)] = t * dinv[j];
+      }
+    }
+  }
+  r.dmin = (float)dmin;
+  r.dmax = (float)dmax;
+  r.valid = pos && (m.cnt >= (float)P) && (dmin > (T)min_pivot);
+  // l = D (D A D)^{-1} D e_0: forward (unit L), diagonal, backward (L^T)
+  T x[P];
+#pragma unroll
+  for (int i = 0; i < P; i++) {
+    T t = (i == 0) ? s[0] : T(0);
+#pragma unroll
+    for (int q = 0; q < P; q++)
+      if (q < i) t -= a[tri(i, q)] * x[q];
+    x[i] = t;
+  }
+#pragma unroll
+  for (int i = 0; i < P; i++) x[i] *= dinv[i];
+#pragma unroll
+  for (int ii = 0; ii < P; ii++) {
+    const int i = P - 1 - ii;
+    T t = x[i];
+#pragma unroll
+    for (int q = 0; q < P; q++)
+      if (q > i) t -= a[tri(q, i)] * x[q];
+    x[i] = t;
+  }
+  T c0 = T(0), var = T(0);
+#pragma unroll
+  for (int i = 0; i < P; i++) {
+    const T li = s[i] * x[i];
+    c0 += li * m.template B<T>(i);
+    T row = T(0);
+#pragma unroll
+    for (int j = 0; j < P; j++) row += s[j] * x[j] * m.template Kv<T>(mono_index(ex(i) + ex(j), ey(i) + ey(j)));
+    var += li * row;
+  }
+  r.c0 = (float)c0;
+  r.var = (float)var;
+  return r;
+}
+
+// Bound on the absolute error of an FP32 pivot of the equilibrated normal matrix
+// (unit diagonal): at most 6 x 6 terms accumulated over a few hundred samples at
+// 2^-24 relative rounding each stays well below this.
+#define LPA_PIVOT_FP32_ERR 1e-4f
+
+// FP32 solve; the same solve in FP64 when the FP32 pivots span more than
+// cond_fallback and the fit could still pass min_pivot in exact arithmetic.
+template <int P, class MOM>
+__device__ __forceinline__ FitOut solve_with_fallback(const MOM &m, float min_pivot, float cond_fallback) {
+  FitOut r = solve<float, P>(m, min_pivot);
+  bool redo = cond_fallback > 0.f && m.cnt >= (float)P && !(r.dmin * cond_fallback >= r.dmax) &&
+              r.dmin > min_pivot - LPA_PIVOT_FP32_ERR;
+  if (redo) r = solve<double, P>(m, min_pivot);
+  return r;
+}
+
+// Lower-order fits at the largest scale reuse the leading block of the moments.
+template <int ORDER, int I, class MOM>
+__device__ __forceinline__ FitOut fallback_fit(const MOM &m, float min_pivot, float cond_fallback) {
+  if constexpr (ORDER - 1 - I == 1) return solve_with_fallback<3>(m, min_pivot, cond_fallback);
+  else return solve_with_fallback<1>(m, min_pivot, cond_fallback);
+}
+
+// ---------------------------------------------------------------- scale choice
+
+struct Ici {
+  float lo, hi, val;
+  int choice;
+  bool done;
+  __device__ __forceinline__ void reset(bool active) {
+    lo = -INFINITY;
+    hi = INFINITY;
+    val = __int_as_float(0x7fffffff);
+    choice = 255;
+    done = !active;
+  }
+  // running intersection of C_0 +- gamma sqrt(Var C_0) over usable scales in ascending order
+  __device__ __forceinline__ void step(const FitOut &f, int level, float gamma) {
+    if (done || !f.valid) return;
+    float h = gamma * sqrtf(fmaxf(f.var, 0.f));
+    float nlo = fmaxf(lo, f.c0 - h), nhi = fminf(hi, f.c0 + h);
+    if (nlo > nhi) {
+      done = true;
+      return;
+    }
+    lo = nlo;
+    hi = nhi;
+    val = f.c0;
+    choice = level;
+  }
+};
+
+// ---------------------------------------------------------------- kernel
+
+// sensor-space positions are clamped to +-LPA_FAR px (far outside any sensor) before integer conversion
+#define LPA_FAR 1.0e7
+
+struct Anchor {
+  int ix, iy;
+  float fx, fy;
+};
+
+template <int ORDER, bool COMP>
+__device__ __forceinline__ void accumulate_sensor(Moments<ORDER, COMP> &m, const LpaSensorK &S,
+                                                  const Anchor &an, int du, int dv, int c, float R, float R2,
+                                                  float cexp, float taper, int x0, int y0,
+                                                  const unsigned char *smem, bool active, unsigned *status) {
+  // the pixel's point in sensor s: anchor (FP64 at the 8x8 block corner) + small FP32 step
+  float px = an.fx + (float)du * S.Gf[0] + (float)dv * S.Gf[1];
+  float py = an.fy + (float)du * S.Gf[2] + (float)dv * S.Gf[3];
+  float flx = floorf(px), fly = floorf(py);
+  const int ix = an.ix + (int)flx, iy = an.iy + (int)fly;
+  const float fx = px - flx, fy = py - fly;
+  const float hx = R * S.hx_unit + 1e-3f, hy = R * S.hy_unit + 1e-3f;
+  const int PW = S.box_w >> 1, PH = S.box_h >> 1;
+  const float2 *planes = reinterpret_cast<const float2 *>(smem + S.off_planes);
+  const float a00 = S.A[0], a01 = S.A[1], a10 = S.A[2], a11 = S.A[3];
+  const float sx = 2.f * a00, sy = 2.f * a10;
+  // colour phases of channel c: R (0,0); G (1,0) and (0,1); B (1,1)
+  const int nsub = (c == 1) ? 2 : 1;
+#pragma unroll 1
+  for (int sub = 0; sub < nsub; sub++) {
+    const int ox = (c == 0) ? 0 : (c == 2 ? 1 : 1 - sub);
+    const int oy = (c == 0) ? 0 : (c == 2 ? 1 : sub);
+    const int bx = ix - ox, by = iy - oy;
+    const int bxe = bx - (bx & 1), bye = by - (by & 1);
+    const float rx = (float)(bx - bxe) + fx;  // q_x - (ox + bxe), in [0, 2)
+    const float ry = (float)(by - bye) + fy;
+    const int ilo = (int)ceilf((rx - hx) * 0.5f), ihi = (int)floorf((rx + hx) * 0.5f);
+    const int jlo = (int)ceilf((ry - hy) * 0.5f), jhi = (int)floorf((ry + hy) * 0.5f);
+    const int ni = active ? max(ihi - ilo + 1, 0) : 0;
+    const int nj = active ? max(jhi - jlo + 1, 0) : 0;
+    const int NI = __reduce_max_sync(LPA_FULL, ni);
+    const int NJ = __reduce_max_sync(LPA_FULL, nj);
+    if (NI == 0 || NJ == 0) continue;
+    const int pc0 = ((bxe - x0) >> 1) + ilo;
+    const int pr0 = ((bye - y0) >> 1) + jlo;
+    const bool colok = pc0 >= 0 && pc0 + NI <= PW;
+    const float2 *pl = planes + (ox + 2 * oy) * (PH * PW);
+    const float Dx0 = 2.f * (float)ilo - rx;
+#pragma unroll 1
+    for (int r = 0; r < NJ; r++) {
+      const int pr = pr0 + r;
+      if (!(colok && pr >= 0 && pr < PH)) {
+        if (active && r < nj) atomicOr(status, LPA_ERR_BOUNDS);
+        continue;
+      }
+      const float Dy = 2.f * (float)(jlo + r) - ry;
+      const float dxr = fmaf(a00, Dx0, a01 * Dy), dyr = fmaf(a10, Dx0, a11 * Dy);
+      const float2 *rowp = pl + pr * PW + pc0;
+      float qf = 0.f;
+#pragma unroll 2
+      for (int q = 0; q < NI; q++, qf += 1.f) {
+        const float dx = fmaf(qf, sx, dxr), dy = fmaf(qf, sy, dyr);
+        const float r2 = fmaf(dx, dx, dy * dy);
+        const float2 fv = rowp[q];
+        if (r2 < R2 && fv.y > 0.f) {
+          const float K = ex2_approx(r2 * cexp) - taper;  // Eq. 8, truncated and tapered
+          const float w = K * fv.y;                       // window x inverse variance
+          m.add(dx, dy, w, w * fv.x, w * K);
+        }
+      }
+    }
+  }
+}
+
+template <int ORDER, bool COMP, bool DIAG>
+__global__ void __launch_bounds__(LPA_THREADS, 2) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
+  __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
+  __shared__ __align__(8) uint64_t mbar;
+
+  const int tid = threadIdx.x;
+  // once any CTA's bounded wait has run out, later CTAs retire at once
+  if (*reinterpret_cast<volatile unsigned int *>(L.status) & LPA_ERR_TIMEOUT) return;
+  const int tu = blockIdx.x % L.tiles_x, tv = blockIdx.x / L.tiles_x;
+  const int u0 = tu * LPA_TILE, v0 = tv * LPA_TILE;
+  const int S = L.n_sensors;
+
+  if (tid == 0) mbar_init(&mbar, 1);
+  if (tid < S) {
+    // staged footprint: sensor-space bounding box of the tile's pixel points, grown by the
+    // largest window's half extent and the margin; x origin on a 16-byte boundary
+    const LpaSensorK &Sk = L.s[tid];
+    double mnx = 1e300, mny = 1e300;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      double uu = u0 + (k & 1) * (LPA_TILE - 1), vv = v0 + (k >> 1) * (LPA_TILE - 1);
+      double qx = Sk.G[0] * uu + Sk.G[1] * vv + Sk.G[2];
+      double qy = Sk.G[3] * uu + Sk.G[4] * vv + Sk.G[5];
+      mnx = fmin(mnx, fmin(fmax(qx, -LPA_FAR), LPA_FAR));
+      mny = fmin(mny, fmin(fmax(qy, -LPA_FAR), LPA_FAR));
+    }
+    int x0 = (int)floor(mnx - Sk.ext_x);
+    int y0 = (int)floor(mny - Sk.ext_y);
+    x0 -= ((x0 % 8) + 8) % 8;
+    y0 -= (y0 & 1);
+    fp_x0[tid] = x0;
+    fp_y0[tid] = y0;
+  }
+  if (tid >= 32 && tid < 32 + 4 * S) {
+    const int k = tid - 32, a = k & 3, s = k >> 2;
+    const LpaSensorK &Sk = L.s[s];
+    double uu = u0 + (a & 1) * LPA_ANCHOR, vv = v0 + (a >> 1) * LPA_ANCHOR;
+    double qx = fmin(fmax(Sk.G[0] * uu + Sk.G[1] * vv + Sk.G[2], -LPA_FAR), LPA_FAR);
+    double qy = fmin(fmax(Sk.G[3] * uu + Sk.G[4] * vv + Sk.G[5], -LPA_FAR), LPA_FAR);
+    double flx = floor(qx), fly = floor(qy);
+    anchors[a][s] = Anchor{(int)flx, (int)fly, (float)(qx - flx), (float)(qy - fly)};
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&mbar, L.tx_bytes);
+    for (int s = 0; s < S; s++) tma_load_2d(smem + L.s[s].off_raw, &L.s[s].tmap, fp_x0[s], fp_y0[s], &mbar);
+  }
+  bool landed = mbar_wait_bounded(&mbar, 0, 1u << 20);
+  landed = __syncthreads_and(landed);
+  if (!landed) {
+    if (tid == 0) {
+      atomicOr(L.status, LPA_ERR_TIMEOUT);
+      mbar_wait_bounded(&mbar, 0, 1u << 20);  // let copies in flight land before the CTA retires
+    }
+    return;
+  }
+
+  // convert the staged raw values once per sample: Eq. 18 and the inverse of Eq. 20
+  for (int s = 0; s < S; s++) {
+    const LpaSensorK &Sk = L.s[s];
+    const uint16_t *raw = reinterpret_cast<const uint16_t *>(smem + Sk.off_raw);
+    float2 *planes = reinterpret_cast<float2 *>(smem + Sk.off_planes);
+    const int bw = Sk.box_w, n = bw * Sk.box_h, PW = bw >> 1, PP = (bw >> 1) * (Sk.box_h >> 1);
+    const int x0 = fp_x0[s], y0 = fp_y0[s];
+    for (int e = tid; e < n; e += LPA_THREADS) {
+      const int lx = e % bw, ly = e / bw;
+      const int X = x0 + lx, Y = y0 + ly;
+      float f = 0.f, iv = 0.f;
+      if (X >= 0 && X < Sk.width && Y >= 0 && Y < Sk.height) {
+        const float y = (float)raw[e];
+        const long px = (long)Y * Sk.width + X;
+        const float b = Sk.bias ? Sk.bias[px] : Sk.black;
+        const float rv = Sk.rvar ? Sk.rvar[px] : Sk.read_var;
+        const float sat = Sk.satf ? (float)Sk.satf[px] : Sk.sat;
+        if (y < sat) {
+          const float a = Sk.prnu ? Sk.prnu[px] : 1.f;
+          const float e0 = y - b;
+          f = e0 * Sk.inv_gtn / a;
+          iv = (Sk.gtn2 * a * a) / fmaf(Sk.gain, fmaxf(e0, 0.f), rv);
+        }
+      }
+      planes[((lx & 1) + 2 * (ly & 1)) * PP + (ly >> 1) * PW + (lx >> 1)] = make_float2(f, iv);
+    }
+  }
+  __syncthreads();
+
+  // pixel of this thread: warp = parity class x half tile, lanes 8 x 4 at stride 2
+  const int warp = tid >> 5, lane = tid & 31;
+  const int par = warp & 3, hf = warp >> 2;
+  const int u = u0 + 2 * (lane & 7) + (par & 1);
+  const int v = v0 + 2 * ((lane >> 3) + 4 * hf) + (par >> 1);
+  const bool pix = (u < L.out_w) && (v < L.out_h);
+  const int ab = ((u - u0) >> 3) + 2 * ((v - v0) >> 3);
+  const int du = (u - u0) & 7, dv = (v - v0) & 7;
+  constexpr int P = n_unknowns(ORDER);
+  const int J = L.n_scales;
+  const int NL = J + ORDER;
+  const size_t plane_px = (size_t)L.out_w * L.out_h;
+  const size_t opix = (size_t)v * L.out_w + u;
+  const float log2e = 1.4426950408889634f;
+
+#pragma unroll 1
+  for (int c = 0; c < 3; c++) {
+    Ici ici;
+    ici.reset(pix);
+    Moments<ORDER, COMP> m;
+    const float gsc = (c == 1) ? L.green_ratio : 1.f;
+#pragma unroll 1
+    for (int j = 0; j < J; j++) {
+      if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
+      m.zero();
+      const float sg = L.sigma[j] * gsc;
+      const float R = L.trunc_k * sg, R2 = R * R;
+      const float cexp = -log2e / (2.f * sg * sg);
+      const bool act = DIAG ? pix : !ici.done;
+#pragma unroll 1
+      for (int s = 0; s < S; s++)
+        accumulate_sensor<ORDER, COMP>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, L.taper, fp_x0[s],
+                                       fp_y0[s], smem, act, L.status);
+      FitOut f = solve_with_fallback<P>(m, L.min_pivot, L.cond_fallback);
+      if (DIAG && pix) {
+        float *o = L.levels + (((size_t)c * NL + j) * plane_px + opix) * 2;
+        o[0] = f.valid ? f.c0 : __int_as_float(0x7fffffff);
+        o[1] = f.valid ? f.var : __int_as_float(0x7fffffff);
+      }
+      ici.step(f, j, L.ici_gamma);
+    }
+    // order fallback at the largest scale (the moments still hold it when any lane needs it)
+    const bool need = ici.choice == 255 && pix;
+    if (DIAG || __any_sync(LPA_FULL, need)) {
+      auto take = [&](const FitOut &f, int i) {
+        if (DIAG && pix) {
+          float *o = L.levels + (((size_t)c * NL + J + i) * plane_px + opix) * 2;
+          o[0] = f.valid ? f.c0 : __int_as_float(0x7fffffff);
+          o[1] = f.valid ? f.var : __int_as_float(0x7fffffff);
+        }
+        if (ici.choice == 255 && f.valid) {
+          ici.choice = J + i;
+          ici.val = f.c0;
+        }
+      };
+      if constexpr (ORDER >= 1) take(fallback_fit<ORDER, 0>(m, L.min_pivot, L.cond_fallback), 0);
+      if constexpr (ORDER >= 2) take(fallback_fit<ORDER, 1>(m, L.min_pivot, L.cond_fallback), 1);
+    }
+    if (pix) {
+      if (L.out_half)
+        reinterpret_cast<__half *>(L.out)[c * plane_px + opix] = __float2half_rn(ici.val);
+      else
+        reinterpret_cast<float *>(L.out)[c * plane_px + opix] = ici.val;
+      if (L.choice) L.choice[c * plane_px + opix] = (uint8_t)ici.choice;
+    }
+  }
+}
+
+}  // namespace lpa

@@ -1,0 +1,60 @@
+// Launch descriptor shared by the host code and the reconstruction kernels.
+// Internal to the CUDA library; not part of the C ABI.
+#pragma once
+#include <cuda.h>
+#include <stdint.h>
+
+#define LPA_MAX_SENSORS 8
+#define LPA_MAX_SCALES 8
+#define LPA_TILE 16         // output tile edge in pixels (one CTA per tile)
+#define LPA_THREADS 256     // one thread per output pixel of the tile
+#define LPA_ANCHOR 8        // edge of the output blocks whose sensor positions are anchored in FP64
+#define LPA_MARGIN 4        // staging margin in sensor px around every window box
+
+// Device status word bits (read and cleared by hdr_check).
+#define LPA_ERR_TIMEOUT 1u  // a bounded mbarrier wait ran out
+#define LPA_ERR_BOUNDS 2u   // a window row fell outside the staged footprint
+
+struct alignas(64) LpaSensorK {
+  CUtensorMap tmap;         // 2-D tiled map of the raw frame (uint16, dims width x height)
+  double G[6];              // output px -> sensor px: T_s^{-1} composed with the output mapping
+  float Gf[4];              // linear part of G in FP32 (steps between neighbouring output pixels)
+  float A[4];               // linear part of T_s (sensor px -> reference px), row-major
+  float hx_unit, hy_unit;   // sensor-space half extent of a reference disc of radius 1
+  float inv_gtn;            // 1 / (g t n)
+  float gtn2;               // (g t n)^2
+  float gain, read_var, black, sat;
+  int width, height;
+  int box_w, box_h;         // staged footprint in elements; box_w % 8 == 0, box_h even
+  float ext_x, ext_y;       // half extent of the window box in sensor px incl. margin (max scale)
+  uint32_t off_raw;         // byte offset of the raw box in dynamic shared memory
+  uint32_t off_planes;      // byte offset of the four colour-phase planes (float2 each)
+  const float *bias;        // optional per-pixel frames [height][width] (device)
+  const float *prnu;
+  const float *rvar;
+  const uint16_t *satf;
+};
+
+struct LpaLaunch {
+  LpaSensorK s[LPA_MAX_SENSORS];
+  int n_sensors;
+  int order;
+  int n_scales;
+  float sigma[LPA_MAX_SCALES];   // R/B scales in reference px
+  float green_ratio;
+  float trunc_k;
+  float ici_gamma;
+  float min_pivot;
+  float cond_fallback;           // <= 0: never
+  float taper;                   // exp(-k^2 / 2)
+  int out_w, out_h;
+  int tiles_x, tiles_y;
+  int out_half;                  // 0 float32, 1 float16
+  void *out;
+  uint8_t *choice;
+  float *levels;
+  unsigned int *status;
+  uint32_t tx_bytes;             // bytes landed by the bulk tensor copies of one tile
+  uint32_t off_anchor;           // byte offset of the anchor table
+  uint32_t smem_bytes;
+};

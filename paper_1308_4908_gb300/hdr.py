@@ -1,0 +1,248 @@
+"""Thin ctypes binding of the C ABI in include/hdr_lpa.h (argument marshalling only).
+
+Every entry point of the library is exposed under its C name; `Context` adds a
+small convenience layer that takes torch tensors (device memory and streams are
+torch's; all computation runs in the library's CUDA kernels). There is no CPU
+fallback: importing works without a GPU, but every call needs the compiled
+library and a CUDA device, and fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+HDR_MAX_SENSORS = 8
+HDR_MAX_SCALES = 8
+
+HDR_OK, HDR_E_INVALID, HDR_E_NOMEM, HDR_E_CUDA, HDR_E_BUSY, HDR_E_TIMEOUT, HDR_E_UNSUPPORTED, HDR_E_INTERNAL = range(8)
+STATUS_NAMES = {0: "HDR_OK", 1: "HDR_E_INVALID", 2: "HDR_E_NOMEM", 3: "HDR_E_CUDA", 4: "HDR_E_BUSY",
+                5: "HDR_E_TIMEOUT", 6: "HDR_E_UNSUPPORTED", 7: "HDR_E_INTERNAL"}
+
+
+class hdr_sensor_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("pitch_elems", ctypes.c_int32),
+                ("cfa", ctypes.c_int32), ("gain", ctypes.c_double), ("exposure", ctypes.c_double),
+                ("nd", ctypes.c_double), ("read_var", ctypes.c_double), ("black", ctypes.c_double),
+                ("sat", ctypes.c_double), ("affine", ctypes.c_double * 6),
+                ("bias_frame", ctypes.c_void_p), ("prnu_frame", ctypes.c_void_p),
+                ("read_var_frame", ctypes.c_void_p), ("sat_frame", ctypes.c_void_p)]
+
+
+class hdr_params(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("n_scales", ctypes.c_int32),
+                ("sigma", ctypes.c_double * HDR_MAX_SCALES), ("green_ratio", ctypes.c_double),
+                ("trunc_k", ctypes.c_double), ("ici_gamma", ctypes.c_double), ("min_pivot", ctypes.c_double),
+                ("cond_fallback", ctypes.c_double), ("out_w", ctypes.c_int32), ("out_h", ctypes.c_int32),
+                ("out_affine", ctypes.c_double * 6), ("out_dtype", ctypes.c_int32), ("accum", ctypes.c_int32)]
+
+
+class HdrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libhdrlpa.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: run paper_1308_4908_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    lib.hdr_params_default.argtypes = [_P]
+    lib.hdr_params_default.restype = None
+    lib.hdr_create.argtypes = [ctypes.c_int, _P]
+    lib.hdr_destroy.argtypes = [_P]
+    lib.hdr_destroy.restype = None
+    lib.hdr_set_rig.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P]
+    lib.hdr_reconstruct.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
+    lib.hdr_reconstruct_levels.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
+    lib.hdr_reconstruct_host.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
+    lib.hdr_check.argtypes = [_P, _P]
+    lib.hdr_last_error.argtypes = []
+    lib.hdr_last_error.restype = ctypes.c_char_p
+    for name in ("hdr_create", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_levels", "hdr_reconstruct_host",
+                 "hdr_check"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != HDR_OK:
+        raise HdrError(status, load().hdr_last_error().decode())
+
+
+# ------------------------------------------------------------------ C entry points (same names)
+
+def hdr_params_default() -> hdr_params:
+    p = hdr_params()
+    load().hdr_params_default(ctypes.byref(p))
+    return p
+
+
+def hdr_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().hdr_create(int(device), ctypes.byref(h)))
+    return h.value
+
+
+def hdr_destroy(ctx: int) -> None:
+    load().hdr_destroy(ctypes.c_void_p(ctx))
+
+
+def hdr_set_rig(ctx: int, rig_id: int, sensors: Sequence[hdr_sensor_desc]) -> None:
+    arr = (hdr_sensor_desc * len(sensors))(*sensors)
+    _check(load().hdr_set_rig(ctypes.c_void_p(ctx), int(rig_id), len(sensors), arr))
+
+
+def _ptr_array(ptrs: Sequence[int]):
+    return (ctypes.c_void_p * max(len(ptrs), 1))(*ptrs)
+
+
+def hdr_reconstruct(ctx: int, rig_id: int, params: hdr_params, raw_dev: Sequence[int], out_dev: int,
+                    choice_dev: Optional[int] = None, stream: Optional[int] = None) -> None:
+    _check(load().hdr_reconstruct(ctypes.c_void_p(ctx), int(rig_id), ctypes.byref(params), _ptr_array(raw_dev),
+                                  ctypes.c_void_p(out_dev), ctypes.c_void_p(choice_dev), ctypes.c_void_p(stream)))
+
+
+def hdr_reconstruct_levels(ctx: int, rig_id: int, params: hdr_params, raw_dev: Sequence[int], out_dev: int,
+                           choice_dev: Optional[int], levels_dev: int, stream: Optional[int] = None) -> None:
+    _check(load().hdr_reconstruct_levels(ctypes.c_void_p(ctx), int(rig_id), ctypes.byref(params),
+                                         _ptr_array(raw_dev), ctypes.c_void_p(out_dev), ctypes.c_void_p(choice_dev),
+                                         ctypes.c_void_p(levels_dev), ctypes.c_void_p(stream)))
+
+
+def hdr_reconstruct_host(ctx: int, rig_id: int, params: hdr_params, raw_host: Sequence[int], out_host: int,
+                         choice_host: Optional[int] = None, stream: Optional[int] = None) -> None:
+    _check(load().hdr_reconstruct_host(ctypes.c_void_p(ctx), int(rig_id), ctypes.byref(params),
+                                       _ptr_array(raw_host), ctypes.c_void_p(out_host), ctypes.c_void_p(choice_host),
+                                       ctypes.c_void_p(stream)))
+
+
+def hdr_check(ctx: int, stream: Optional[int] = None) -> None:
+    _check(load().hdr_check(ctypes.c_void_p(ctx), ctypes.c_void_p(stream)))
+
+
+def hdr_last_error() -> str:
+    return load().hdr_last_error().decode()
+
+
+# ------------------------------------------------------------------ marshalling helpers
+
+def sensor_desc(sensor, keep: list) -> hdr_sensor_desc:
+    """hdr_sensor_desc from a synth.Sensor-like object; `keep` holds arrays the struct points at."""
+    d = hdr_sensor_desc()
+    d.width, d.height = int(sensor.width), int(sensor.height)
+    d.pitch_elems = int(sensor.pitch)
+    d.cfa = 0
+    d.gain, d.exposure, d.nd = float(sensor.gain), float(sensor.exposure), float(sensor.nd)
+    d.read_var, d.black, d.sat = float(sensor.read_var), float(sensor.black), float(sensor.sat)
+    d.affine[:] = [float(x) for x in np.asarray(sensor.affine, dtype=np.float64).reshape(6)]
+    for name, field, dt in (("bias_frame", "bias_frame", np.float32), ("prnu_frame", "prnu_frame", np.float32),
+                            ("read_var_frame", "read_var_frame", np.float32), ("sat_frame", "sat_frame", np.uint16)):
+        fr = getattr(sensor, name, None)
+        if fr is not None:
+            a = np.ascontiguousarray(fr, dtype=dt)
+            keep.append(a)
+            setattr(d, field, a.ctypes.data)
+        else:
+            setattr(d, field, None)
+    return d
+
+
+def params_struct(p) -> hdr_params:
+    """hdr_params from a synth.Params-like object (defaults for fields it lacks)."""
+    h = hdr_params_default()
+    h.order = int(p.order)
+    h.n_scales = len(p.sigmas)
+    for j, s in enumerate(p.sigmas):
+        h.sigma[j] = float(s)
+    h.green_ratio = float(p.green_ratio)
+    h.trunc_k = float(p.trunc_k)
+    h.ici_gamma = float(p.ici_gamma)
+    h.min_pivot = float(p.min_pivot)
+    h.cond_fallback = float(getattr(p, "cond_fallback", h.cond_fallback))
+    h.out_w, h.out_h = int(p.out_w), int(p.out_h)
+    h.out_affine[:] = [float(x) for x in np.asarray(p.out_affine, dtype=np.float64).reshape(6)]
+    h.out_dtype = int(getattr(p, "out_dtype", 0))
+    h.accum = int(getattr(p, "accum", 0))
+    return h
+
+
+class Context:
+    """One library context on one CUDA device; rigs are uploaded once and stay resident."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1308_4908_gb300 needs a CUDA device (there is no CPU path)")
+        load()
+        self.device = int(device)
+        self.handle = hdr_create(self.device)
+
+    def close(self):
+        if self.handle:
+            hdr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_rig(self, rig_id: int, sensors) -> None:
+        keep: list = []
+        descs = [sensor_desc(s, keep) for s in sensors]
+        hdr_set_rig(self.handle, rig_id, descs)
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return s.cuda_stream
+
+    def reconstruct(self, rig_id: int, params, raws, out=None, choice=None, levels=None, stream=None):
+        """Reconstruct one frame from device tensors `raws` (uint16 [H, pitch] each); returns `out`."""
+        import torch
+        hp = params if isinstance(params, hdr_params) else params_struct(params)
+        if out is None:
+            dt = torch.float16 if hp.out_dtype == 1 else torch.float32
+            out = torch.empty((3, hp.out_h, hp.out_w), dtype=dt, device=f"cuda:{self.device}")
+        ptrs = [int(r.data_ptr()) for r in raws]
+        if levels is not None:
+            hdr_reconstruct_levels(self.handle, rig_id, hp, ptrs, out.data_ptr(),
+                                   choice.data_ptr() if choice is not None else None, levels.data_ptr(),
+                                   self._stream(stream))
+        else:
+            hdr_reconstruct(self.handle, rig_id, hp, ptrs, out.data_ptr(),
+                            choice.data_ptr() if choice is not None else None, self._stream(stream))
+        return out
+
+    def reconstruct_host(self, rig_id: int, params, raws_host: Sequence[np.ndarray], out_host: np.ndarray,
+                         choice_host: Optional[np.ndarray] = None, stream=None):
+        hp = params if isinstance(params, hdr_params) else params_struct(params)
+        hdr_reconstruct_host(self.handle, rig_id, hp, [int(r.ctypes.data) for r in raws_host], out_host.ctypes.data,
+                             choice_host.ctypes.data if choice_host is not None else None, self._stream(stream))
+        return out_host
+
+    def check(self, stream=None):
+        hdr_check(self.handle, self._stream(stream))

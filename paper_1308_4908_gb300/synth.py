@@ -200,6 +200,9 @@ class Params:
     out_h: int = 0
     out_affine: Optional[np.ndarray] = None   # output px -> reference px
     min_pivot: float = 1e-3
+    cond_fallback: float = 1e6
+    out_dtype: int = 0        # 0 float32, 1 float16
+    accum: int = 0            # 0 plain, 1 compensated
 
     def __post_init__(self):
         if self.out_affine is None:

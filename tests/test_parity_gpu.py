@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle on seeded inputs."""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1308_4908_gb300 import synth
+from tests import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1308_4908_gb300 import hdr
+    c = hdr.Context(0)
+    yield c
+    c.close()
+
+
+def upload(frame):
+    return [torch.from_numpy(s.raw).cuda() for s in frame.sensors]
+
+
+def run(ctx, frame, params=None, rig_id=0, levels=False):
+    p = params or frame.params
+    ctx.set_rig(rig_id, frame.sensors)
+    raws = upload(frame)
+    choice = torch.empty((3, p.out_h, p.out_w), dtype=torch.uint8, device="cuda")
+    lv = None
+    if levels:
+        NL = len(p.sigmas) + p.order
+        lv = torch.empty((3, NL, p.out_h, p.out_w, 2), dtype=torch.float32, device="cuda")
+    out = ctx.reconstruct(rig_id, p, raws, choice=choice, levels=lv)
+    ctx.check()
+    res = dict(out=out.float().cpu().numpy(), choice=choice.cpu().numpy())
+    if levels:
+        res["levels"] = lv.cpu().numpy()
+    return res
+
+
+def check_frame(ctx, frame, params=None, pixels=None, rel_tol=parity.REL_TOL, extra=0.0, levels=False):
+    """Run the frame on the GPU and compare with the oracle (tolerance in tests/parity.py)."""
+    p = params or frame.params
+    g = run(ctx, frame, p, levels=levels)
+    if pixels is None:
+        vv, uu = np.mgrid[0:p.out_h, 0:p.out_w]
+        pixels = np.stack([uu.ravel(), vv.ravel()], axis=1)
+    o = oracle.reconstruct(frame.sensors, p, pixels, levels=True, kappa=True)
+    gu = g["out"][:, pixels[:, 1], pixels[:, 0]]
+    gc = g["choice"][:, pixels[:, 1], pixels[:, 0]]
+    stats = parity.compare(gu, gc, o, pixels, len(p.sigmas), p.order, p.ici_gamma, p.min_pivot,
+                           rel_tol=rel_tol, extra_rel=extra)
+    return stats, g, o
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_tiny_full_frame(ctx):
+    """2 sensors of 64x64, order 0, one scale: every output pixel against the oracle."""
+    stats, _, _ = check_frame(ctx, synth.tiny())
+    assert stats["n"] > 3 * 64 * 64 * 0.9
+    assert stats["mismatched_choice"] == 0
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_paper_rig_small_all_orders(ctx, order):
+    """The paper-scale recipe (3 sensors, affine misalignment, 4 scales with ICI) on a 96x96
+    frame - six tiles per side with a ragged tail - for every order, all pixels."""
+    fr = synth.paper_scale(size=96)
+    p = dataclasses.replace(fr.params, order=order)
+    stats, _, _ = check_frame(ctx, fr, p)
+    assert stats["n"] > 0
+
+
+def test_paper_scale_full_size_sampled(ctx):
+    """Full 3 x 2048^2 frame, order 2, ICI over 4 scales, in the benchmark's launch
+    configuration; the oracle checks 3000 sampled pixels plus the frame border."""
+    fr = synth.paper_scale()
+    r = np.random.default_rng(0)
+    pix = r.integers(0, 2048, (2400, 2))
+    edge = np.concatenate([np.stack([np.arange(0, 2048, 17), np.zeros(121, int)], 1),
+                           np.stack([np.full(121, 2047), np.arange(0, 2048, 17)], 1),
+                           np.stack([np.arange(0, 2048, 17), np.full(121, 2047)], 1),
+                           np.stack([np.zeros(121, int), np.arange(0, 2048, 17)], 1)])
+    pix = np.concatenate([pix, edge, [[0, 0], [2047, 2047], [0, 2047], [2047, 0]]])
+    stats, g, _ = check_frame(ctx, fr, pixels=pix)
+    assert stats["n"] > 3 * 2400
+    assert np.isfinite(g["out"]).mean() > 0.999
+
+
+def test_levels_match_oracle(ctx):
+    """Every level (each scale at order M, then the lower orders at the largest scale):
+    C_0 and Var C_0 from the diagnostic entry point against the oracle's."""
+    fr = synth.paper_scale(size=64, seed=1010)
+    p = fr.params
+    g = run(ctx, fr, p, levels=True)
+    vv, uu = np.mgrid[0:64, 0:64]
+    pix = np.stack([uu.ravel(), vv.ravel()], axis=1)
+    o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True)
+    lv = g["levels"]  # [3, NL, H, W, 2]
+    NL = lv.shape[1]
+    n_cmp = 0
+    for c in range(3):
+        for l in range(NL):
+            gc0 = lv[c, l, pix[:, 1], pix[:, 0], 0]
+            gv = lv[c, l, pix[:, 1], pix[:, 0], 1]
+            ov, oc0, ovar, piv = o["valid"][:, c, l], o["c0"][:, c, l], o["var"][:, c, l], o["pivot"][:, c, l]
+            clear = np.abs(piv - p.min_pivot) > 0.02 * p.min_pivot + 1e-5
+            both = clear & (ov == 1)
+            assert np.all(np.isfinite(gc0[both])), (c, l)
+            assert np.all(np.isnan(gc0[clear & (ov == 0)])), (c, l)
+            tol = parity.level_tol(oc0[both], o["efit"][both, c, l], o["ew"][both, c, l])
+            err = np.abs(gc0[both] - oc0[both])
+            assert np.all(err <= tol), (c, l, float((err / tol).max()))
+            # Var C_0 is a quadratic form in the same fit: allow 10x the C_0 tolerance, relative
+            ev = np.abs(gv[both] - ovar[both]) / np.abs(ovar[both])
+            assert np.all(ev <= 10 * tol / np.maximum(np.abs(oc0[both]), parity.TAU) + 1e-4), (c, l, float(ev.max()))
+            n_cmp += both.sum()
+    assert n_cmp > 3 * 64 * 64 * 3
+
+
+# ------------------------------------------------------------------ rigs and mappings
+
+@pytest.mark.parametrize("case", ["aligned", "translated", "rotated6", "upsampled"])
+def test_rigs(ctx, case):
+    """Perfectly aligned sensors, the [0.4, 0.45] px middle-sensor offset, 6 degree rotations
+    (Section 7.2) and a 1.5x upsampled output (Section 4.2: arbitrary output resolution)."""
+    fr = synth.paper_scale(size=80, seed=1020)
+    W = 80
+    if case == "aligned":
+        affs = [synth.affine_about_center(W, W)] * 3
+    elif case == "translated":
+        affs = [synth.affine_about_center(W, W), synth.affine_about_center(W, W, 0.4, 0.45),
+                synth.affine_about_center(W, W)]
+    elif case == "rotated6":
+        affs = [synth.affine_about_center(W, W), synth.affine_about_center(W, W, 0.3, -0.2, 6.0),
+                synth.affine_about_center(W, W, -0.5, 0.1, -6.0)]
+    else:
+        affs = [s.affine for s in fr.sensors]
+    for s, a in zip(fr.sensors, affs):
+        s.affine = np.asarray(a)
+        s.raw = synth.simulate_raw(fr.scene, s, 1020, int(s.nd * 1000))
+    p = fr.params
+    if case == "upsampled":
+        p = dataclasses.replace(p, out_w=120, out_h=120, out_affine=synth.output_affine(W, W, 120, 120))
+    if case == "aligned":
+        p = dataclasses.replace(p, order=1)
+    check_frame(ctx, fr, p)
+
+
+def test_ragged_and_tiny_outputs(ctx):
+    """Output sizes that are not multiples of the tile, a 1x1 output, and an output that
+    extends past the sensors (NaN where no sample exists)."""
+    fr = synth.paper_scale(size=48, seed=1030)
+    for (w, h) in ((37, 23), (1, 1), (17, 16)):
+        check_frame(ctx, fr, dataclasses.replace(fr.params, out_w=w, out_h=h))
+    p = dataclasses.replace(fr.params, out_w=64, out_h=64,
+                            out_affine=np.array([[1.0, 0, -8.0], [0, 1.0, -8.0]]))
+    _, g, o = check_frame(ctx, fr, p)
+    assert np.isnan(g["out"][:, 0, 0]).all()
+
+
+def test_empty_output_is_a_noop(ctx):
+    fr = synth.tiny()
+    p = dataclasses.replace(fr.params, out_w=0, out_h=0)
+    ctx.set_rig(0, fr.sensors)
+    out = torch.empty((3, 0, 0), device="cuda")
+    ctx.reconstruct(0, p, upload(fr), out=out)
+    ctx.check()
+
+
+@pytest.mark.parametrize("n_scales", [1, 8])
+def test_scale_counts(ctx, n_scales):
+    fr = synth.paper_scale(size=40, seed=1040)
+    sig = (1.1,) if n_scales == 1 else tuple(0.4 + 0.25 * k for k in range(8))
+    check_frame(ctx, fr, dataclasses.replace(fr.params, sigmas=sig))
+
+
+def test_one_and_eight_sensors(ctx):
+    fr = synth.paper_scale(size=40, seed=1050)
+    one = synth.Frame(fr.sensors[:1], dataclasses.replace(fr.params, order=1), fr.scene)
+    check_frame(ctx, one)
+    r = np.random.default_rng(3)
+    sens = []
+    for k in range(8):
+        s = synth.Sensor(40, 40, 2.0 ** (-2 * k), synth.affine_about_center(40, 40, *r.uniform(-1, 1, 2),
+                                                                           r.uniform(-3, 3)))
+        s.raw = synth.simulate_raw(fr.scene, s, 1050, k)
+        sens.append(s)
+    check_frame(ctx, synth.Frame(sens, fr.params, fr.scene))
+
+
+def test_saturated_sensor_and_calibration_frames(ctx):
+    """A fully saturated sensor contributes nothing; per-pixel bias / non-uniformity /
+    read-noise / saturation frames (Sections 4.1, 6) follow the oracle."""
+    fr = synth.paper_scale(size=48, seed=1060)
+    fr.sensors[0].raw[:] = synth.CLIP_DN
+    check_frame(ctx, fr)
+    r = np.random.default_rng(4)
+    for s in fr.sensors:
+        s.bias_frame = (s.black + r.uniform(-2, 2, (48, 48))).astype(np.float32)
+        s.prnu_frame = r.uniform(0.95, 1.05, (48, 48)).astype(np.float32)
+        s.read_var_frame = r.uniform(6, 12, (48, 48)).astype(np.float32)
+        s.sat_frame = np.full((48, 48), 4000, np.uint16)
+    check_frame(ctx, fr)
+
+
+def test_sensor_order_independence_gpu(ctx):
+    """Permuting the sensors changes only the FP32 summation order: both orders meet the oracle,
+    and where they used the same level they differ by at most twice its tolerance."""
+    fr = synth.paper_scale(size=64, seed=1070)
+    sa, a, o = check_frame(ctx, fr)
+    fr2 = synth.Frame(fr.sensors[::-1], fr.params, fr.scene)
+    sb, b, _ = check_frame(ctx, fr2)
+    same = a["choice"] == b["choice"]
+    assert same.mean() > 0.99
+    vv, uu = np.mgrid[0:64, 0:64]
+    lvl = np.where(a["choice"] == 255, 0, a["choice"]).astype(int)          # [3, H, W]
+    ochoice = o["choice"].T.reshape(3, 64, 64) if o["choice"].ndim == 2 else o["choice"]
+    for c in range(3):
+        m = same[c] & (a["choice"][c] != 255)
+        idx = (vv[m] * 64 + uu[m])
+        l = lvl[c][m]
+        tol = parity.level_tol(o["c0"][idx, c, l], o["efit"][idx, c, l], o["ew"][idx, c, l])
+        assert np.all(np.abs(a["out"][c][m] - b["out"][c][m]) <= 2 * tol)
+
+
+# ------------------------------------------------------------------ precision variants and APIs
+
+@pytest.mark.parametrize("out_dtype,accum", [(0, 1), (1, 0), (1, 1)])
+def test_precision_variants(ctx, out_dtype, accum):
+    fr = synth.paper_scale(size=64, seed=1080)
+    p = dataclasses.replace(fr.params)
+    p.out_dtype = out_dtype
+    p.accum = accum
+    extra = parity.HALF_TOL if out_dtype == 1 else 0.0
+    check_frame(ctx, fr, p, extra=extra)
+
+
+def test_host_buffer_entry_point_matches(ctx):
+    fr = synth.paper_scale(size=64, seed=1090)
+    a = run(ctx, fr)
+    out = np.empty((3, 64, 64), np.float32)
+    ch = np.empty((3, 64, 64), np.uint8)
+    ctx.reconstruct_host(0, fr.params, [np.ascontiguousarray(s.raw) for s in fr.sensors], out, ch)
+    np.testing.assert_array_equal(out, a["out"])
+    np.testing.assert_array_equal(ch, a["choice"])
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    from paper_1308_4908_gb300 import hdr
+    fr = synth.tiny()
+    ctx.set_rig(0, fr.sensors)
+    raws = upload(fr)
+    for bad in (dict(order=3), dict(sigmas=(0.8, 0.5)), dict(sigmas=(-1.0,)), dict(trunc_k=0.0)):
+        p = dataclasses.replace(fr.params, **bad)
+        with pytest.raises(hdr.HdrError) as ei:
+            ctx.reconstruct(0, p, raws)
+        assert ei.value.status == hdr.HDR_E_INVALID
+    with pytest.raises(hdr.HdrError):
+        ctx.reconstruct(5, fr.params, raws)          # undefined rig
+    bad_sensor = dataclasses.replace(fr.sensors[0], pitch=63)
+    with pytest.raises(hdr.HdrError):
+        ctx.set_rig(2, [bad_sensor])
+    ctx.check()
