@@ -10,7 +10,7 @@
 #include <mutex>
 #include <string>
 
-#include "../../include/hdr_lpa.h"
+#include "hdr_lpa.h"
 #include "lpa_dispatch.h"
 #include "lpa_launch.h"
 
