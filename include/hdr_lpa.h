@@ -142,6 +142,30 @@ hdr_status hdr_check(hdr_ctx *ctx, void *cuda_stream);
 /* Message of the calling thread's last failed call ("" if none). */
 const char *hdr_last_error(void);
 
+/* Size of the fixed device array that hdr_reconstruct_noalloc uses as scratch. */
+#define HDR_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/* Reconstruct one frame without allocating anything, for callers that cannot allocate device
+ * memory: a real-time capture thread that must not enter the allocator, or a host program whose
+ * GPU memory is wholly reserved by another runtime's pool. The paper has no counterpart; this is
+ * a convenience of this library. No context is needed and nothing is allocated (no cudaMalloc,
+ * no cudaFree, no allocating library routine); the call is synchronous.
+ *   device      CUDA device to run on (made current by the call);
+ *   sensors     the rig, as for hdr_set_rig (per-pixel frames are HOST pointers, copied on each call);
+ *   params, raw_dev, out_dev, choice_dev, cuda_stream   as for hdr_reconstruct.
+ * Scratch: the kernel's status word and the rig's per-pixel calibration frames are placed in one
+ * fixed device array of HDR_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits. A call whose frames do not fit (256 bytes plus each frame rounded up to 256
+ * bytes) is rejected with HDR_E_UNSUPPORTED before any GPU work. The array keeps the last call's
+ * contents; each call clears the status word and rewrites the frames it uses. All calls share the
+ * one array per device, so calls that overlap on the GPU (other threads or other streams) race:
+ * serialise them. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and the tensor-map encoder; make that first call before any stream
+ * capture. Returns HDR_E_TIMEOUT / HDR_E_INTERNAL for device-side errors, like hdr_check. */
+hdr_status hdr_reconstruct_noalloc(int device, int32_t n_sensors, const hdr_sensor_desc *sensors,
+                                   const hdr_params *params, const uint16_t *const *raw_dev, void *out_dev,
+                                   uint8_t *choice_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,6 +112,36 @@ void compose_affine(const double a[6], const double b[6], double c[6]) {
   c[5] = a[3] * b[2] + a[4] * b[5] + a[5];
 }
 
+// Validate the descriptors of a rig of n_sensors sensors.
+hdr_status check_sensors(int32_t n_sensors, const hdr_sensor_desc *sensors) {
+  if (n_sensors < 1 || n_sensors > HDR_MAX_SENSORS)
+    return fail(HDR_E_INVALID, "n_sensors %d not in [1,%d]", n_sensors, HDR_MAX_SENSORS);
+  if (!sensors) return fail(HDR_E_INVALID, "sensors is NULL");
+  for (int s = 0; s < n_sensors; s++) {
+    const hdr_sensor_desc &d = sensors[s];
+    if (d.width < 1 || d.height < 1 || d.pitch_elems < d.width || (d.pitch_elems * 2) % 16)
+      return fail(HDR_E_INVALID, "sensor %d: bad size %dx%d / pitch %d (pitch*2 must be a multiple of 16)", s,
+                  d.width, d.height, d.pitch_elems);
+    if (d.width > (1 << 20) || d.height > (1 << 20)) return fail(HDR_E_UNSUPPORTED, "sensor %d too large", s);
+    if (d.cfa != 0) return fail(HDR_E_UNSUPPORTED, "sensor %d: only the RGGB layout (cfa 0) is implemented", s);
+    if (!(d.gain > 0) || !(d.exposure > 0) || !(d.nd > 0) || !std::isfinite(d.gain * d.exposure * d.nd))
+      return fail(HDR_E_INVALID, "sensor %d: gain, exposure and nd must be finite and > 0", s);
+    if (!d.read_var_frame && !(d.read_var > 0)) return fail(HDR_E_INVALID, "sensor %d: read_var must be > 0", s);
+    if (!std::isfinite(d.black) || !std::isfinite(d.sat)) return fail(HDR_E_INVALID, "sensor %d: black/sat not finite", s);
+    if (!finite6(d.affine)) return fail(HDR_E_INVALID, "sensor %d: affine not finite", s);
+    const double det = d.affine[0] * d.affine[4] - d.affine[1] * d.affine[3];
+    if (!(std::fabs(det) > 1e-12)) return fail(HDR_E_INVALID, "sensor %d: affine is singular", s);
+    const size_t npx = (size_t)d.width * d.height;
+    for (size_t i = 0; d.prnu_frame && i < npx; i++)
+      if (!(d.prnu_frame[i] > 0.f) || !std::isfinite(d.prnu_frame[i]))
+        return fail(HDR_E_INVALID, "sensor %d: prnu_frame must be finite and > 0", s);
+    for (size_t i = 0; d.read_var_frame && i < npx; i++)
+      if (!(d.read_var_frame[i] > 0.f) || !std::isfinite(d.read_var_frame[i]))
+        return fail(HDR_E_INVALID, "sensor %d: read_var_frame must be finite and > 0", s);
+  }
+  return HDR_OK;
+}
+
 hdr_status check_params(const hdr_params *p) {
   if (!p) return fail(HDR_E_INVALID, "params is NULL");
   if (p->order < 0 || p->order > 2) return fail(HDR_E_INVALID, "order %d not in {0,1,2}", p->order);
@@ -133,8 +163,17 @@ hdr_status check_params(const hdr_params *p) {
   return HDR_OK;
 }
 
+// What launch planning needs besides the rig: the tensor-map encoder, the device status word
+// the kernel reports to, and the device.
+struct PlanEnv {
+  EncodeTiledFn encode;
+  unsigned int *status;
+  int device;
+};
+
 // Fill the launch descriptor for one frame. raw: device pointers per sensor.
-hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L) {
+hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, const uint16_t *const *raw,
+                    LpaLaunch &L) {
   memset(&L, 0, sizeof(L));
   L.n_sensors = rig.n;
   L.order = p->order;
@@ -151,7 +190,7 @@ hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_
   L.tiles_x = (p->out_w + LPA_TILE - 1) / LPA_TILE;
   L.tiles_y = (p->out_h + LPA_TILE - 1) / LPA_TILE;
   L.out_half = p->out_dtype;
-  L.status = ctx->status;
+  L.status = env.status;
   const double rmax = p->trunc_k * p->sigma[p->n_scales - 1] * std::fmax(1.0, p->green_ratio);
   uint32_t off = 0, tx = 0;
   for (int s = 0; s < rig.n; s++) {
@@ -211,7 +250,7 @@ hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_
     cuuint64_t gstride[1] = {(cuuint64_t)d.pitch_elems * 2};
     cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
     cuuint32_t estr[2] = {1, 1};
-    CUresult cr = ctx->encode(&K.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t *>(raw[s]), gdim, gstride,
+    CUresult cr = env.encode(&K.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t *>(raw[s]), gdim, gstride,
                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled failed for sensor %d (code %d)", s, (int)cr);
@@ -219,10 +258,14 @@ hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_
   L.tx_bytes = tx;
   L.smem_bytes = off;
   int max_smem = 0;
-  CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, env.device));
   if ((int)off > max_smem - 1024)
     return fail(HDR_E_UNSUPPORTED, "staging needs %u bytes of shared memory (limit %d)", off, max_smem - 1024);
   return HDR_OK;
+}
+
+hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L) {
+  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device}, rig, p, raw, L);
 }
 
 hdr_status launch(const LpaLaunch &L, int accum, bool diag, cudaStream_t st) {
@@ -330,31 +373,8 @@ void hdr_destroy(hdr_ctx *ctx) {
 hdr_status hdr_set_rig(hdr_ctx *ctx, int32_t rig_id, int32_t n_sensors, const hdr_sensor_desc *sensors) {
   if (!ctx) return fail(HDR_E_INVALID, "ctx is NULL");
   if (rig_id < 0 || rig_id >= kMaxRigs) return fail(HDR_E_INVALID, "rig_id %d not in [0,%d)", rig_id, kMaxRigs);
-  if (n_sensors < 1 || n_sensors > HDR_MAX_SENSORS)
-    return fail(HDR_E_INVALID, "n_sensors %d not in [1,%d]", n_sensors, HDR_MAX_SENSORS);
-  if (!sensors) return fail(HDR_E_INVALID, "sensors is NULL");
-  for (int s = 0; s < n_sensors; s++) {
-    const hdr_sensor_desc &d = sensors[s];
-    if (d.width < 1 || d.height < 1 || d.pitch_elems < d.width || (d.pitch_elems * 2) % 16)
-      return fail(HDR_E_INVALID, "sensor %d: bad size %dx%d / pitch %d (pitch*2 must be a multiple of 16)", s,
-                  d.width, d.height, d.pitch_elems);
-    if (d.width > (1 << 20) || d.height > (1 << 20)) return fail(HDR_E_UNSUPPORTED, "sensor %d too large", s);
-    if (d.cfa != 0) return fail(HDR_E_UNSUPPORTED, "sensor %d: only the RGGB layout (cfa 0) is implemented", s);
-    if (!(d.gain > 0) || !(d.exposure > 0) || !(d.nd > 0) || !std::isfinite(d.gain * d.exposure * d.nd))
-      return fail(HDR_E_INVALID, "sensor %d: gain, exposure and nd must be finite and > 0", s);
-    if (!d.read_var_frame && !(d.read_var > 0)) return fail(HDR_E_INVALID, "sensor %d: read_var must be > 0", s);
-    if (!std::isfinite(d.black) || !std::isfinite(d.sat)) return fail(HDR_E_INVALID, "sensor %d: black/sat not finite", s);
-    if (!finite6(d.affine)) return fail(HDR_E_INVALID, "sensor %d: affine not finite", s);
-    const double det = d.affine[0] * d.affine[4] - d.affine[1] * d.affine[3];
-    if (!(std::fabs(det) > 1e-12)) return fail(HDR_E_INVALID, "sensor %d: affine is singular", s);
-    const size_t npx = (size_t)d.width * d.height;
-    for (size_t i = 0; d.prnu_frame && i < npx; i++)
-      if (!(d.prnu_frame[i] > 0.f) || !std::isfinite(d.prnu_frame[i]))
-        return fail(HDR_E_INVALID, "sensor %d: prnu_frame must be finite and > 0", s);
-    for (size_t i = 0; d.read_var_frame && i < npx; i++)
-      if (!(d.read_var_frame[i] > 0.f) || !std::isfinite(d.read_var_frame[i]))
-        return fail(HDR_E_INVALID, "sensor %d: read_var_frame must be finite and > 0", s);
-  }
+  hdr_status vst = check_sensors(n_sensors, sensors);
+  if (vst) return vst;
   CUDA_TRY(cudaSetDevice(ctx->device));
   Rig &rig = ctx->rigs[rig_id];
   if (rig.n) {
@@ -467,3 +487,119 @@ hdr_status hdr_check(hdr_ctx *ctx, void *cuda_stream) {
 const char *hdr_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ reconstruction without allocation
+//
+// Scratch of hdr_reconstruct_noalloc: the kernel's status word and any per-pixel calibration
+// frames live in this fixed array instead of in device memory allocated by a context. Every GPU
+// that loads the library holds it until the process exits. In host code its name only stands
+// in for the array; the device address comes from cudaGetSymbolAddress, looked up once per
+// device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HDR_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr size_t kScratchHeader = 256;  // bytes before the first frame; the status word is at 0
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_ptr[kMaxDevices] = {};
+EncodeTiledFn g_noalloc_encode = nullptr;
+
+// One-time set-up for `device` (which must be current): the scratch address and the encoder.
+hdr_status noalloc_setup(int device, unsigned char **scratch, EncodeTiledFn *encode) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_encode) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
+    g_noalloc_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  if (!g_noalloc_ptr[device]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(HDR_E_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[device] = static_cast<unsigned char *>(ptr);
+  }
+  *scratch = g_noalloc_ptr[device];
+  *encode = g_noalloc_encode;
+  return HDR_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" hdr_status hdr_reconstruct_noalloc(int device, int32_t n_sensors, const hdr_sensor_desc *sensors,
+                                              const hdr_params *params, const uint16_t *const *raw_dev,
+                                              void *out_dev, uint8_t *choice_dev, void *cuda_stream) {
+  hdr_status st = check_sensors(n_sensors, sensors);
+  if (st) return st;
+  st = check_params(params);
+  if (st) return st;
+  if (!raw_dev) return fail(HDR_E_INVALID, "raw pointer array is NULL");
+  if (!out_dev && (long long)params->out_w * params->out_h > 0) return fail(HDR_E_INVALID, "output pointer is NULL");
+  if (device < 0 || device >= kMaxDevices) return fail(HDR_E_INVALID, "device %d out of range", device);
+  // scratch layout: status word, then each sensor's per-pixel frames on 256-byte boundaries
+  size_t need = kScratchHeader;
+  for (int s = 0; s < n_sensors; s++) {
+    const size_t npx = (size_t)sensors[s].width * sensors[s].height;
+    if (sensors[s].bias_frame) need += align256(npx * 4);
+    if (sensors[s].prnu_frame) need += align256(npx * 4);
+    if (sensors[s].read_var_frame) need += align256(npx * 4);
+    if (sensors[s].sat_frame) need += align256(npx * 2);
+  }
+  if (need > (size_t)HDR_NOALLOC_SCRATCH_BYTES)
+    return fail(HDR_E_UNSUPPORTED,
+                "the per-pixel calibration frames need %zu bytes of scratch; this entry point holds at most %u "
+                "(use a context and hdr_set_rig for larger frames)",
+                need, (unsigned)HDR_NOALLOC_SCRATCH_BYTES);
+  int n_dev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&n_dev));
+  if (device >= n_dev) return fail(HDR_E_INVALID, "device %d not present (%d devices)", device, n_dev);
+  CUDA_TRY(cudaSetDevice(device));
+  unsigned char *scratch = nullptr;
+  EncodeTiledFn encode = nullptr;
+  st = noalloc_setup(device, &scratch, &encode);
+  if (st) return st;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  unsigned int *status = reinterpret_cast<unsigned int *>(scratch);
+  // the array keeps the previous call's contents: clear the status word, copy this call's frames
+  CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned int), stream));
+  Rig rig;
+  rig.n = n_sensors;
+  size_t off = kScratchHeader;
+  for (int s = 0; s < n_sensors; s++) {
+    RigSensor &rs = rig.s[s];
+    rs.d = sensors[s];
+    const size_t npx = (size_t)rs.d.width * rs.d.height;
+    auto place = [&](const void *src, size_t bytes, void **dst) -> cudaError_t {
+      if (!src) return cudaSuccess;
+      *dst = scratch + off;
+      off += align256(bytes);
+      return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, stream);
+    };
+    CUDA_TRY(place(rs.d.bias_frame, npx * 4, (void **)&rs.bias));
+    CUDA_TRY(place(rs.d.prnu_frame, npx * 4, (void **)&rs.prnu));
+    CUDA_TRY(place(rs.d.read_var_frame, npx * 4, (void **)&rs.rvar));
+    CUDA_TRY(place(rs.d.sat_frame, npx * 2, (void **)&rs.satf));
+  }
+  LpaLaunch L;
+  st = plan_env(PlanEnv{encode, status, device}, rig, params, raw_dev, L);
+  for (int s = 0; s < n_sensors; s++) rig.s[s] = RigSensor();  // the frames belong to the scratch array
+  rig.n = 0;
+  if (st) return st;
+  L.out = out_dev;
+  L.choice = choice_dev;
+  L.levels = nullptr;
+  st = launch(L, params->accum, false, stream);
+  if (st) return st;
+  unsigned int word = 0;
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  CUDA_TRY(cudaMemcpy(&word, status, sizeof(word), cudaMemcpyDeviceToHost));
+  if (word & LPA_ERR_TIMEOUT) return fail(HDR_E_TIMEOUT, "a bounded device wait ran out (status 0x%x)", word);
+  if (word & LPA_ERR_BOUNDS) return fail(HDR_E_INTERNAL, "a window left the staged footprint (status 0x%x)", word);
+  return HDR_OK;
+}

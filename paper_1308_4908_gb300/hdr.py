@@ -76,10 +76,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.hdr_reconstruct_levels.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
     lib.hdr_reconstruct_host.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
     lib.hdr_check.argtypes = [_P, _P]
+    lib.hdr_reconstruct_noalloc.argtypes = [ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
     lib.hdr_last_error.argtypes = []
     lib.hdr_last_error.restype = ctypes.c_char_p
     for name in ("hdr_create", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_levels", "hdr_reconstruct_host",
-                 "hdr_check"):
+                 "hdr_check", "hdr_reconstruct_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -143,6 +144,20 @@ def hdr_check(ctx: int, stream: Optional[int] = None) -> None:
 
 def hdr_last_error() -> str:
     return load().hdr_last_error().decode()
+
+
+HDR_NOALLOC_SCRATCH_BYTES = 4 << 20
+
+
+def hdr_reconstruct_noalloc(device: int, sensors: Sequence[hdr_sensor_desc], params: hdr_params,
+                            raw_dev: Sequence[int], out_dev: int, choice_dev: Optional[int] = None,
+                            stream: Optional[int] = None) -> None:
+    """Synchronous reconstruction that allocates nothing (scratch in a fixed device array); for callers
+    that may not allocate device memory. Concurrent calls on one device race on that array."""
+    arr = (hdr_sensor_desc * len(sensors))(*sensors)
+    _check(load().hdr_reconstruct_noalloc(int(device), len(sensors), arr, ctypes.byref(params), _ptr_array(raw_dev),
+                                          ctypes.c_void_p(out_dev), ctypes.c_void_p(choice_dev),
+                                          ctypes.c_void_p(stream)))
 
 
 # ------------------------------------------------------------------ marshalling helpers
