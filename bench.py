@@ -80,48 +80,65 @@ def algorithmic_flops(params, sensors, choice: np.ndarray) -> float:
 
 
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi sampling (every 50 ms) of SM clock, power and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, device_index: int):
         self.dev = device_index
-        self.samples = []
-        self._stop = threading.Event()
-        self._t = None
-
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
-                if out.returncode == 0 and out.stdout.strip():
-                    self.samples.append([x.strip() for x in out.stdout.strip().split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        self.proc = None
+        self.lines = []
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)   # let the first samples arrive before the region starts
+        except Exception:
+            self.proc = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        if self._t:
-            self._t.join(timeout=10)
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l.split(",") for l in out.strip().splitlines() if l.count(",") >= 6]
 
     def summary(self):
-        if not self.samples:
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        if not self.lines:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 4 + i and s[4 + i] == "Active"})
+        sm = [v for v in (num(l[0]) for l in self.lines) if v is not None]
+        mx = [v for v in (num(l[1]) for l in self.lines) if v is not None]
+        pw = [v for v in (num(l[2]) for l in self.lines) if v is not None]
+        reasons = sorted({self.NAMES[i] for l in self.lines for i in range(4) if l[3 + i].strip() == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples),
-                "power_w_max": max(float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit())
-                if any(s[2].replace(".", "").isdigit() for s in self.samples) else None}
+                "reasons": reasons, "samples": len(self.lines), "power_w_max": max(pw) if pw else None}
+
+
+def recorded_traffic(px: int):
+    """DRAM bytes per launch from the committed ncu record, if it was taken on this kernel source."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        src = open(os.path.join(ROOT, "paper_1308_4908_gb300", "csrc", "lpa_kernel.cuh"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["kernel_source_sha256"]:
+            return None
+        return round(rec["dram_bytes_per_output_pixel"] * px)
+    except Exception:
+        return None
 
 
 def dist_setup(args):
@@ -210,7 +227,7 @@ def run_ours(args, world, rank, local, pg):
     from paper_1308_4908_gb300 import hdr, synth
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
-    frame = synth.paper_scale()
+    frame = synth.paper_scale(size=args.size)
     p = frame.params
     ctx = hdr.Context(local)
     ctx.set_rig(0, frame.sensors)
@@ -259,21 +276,23 @@ def run_ours(args, world, rank, local, pg):
     value = px * world / (ms_max * 1e-3) / 1e6
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
-    raw_host = [torch.from_numpy(s.raw).pin_memory() for s in frame.sensors]
-    out_host = torch.empty((3, p.out_h, p.out_w), dtype=torch.float32).pin_memory()
-    raw_np = [r.numpy() for r in raw_host]
-    out_np = out_host.numpy()
-    e2e_steps = max(3, min(args.steps, 10))
-    ctx.reconstruct_host(0, hp, raw_np, out_np, stream=stream)   # grow staging once
-    barrier(pg, local)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.reconstruct_host(0, hp, raw_np, out_np, stream=stream)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_s = max_over_ranks(pg, e2e_s, local)
-    h2d = sum(int(r.numel()) * 2 for r in raw_host)
-    d2h = int(out_host.numel()) * 4
-    ctx.check(stream)
+    raw_host = [torch.from_numpy(s.raw).pin_memory() for s in frame.sensors] if not args.no_e2e else []
+    e2e_s, h2d, d2h = None, 0, 0
+    if not args.no_e2e:
+        out_host = torch.empty((3, p.out_h, p.out_w), dtype=torch.float32).pin_memory()
+        raw_np = [r.numpy() for r in raw_host]
+        out_np = out_host.numpy()
+        e2e_steps = max(3, min(args.steps, 10))
+        ctx.reconstruct_host(0, hp, raw_np, out_np, stream=stream)   # grow staging once
+        barrier(pg, local)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.reconstruct_host(0, hp, raw_np, out_np, stream=stream)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_s = max_over_ranks(pg, e2e_s, local)
+        h2d = sum(int(r.numel()) * 2 for r in raw_host)
+        d2h = int(out_host.numel()) * 4
+        ctx.check(stream)
 
     if rank == 0:
         pk = peaks()
@@ -286,17 +305,21 @@ def run_ours(args, world, rank, local, pg):
             "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": 1, "output_px": px,
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "frac": round(achieved / peak, 4), "traffic": recorded_traffic(px),
+                         "traffic_unit": "bytes per launch (ncu dram read+write, scaled from the profiled case)",
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz of MEASURED_PEAKS.json",
                          "algorithmic_gflop_per_launch": round(flops / 1e9, 3)},
-            "e2e": {"value": round(px * world / e2e_s / 1e6, 2), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3, 3),
-                    "api": "hdr_reconstruct_host (pinned host buffers, copies and kernel on one stream)"},
+            "e2e": ({"value": round(px * world / e2e_s / 1e6, 2), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
+                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3, 3),
+                     "api": "hdr_reconstruct_host (pinned host buffers, copies and kernel on one stream)"}
+                    if e2e_s else None),
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "kernel_ms": {"mean": round(ms, 4), "min": round(min(kern_ms), 4), "max": round(max(kern_ms), 4)},
             "wall_s_timed_region": round(t_wall, 4),
         }
+        if args.size != 2048:
+            line["config"]["workload"] = WORKLOAD.replace("2048x2048", f"{args.size}x{args.size}")
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(frame)
         print(json.dumps(line), flush=True)
@@ -306,10 +329,12 @@ def run_ours(args, world, rank, local, pg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--size", type=int, default=2048, help="raw and output edge (2048 = the paper-scale workload)")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup(args)
     try:
