@@ -386,7 +386,9 @@ __device__ __forceinline__ void accumulate_sensor(Moments<ORDER, COMP> &m, const
       const float dxr = fmaf(a00, Dx0, a01 * Dy), dyr = fmaf(a10, Dx0, a11 * Dy);
       const float2 *rowp = pl + pr * PW + pc0;
       float qf = 0.f;
-#pragma unroll 2
+      // two samples in flight pay off only for the long order-2 bodies
+      constexpr int kUnroll = ORDER == 2 ? 2 : 1;
+#pragma unroll kUnroll
       for (int q = 0; q < NI; q++, qf += 1.f) {
         const float dx = fmaf(qf, sx, dxr), dy = fmaf(qf, sy, dyr);
         const float r2 = fmaf(dx, dx, dy * dy);
@@ -467,24 +469,43 @@ __global__ void __launch_bounds__(LPA_THREADS, 2) lpa_reconstruct(const __grid_c
     float2 *planes = reinterpret_cast<float2 *>(smem + Sk.off_planes);
     const int bw = Sk.box_w, n = bw * Sk.box_h, PW = bw >> 1, PP = (bw >> 1) * (Sk.box_h >> 1);
     const int x0 = fp_x0[s], y0 = fp_y0[s];
+    const bool scalar = !Sk.bias && !Sk.rvar && !Sk.satf && !Sk.prnu;
+    const float inv_gtn = Sk.inv_gtn, gtn2 = Sk.gtn2, gain = Sk.gain, rv0 = Sk.read_var, b0 = Sk.black;
+    const float sat0 = Sk.sat;
+    const int W = Sk.width, H = Sk.height;
+    const int step_y = LPA_THREADS / bw, step_x = LPA_THREADS - step_y * bw;
+    int lx = tid % bw, ly = tid / bw;
     for (int e = tid; e < n; e += LPA_THREADS) {
-      const int lx = e % bw, ly = e / bw;
       const int X = x0 + lx, Y = y0 + ly;
       float f = 0.f, iv = 0.f;
-      if (X >= 0 && X < Sk.width && Y >= 0 && Y < Sk.height) {
+      if (X >= 0 && X < W && Y >= 0 && Y < H) {
         const float y = (float)raw[e];
-        const long px = (long)Y * Sk.width + X;
-        const float b = Sk.bias ? Sk.bias[px] : Sk.black;
-        const float rv = Sk.rvar ? Sk.rvar[px] : Sk.read_var;
-        const float sat = Sk.satf ? (float)Sk.satf[px] : Sk.sat;
-        if (y < sat) {
-          const float a = Sk.prnu ? Sk.prnu[px] : 1.f;
-          const float e0 = y - b;
-          f = e0 * Sk.inv_gtn / a;
-          iv = (Sk.gtn2 * a * a) / fmaf(Sk.gain, fmaxf(e0, 0.f), rv);
+        if (scalar) {
+          if (y < sat0) {
+            const float e0 = y - b0;
+            f = e0 * inv_gtn;
+            iv = __fdividef(gtn2, fmaf(gain, fmaxf(e0, 0.f), rv0));
+          }
+        } else {
+          const long px = (long)Y * W + X;
+          const float b = Sk.bias ? Sk.bias[px] : b0;
+          const float rv = Sk.rvar ? Sk.rvar[px] : rv0;
+          const float sat = Sk.satf ? (float)Sk.satf[px] : sat0;
+          if (y < sat) {
+            const float a = Sk.prnu ? Sk.prnu[px] : 1.f;
+            const float e0 = y - b;
+            f = __fdividef(e0 * inv_gtn, a);
+            iv = __fdividef(gtn2 * a * a, fmaf(gain, fmaxf(e0, 0.f), rv));
+          }
         }
       }
       planes[((lx & 1) + 2 * (ly & 1)) * PP + (ly >> 1) * PW + (lx >> 1)] = make_float2(f, iv);
+      lx += step_x;
+      ly += step_y;
+      if (lx >= bw) {
+        lx -= bw;
+        ly += 1;
+      }
     }
   }
   __syncthreads();
