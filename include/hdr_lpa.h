@@ -134,6 +134,41 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
                                 const uint16_t *const *raw_host, void *out_host, uint8_t *choice_host,
                                 void *cuda_stream);
 
+/* One frame of a batch: rig, parameters and caller-owned device buffers, as for
+ * hdr_reconstruct (raw_dev[s] for s < the rig's sensor count). */
+typedef struct {
+  int32_t rig_id;
+  const hdr_params *params;
+  const uint16_t *raw_dev[HDR_MAX_SENSORS];
+  void *out_dev;
+  uint8_t *choice_dev;          /* optional level map, NULL = not written */
+} hdr_frame;
+
+/* Launch configuration of the batched kernel. */
+typedef struct {
+  int32_t tile_h;               /* output rows per tile: 8 (128-thread CTAs) or 16 (256 threads) */
+  int32_t ctas_per_sm;          /* persistent CTAs per SM; 0 = as many as fit                    */
+  int32_t cost_order;           /* 1 = tiles of the most expensive frames first, 0 = given order  */
+} hdr_batch_config;
+
+/* Reconstruct n_frames (1..4096) frames of any sizes, rigs, orders and scales in ONE persistent
+ * kernel launch on `cuda_stream` (A8 of the workload: batching). The launch is recorded once in a
+ * CUDA graph per launch shape (configuration, grid, shared-memory size, table capacity) and
+ * replayed: the graph copies the frame and tile tables from pinned staging owned by the context,
+ * clears the tile counter and runs the kernel. `cfg` NULL = the configuration hdr_tune_batch found
+ * for batches of this kind, else the default {16, 0, 1}. All frames must use the same `accum`.
+ * Asynchronous like hdr_reconstruct; the context must not start another batch before the previous
+ * one has finished reading its tables (the call waits for that). Results are identical to
+ * reconstructing each frame with hdr_reconstruct. */
+hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames,
+                                 const hdr_batch_config *cfg, void *cuda_stream);
+
+/* Autotuner: times every candidate configuration (tile height 8/16 x 1/2/max CTAs per SM x frame
+ * order) on this batch, keeps the fastest for batches of the same kind (orders present, largest
+ * sensor count, scale count, output-size bucket) and writes it to *best. Synchronous. */
+hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, hdr_batch_config *best,
+                          void *cuda_stream);
+
 /* Wait for `cuda_stream`, then read and clear the context's device status word.
  * Returns HDR_E_TIMEOUT or HDR_E_INTERNAL if a kernel recorded one, HDR_E_CUDA on a
  * CUDA error, else HDR_OK. */

@@ -6,9 +6,13 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "hdr_lpa.h"
 #include "lpa_dispatch.h"
@@ -58,9 +62,32 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 }  // namespace
 
+// Device tables and recorded graphs of the batched launch.
+struct BatchState {
+  size_t cap_frames = 0, cap_tiles = 0;
+  LpaLaunch *frames_dev = nullptr, *frames_host = nullptr;   // host side is pinned staging
+  int2 *tiles_dev = nullptr, *tiles_host = nullptr;
+  int *ntiles_dev = nullptr, *ntiles_host = nullptr;
+  unsigned int *counter_dev = nullptr;
+  cudaEvent_t tables_read = nullptr;                          // the last graph finished reading staging
+  bool pending = false;
+  struct Key {
+    int comp, tile_h, grid;
+    uint32_t smem;
+    size_t cap_frames, cap_tiles;
+    bool operator<(const Key &o) const {
+      return std::tie(comp, tile_h, grid, smem, cap_frames, cap_tiles) <
+             std::tie(o.comp, o.tile_h, o.grid, o.smem, o.cap_frames, o.cap_tiles);
+    }
+  };
+  std::map<Key, cudaGraphExec_t> graphs;
+  std::map<uint64_t, hdr_batch_config> tuned;
+};
+
 struct hdr_ctx {
   int device = 0;
   unsigned int *status = nullptr;
+  BatchState batch;
   Rig rigs[kMaxRigs];
   EncodeTiledFn encode = nullptr;
   // staging for the host-buffer entry point
@@ -173,7 +200,7 @@ struct PlanEnv {
 
 // Fill the launch descriptor for one frame. raw: device pointers per sensor.
 hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, const uint16_t *const *raw,
-                    LpaLaunch &L) {
+                    LpaLaunch &L, int tile_h = 16) {
   memset(&L, 0, sizeof(L));
   L.n_sensors = rig.n;
   L.order = p->order;
@@ -187,8 +214,9 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
   L.taper = (float)std::exp(-0.5 * p->trunc_k * p->trunc_k);
   L.out_w = p->out_w;
   L.out_h = p->out_h;
+  L.tile_h = tile_h;
   L.tiles_x = (p->out_w + LPA_TILE - 1) / LPA_TILE;
-  L.tiles_y = (p->out_h + LPA_TILE - 1) / LPA_TILE;
+  L.tiles_y = (p->out_h + tile_h - 1) / tile_h;
   L.out_half = p->out_dtype;
   L.status = env.status;
   const double rmax = p->trunc_k * p->sigma[p->n_scales - 1] * std::fmax(1.0, p->green_ratio);
@@ -228,8 +256,8 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
     // the alignment of the origin (x to 8 elements = 16 bytes, y to 2)
     K.ext_x = (float)(rmax * hxu + LPA_MARGIN);
     K.ext_y = (float)(rmax * hyu + LPA_MARGIN);
-    const double span_x = (std::fabs(K.G[0]) + std::fabs(K.G[1])) * (LPA_TILE - 1);
-    const double span_y = (std::fabs(K.G[3]) + std::fabs(K.G[4])) * (LPA_TILE - 1);
+    const double span_x = std::fabs(K.G[0]) * (LPA_TILE - 1) + std::fabs(K.G[1]) * (tile_h - 1);
+    const double span_y = std::fabs(K.G[3]) * (LPA_TILE - 1) + std::fabs(K.G[4]) * (tile_h - 1);
     int bw = (int)std::ceil(span_x + 2.0 * K.ext_x) + 9;
     int bh = (int)std::ceil(span_y + 2.0 * K.ext_y) + 3;
     bw = (bw + 7) / 8 * 8;
@@ -367,6 +395,15 @@ void hdr_destroy(hdr_ctx *ctx) {
   cudaFree(ctx->out_stage);
   cudaFree(ctx->choice_stage);
   cudaFree(ctx->status);
+  for (auto &g : ctx->batch.graphs) cudaGraphExecDestroy(g.second);
+  cudaFree(ctx->batch.frames_dev);
+  cudaFreeHost(ctx->batch.frames_host);
+  cudaFree(ctx->batch.tiles_dev);
+  cudaFreeHost(ctx->batch.tiles_host);
+  cudaFree(ctx->batch.ntiles_dev);
+  cudaFreeHost(ctx->batch.ntiles_host);
+  cudaFree(ctx->batch.counter_dev);
+  if (ctx->batch.tables_read) cudaEventDestroy(ctx->batch.tables_read);
   delete ctx;
 }
 
@@ -487,6 +524,235 @@ hdr_status hdr_check(hdr_ctx *ctx, void *cuda_stream) {
 const char *hdr_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batched launch
+
+namespace {
+
+// Relative cost of a frame's tile (for the most-expensive-first order): order weight x sensors
+// x summed squared scales (the expected samples per window).
+double frame_cost(const hdr_params &p, int n_sensors) {
+  static const double order_w[3] = {11.0, 41.0, 92.0};
+  double s2 = 0.0;
+  for (int j = 0; j < p.n_scales; j++) s2 += p.sigma[j] * p.sigma[j];
+  return order_w[p.order] * n_sensors * s2;
+}
+
+uint64_t batch_kind(const hdr_ctx *ctx, int n, const hdr_frame *frames) {
+  uint64_t orders = 0, max_s = 0, scales = 0, px = 0;
+  for (int f = 0; f < n; f++) {
+    const hdr_params *p = frames[f].params;
+    orders |= 1ull << p->order;
+    max_s = std::max<uint64_t>(max_s, ctx->rigs[frames[f].rig_id].n);
+    scales = std::max<uint64_t>(scales, p->n_scales);
+    px += (uint64_t)p->out_w * p->out_h;
+  }
+  uint64_t bucket = 0;
+  while ((1ull << (bucket + 1)) <= px / 65536 + 1) bucket++;
+  return orders | (max_s << 4) | (scales << 8) | (bucket << 12) | ((uint64_t)frames[0].params->accum << 20);
+}
+
+hdr_status check_batch(hdr_ctx *ctx, int32_t n, const hdr_frame *frames) {
+  if (!ctx) return fail(HDR_E_INVALID, "ctx is NULL");
+  if (n < 1 || n > 4096) return fail(HDR_E_INVALID, "n_frames %d not in [1, 4096]", n);
+  if (!frames) return fail(HDR_E_INVALID, "frames is NULL");
+  for (int f = 0; f < n; f++) {
+    const hdr_frame &F = frames[f];
+    if (F.rig_id < 0 || F.rig_id >= kMaxRigs || ctx->rigs[F.rig_id].n == 0)
+      return fail(HDR_E_INVALID, "frame %d: rig %d is not defined", f, F.rig_id);
+    hdr_status st = check_params(F.params);
+    if (st) return st;
+    if (F.params->accum != frames[0].params->accum)
+      return fail(HDR_E_INVALID, "frame %d: all frames of a batch must use the same accum", f);
+    if (!F.out_dev && (long long)F.params->out_w * F.params->out_h > 0)
+      return fail(HDR_E_INVALID, "frame %d: output pointer is NULL", f);
+  }
+  return HDR_OK;
+}
+
+// Grow the device tables and pinned staging of the batched launch.
+hdr_status batch_reserve(hdr_ctx *ctx, size_t n_frames, size_t n_tiles) {
+  BatchState &B = ctx->batch;
+  if (!B.tables_read) CUDA_TRY(cudaEventCreateWithFlags(&B.tables_read, cudaEventDisableTiming));
+  if (!B.counter_dev) {
+    CUDA_TRY(cudaMalloc(&B.counter_dev, sizeof(unsigned int)));
+    CUDA_TRY(cudaMalloc(&B.ntiles_dev, sizeof(int)));
+    CUDA_TRY(cudaMallocHost(&B.ntiles_host, sizeof(int)));
+  }
+  if (n_frames > B.cap_frames) {
+    size_t cap = std::max<size_t>(n_frames, 2 * B.cap_frames);
+    cudaFree(B.frames_dev);
+    cudaFreeHost(B.frames_host);
+    B.frames_dev = nullptr;
+    B.frames_host = nullptr;
+    B.cap_frames = 0;
+    CUDA_TRY(cudaMalloc(&B.frames_dev, cap * sizeof(LpaLaunch)));
+    CUDA_TRY(cudaMallocHost(&B.frames_host, cap * sizeof(LpaLaunch)));
+    B.cap_frames = cap;
+  }
+  if (n_tiles > B.cap_tiles) {
+    size_t cap = std::max<size_t>(n_tiles, 2 * B.cap_tiles);
+    cudaFree(B.tiles_dev);
+    cudaFreeHost(B.tiles_host);
+    B.tiles_dev = nullptr;
+    B.tiles_host = nullptr;
+    B.cap_tiles = 0;
+    CUDA_TRY(cudaMalloc(&B.tiles_dev, cap * sizeof(int2)));
+    CUDA_TRY(cudaMallocHost(&B.tiles_host, cap * sizeof(int2)));
+    B.cap_tiles = cap;
+  }
+  return HDR_OK;
+}
+
+// Plan every frame into the pinned staging and write the tile list. Returns the shared memory
+// the launch needs.
+hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const hdr_batch_config &cfg, uint32_t *smem,
+                      int *n_tiles_out) {
+  BatchState &B = ctx->batch;
+  std::vector<LpaLaunch> plans(n);
+  size_t total = 0;
+  uint32_t sm = 0;
+  for (int f = 0; f < n; f++) {
+    const hdr_frame &F = frames[f];
+    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
+                             plans[f], cfg.tile_h);
+    if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
+    plans[f].out = F.out_dev;
+    plans[f].choice = F.choice_dev;
+    plans[f].levels = nullptr;
+    total += (size_t)plans[f].tiles_x * plans[f].tiles_y;
+    sm = std::max(sm, plans[f].smem_bytes);
+  }
+  if (total > (size_t)INT32_MAX) return fail(HDR_E_UNSUPPORTED, "too many tiles in one batch");
+  hdr_status st = batch_reserve(ctx, n, std::max<size_t>(total, 1));
+  if (st) return st;
+  if (B.pending) {  // the previous graph may still be reading the staging
+    CUDA_TRY(cudaEventSynchronize(B.tables_read));
+    B.pending = false;
+  }
+  std::vector<int> order(n);
+  for (int f = 0; f < n; f++) order[f] = f;
+  if (cfg.cost_order) {
+    std::vector<double> cost(n);
+    for (int f = 0; f < n; f++) cost[f] = frame_cost(*frames[f].params, ctx->rigs[frames[f].rig_id].n);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  }
+  size_t t = 0;
+  for (int k = 0; k < n; k++) {
+    const int f = order[k];
+    B.frames_host[f] = plans[f];
+    const int nt = plans[f].tiles_x * plans[f].tiles_y;
+    for (int i = 0; i < nt; i++) B.tiles_host[t++] = make_int2(f, i);
+  }
+  *B.ntiles_host = (int)total;
+  *smem = sm;
+  *n_tiles_out = (int)total;
+  return HDR_OK;
+}
+
+}  // namespace
+
+extern "C" hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames,
+                                            const hdr_batch_config *cfg_in, void *cuda_stream) {
+  hdr_status st = check_batch(ctx, n_frames, frames);
+  if (st) return st;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  hdr_batch_config cfg = {16, 0, 1};
+  if (cfg_in) {
+    cfg = *cfg_in;
+  } else {
+    auto it = ctx->batch.tuned.find(batch_kind(ctx, n_frames, frames));
+    if (it != ctx->batch.tuned.end()) cfg = it->second;
+  }
+  if (cfg.tile_h != 8 && cfg.tile_h != 16) return fail(HDR_E_INVALID, "tile_h must be 8 or 16");
+  if (cfg.ctas_per_sm < 0 || cfg.ctas_per_sm > 8) return fail(HDR_E_INVALID, "ctas_per_sm must be in [0, 8]");
+  uint32_t smem = 0;
+  int n_tiles = 0;
+  st = batch_plan(ctx, n_frames, frames, cfg, &smem, &n_tiles);
+  if (st) return st;
+  BatchState &B = ctx->batch;
+  const bool comp = frames[0].params->accum != 0;
+  int fit = lpa_batch_ctas_per_sm(comp, cfg.tile_h, smem);
+  if (fit < 1) return fail(HDR_E_UNSUPPORTED, "the batched kernel does not fit an SM with %u bytes of shared memory", smem);
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, fit) : fit;
+  const int grid = std::max(1, std::min(sms * per_sm, std::max(n_tiles, 1)));
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  BatchState::Key key{comp ? 1 : 0, cfg.tile_h, grid, smem, B.cap_frames, B.cap_tiles};
+  auto it = B.graphs.find(key);
+  if (it == B.graphs.end()) {
+    // record: tables from pinned staging, counter to zero, one persistent kernel
+    cudaStream_t cap;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(B.frames_dev, B.frames_host, B.cap_frames * sizeof(LpaLaunch), cudaMemcpyHostToDevice, cap);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(B.tiles_dev, B.tiles_host, B.cap_tiles * sizeof(int2), cudaMemcpyHostToDevice, cap);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.ntiles_dev, B.ntiles_host, sizeof(int), cudaMemcpyHostToDevice, cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.counter_dev, 0, sizeof(unsigned int), cap);
+    if (e == cudaSuccess) {
+      LpaBatch lb{B.frames_dev, B.tiles_dev, B.ntiles_dev, B.counter_dev, smem};
+      e = lpa_launch_batch(lb, comp, cfg.tile_h, grid, cap);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = e2;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return fail(HDR_E_CUDA, "recording the batch graph failed: %s", cudaGetErrorString(e));
+    it = B.graphs.emplace(key, exec).first;
+  }
+  CUDA_TRY(cudaGraphLaunch(it->second, stream));
+  CUDA_TRY(cudaEventRecord(B.tables_read, stream));
+  B.pending = true;
+  return HDR_OK;
+}
+
+extern "C" hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, hdr_batch_config *best,
+                                     void *cuda_stream) {
+  hdr_status st = check_batch(ctx, n_frames, frames);
+  if (st) return st;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  hdr_batch_config win = {16, 0, 1};
+  float win_ms = 1e30f;
+  const hdr_batch_config cands[] = {{16, 0, 1}, {16, 1, 1}, {16, 2, 1}, {8, 0, 1}, {8, 2, 1}, {8, 4, 1},
+                                    {16, 0, 0}, {8, 0, 0}};
+  for (const hdr_batch_config &c : cands) {
+    st = hdr_reconstruct_batch(ctx, n_frames, frames, &c, cuda_stream);  // warm-up (and graph record)
+    if (st == HDR_E_UNSUPPORTED) continue;
+    if (st) break;
+    float ms = 0.f;
+    cudaError_t e = cudaEventRecord(e0, stream);
+    for (int r = 0; r < 2 && e == cudaSuccess && st == HDR_OK; r++) st = hdr_reconstruct_batch(ctx, n_frames, frames, &c, cuda_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = fail(HDR_E_CUDA, "timing a batch configuration failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (st) break;
+    if (ms < win_ms) {
+      win_ms = ms;
+      win = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st && st != HDR_E_UNSUPPORTED) return st;
+  if (win_ms >= 1e30f) return fail(HDR_E_UNSUPPORTED, "no batch configuration fits this device");
+  ctx->batch.tuned[batch_kind(ctx, n_frames, frames)] = win;
+  if (best) *best = win;
+  return HDR_OK;
+}
 
 // ------------------------------------------------------------------ reconstruction without allocation
 //

@@ -82,6 +82,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase,
   return false;
 }
 
+// Order this thread's later tensor-map uses after earlier generic writes of the 128-byte map at
+// `map` (global memory).
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -403,21 +410,22 @@ __device__ __forceinline__ void accumulate_sensor(Moments<ORDER, COMP> &m, const
   }
 }
 
-template <int ORDER, bool COMP, bool DIAG>
-__global__ void __launch_bounds__(LPA_THREADS, 2) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
-  __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
-  __shared__ __align__(8) uint64_t mbar;
-
+// One output tile (16 x TH pixels) of frame L, by a CTA of 16*TH threads (one per pixel).
+// GLOBAL_MAPS: L (and its tensor maps) lives in global memory rather than in kernel parameters.
+// `phase` is the parity of the CTA's mbarrier use for this tile. Returns false when the CTA must
+// stop (a bounded wait ran out here or in another CTA).
+template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS>
+__device__ __forceinline__ bool process_tile(const LpaLaunch &L, int tile, unsigned char *smem, uint64_t *mbar,
+                                             uint32_t phase, int *fp_x0, int *fp_y0,
+                                             Anchor (*anchors)[LPA_MAX_SENSORS]) {
+  constexpr int NT = LPA_TILE * TH;
   const int tid = threadIdx.x;
   // once any CTA's bounded wait has run out, later CTAs retire at once
-  if (*reinterpret_cast<volatile unsigned int *>(L.status) & LPA_ERR_TIMEOUT) return;
-  const int tu = blockIdx.x % L.tiles_x, tv = blockIdx.x / L.tiles_x;
-  const int u0 = tu * LPA_TILE, v0 = tv * LPA_TILE;
+  if (*reinterpret_cast<volatile unsigned int *>(L.status) & LPA_ERR_TIMEOUT) return false;
+  const int tu = tile % L.tiles_x, tv = tile / L.tiles_x;
+  const int u0 = tu * LPA_TILE, v0 = tv * TH;
   const int S = L.n_sensors;
 
-  if (tid == 0) mbar_init(&mbar, 1);
   if (tid < S) {
     // staged footprint: sensor-space bounding box of the tile's pixel points, grown by the
     // largest window's half extent and the margin; x origin on a 16-byte boundary
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(LPA_THREADS, 2) lpa_reconstruct(const __grid_c
     double mnx = 1e300, mny = 1e300;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      double uu = u0 + (k & 1) * (LPA_TILE - 1), vv = v0 + (k >> 1) * (LPA_TILE - 1);
+      double uu = u0 + (k & 1) * (LPA_TILE - 1), vv = v0 + (k >> 1) * (TH - 1);
       double qx = Sk.G[0] * uu + Sk.G[1] * vv + Sk.G[2];
       double qy = Sk.G[3] * uu + Sk.G[4] * vv + Sk.G[5];
       mnx = fmin(mnx, fmin(fmax(qx, -LPA_FAR), LPA_FAR));
@@ -438,8 +446,9 @@ __global__ void __launch_bounds__(LPA_THREADS, 2) lpa_reconstruct(const __grid_c
     fp_x0[tid] = x0;
     fp_y0[tid] = y0;
   }
-  if (tid >= 32 && tid < 32 + 4 * S) {
-    const int k = tid - 32, a = k & 3, s = k >> 2;
+  constexpr int NA = 2 * (TH / LPA_ANCHOR);  // anchor blocks per tile
+  if (tid >= 32 && tid < 32 + NA * S) {
+    const int k = tid - 32, a = k % NA, s = k / NA;
     const LpaSensorK &Sk = L.s[s];
     double uu = u0 + (a & 1) * LPA_ANCHOR, vv = v0 + (a >> 1) * LPA_ANCHOR;
     double qx = fmin(fmax(Sk.G[0] * uu + Sk.G[1] * vv + Sk.G[2], -LPA_FAR), LPA_FAR);
@@ -449,17 +458,21 @@ __global__ void __launch_bounds__(LPA_THREADS, 2) lpa_reconstruct(const __grid_c
   }
   __syncthreads();
   if (tid == 0) {
-    mbar_arrive_expect_tx(&mbar, L.tx_bytes);
-    for (int s = 0; s < S; s++) tma_load_2d(smem + L.s[s].off_raw, &L.s[s].tmap, fp_x0[s], fp_y0[s], &mbar);
+    // tensor maps kept in global memory are rewritten between launches at the same addresses:
+    // make this launch's contents visible to the tensor-map proxy before the copies use them
+    if (GLOBAL_MAPS)
+      for (int s = 0; s < S; s++) tensormap_acquire(&L.s[s].tmap);
+    mbar_arrive_expect_tx(mbar, L.tx_bytes);
+    for (int s = 0; s < S; s++) tma_load_2d(smem + L.s[s].off_raw, &L.s[s].tmap, fp_x0[s], fp_y0[s], mbar);
   }
-  bool landed = mbar_wait_bounded(&mbar, 0, 1u << 20);
+  bool landed = mbar_wait_bounded(mbar, phase, 1u << 20);
   landed = __syncthreads_and(landed);
   if (!landed) {
     if (tid == 0) {
       atomicOr(L.status, LPA_ERR_TIMEOUT);
-      mbar_wait_bounded(&mbar, 0, 1u << 20);  // let copies in flight land before the CTA retires
+      mbar_wait_bounded(mbar, phase, 1u << 20);  // let copies in flight land before the CTA retires
     }
-    return;
+    return false;
   }
 
   // convert the staged raw values once per sample: Eq. 18 and the inverse of Eq. 20
@@ -473,9 +486,9 @@ __global__ void __launch_bounds__(LPA_THREADS, 2) lpa_reconstruct(const __grid_c
     const float inv_gtn = Sk.inv_gtn, gtn2 = Sk.gtn2, gain = Sk.gain, rv0 = Sk.read_var, b0 = Sk.black;
     const float sat0 = Sk.sat;
     const int W = Sk.width, H = Sk.height;
-    const int step_y = LPA_THREADS / bw, step_x = LPA_THREADS - step_y * bw;
+    const int step_y = NT / bw, step_x = NT - step_y * bw;
     int lx = tid % bw, ly = tid / bw;
-    for (int e = tid; e < n; e += LPA_THREADS) {
+    for (int e = tid; e < n; e += NT) {
       const int X = x0 + lx, Y = y0 + ly;
       float f = 0.f, iv = 0.f;
       if (X >= 0 && X < W && Y >= 0 && Y < H) {
@@ -516,7 +529,7 @@ __global__ void __launch_bounds__(LPA_THREADS, 2) lpa_reconstruct(const __grid_c
   const int u = u0 + 2 * (lane & 7) + (par & 1);
   const int v = v0 + 2 * ((lane >> 3) + 4 * hf) + (par >> 1);
   const bool pix = (u < L.out_w) && (v < L.out_h);
-  const int ab = ((u - u0) >> 3) + 2 * ((v - v0) >> 3);
+  const int ab = ((u - u0) >> 3) + 2 * ((v - v0) >> 3);  // < NA
   const int du = (u - u0) & 7, dv = (v - v0) & 7;
   constexpr int P = n_unknowns(ORDER);
   const int J = L.n_scales;
@@ -575,6 +588,49 @@ __global__ void __launch_bounds__(LPA_THREADS, 2) lpa_reconstruct(const __grid_c
         reinterpret_cast<float *>(L.out)[c * plane_px + opix] = ici.val;
       if (L.choice) L.choice[c * plane_px + opix] = (uint8_t)ici.choice;
     }
+  }
+  return true;
+}
+
+// Single frame: one CTA per tile.
+template <int ORDER, bool COMP, bool DIAG, int TH>
+__global__ void __launch_bounds__(LPA_TILE *TH, 16 / TH * 2) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
+  __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) mbar_init(&mbar, 1);
+  process_tile<ORDER, COMP, DIAG, TH, false>(L, blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0, anchors);
+}
+
+// Many frames in one launch: persistent CTAs take tiles from a device-wide counter over the
+// tile list (frame index, tile index), most expensive frames first as ordered by the host.
+template <bool COMP, int TH>
+__global__ void __launch_bounds__(LPA_TILE *TH, 16 / TH * 2) lpa_reconstruct_batch(const __grid_constant__ LpaBatch B) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
+  __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int next;
+  if (threadIdx.x == 0) mbar_init(&mbar, 1);
+  const int n_tiles = *B.n_tiles;
+  uint32_t phase = 0;
+  for (;;) {
+    __syncthreads();  // every thread is done with the previous tile's staging
+    if (threadIdx.x == 0) next = (int)atomicAdd(B.counter, 1u);
+    __syncthreads();
+    const int t = next;
+    if (t >= n_tiles) break;
+    const int2 ft = B.tiles[t];
+    const LpaLaunch &F = B.frames[ft.x];
+    bool ok;
+    switch (F.order) {
+      case 0: ok = process_tile<0, COMP, false, TH, true>(F, ft.y, smem, &mbar, phase, fp_x0, fp_y0, anchors); break;
+      case 1: ok = process_tile<1, COMP, false, TH, true>(F, ft.y, smem, &mbar, phase, fp_x0, fp_y0, anchors); break;
+      default: ok = process_tile<2, COMP, false, TH, true>(F, ft.y, smem, &mbar, phase, fp_x0, fp_y0, anchors); break;
+    }
+    if (!__syncthreads_and(ok)) break;
+    phase ^= 1u;
   }
 }
 

@@ -6,8 +6,7 @@
 
 #define LPA_MAX_SENSORS 8
 #define LPA_MAX_SCALES 8
-#define LPA_TILE 16         // output tile edge in pixels (one CTA per tile)
-#define LPA_THREADS 256     // one thread per output pixel of the tile
+#define LPA_TILE 16         // output tile width in pixels; the height TH is 8 or 16 (one thread per pixel)
 #define LPA_ANCHOR 8        // edge of the output blocks whose sensor positions are anchored in FP64
 #define LPA_MARGIN 4        // staging margin in sensor px around every window box
 
@@ -55,6 +54,16 @@ struct LpaLaunch {
   float *levels;
   unsigned int *status;
   uint32_t tx_bytes;             // bytes landed by the bulk tensor copies of one tile
-  uint32_t off_anchor;           // byte offset of the anchor table
   uint32_t smem_bytes;
+  int tile_h;                    // tile height the plan was made for
+};
+
+// Several frames in one persistent launch. The tile list, its length and the counter live in
+// device memory so that a captured graph of the launch stays valid when the frames change.
+struct LpaBatch {
+  const LpaLaunch *frames;       // [n_frames] (device)
+  const int2 *tiles;             // [n_tiles] (frame index, tile index within the frame) (device)
+  const int *n_tiles;            // (device)
+  unsigned int *counter;         // tile counter, zero at launch (device)
+  uint32_t smem_bytes;           // max over the frames
 };

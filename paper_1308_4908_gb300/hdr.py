@@ -41,6 +41,16 @@ class hdr_params(ctypes.Structure):
                 ("out_affine", ctypes.c_double * 6), ("out_dtype", ctypes.c_int32), ("accum", ctypes.c_int32)]
 
 
+class hdr_frame(ctypes.Structure):
+    _fields_ = [("rig_id", ctypes.c_int32), ("params", ctypes.c_void_p),
+                ("raw_dev", ctypes.c_void_p * HDR_MAX_SENSORS), ("out_dev", ctypes.c_void_p),
+                ("choice_dev", ctypes.c_void_p)]
+
+
+class hdr_batch_config(ctypes.Structure):
+    _fields_ = [("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("cost_order", ctypes.c_int32)]
+
+
 class HdrError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -77,10 +87,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.hdr_reconstruct_host.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
     lib.hdr_check.argtypes = [_P, _P]
     lib.hdr_reconstruct_noalloc.argtypes = [ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
+    lib.hdr_reconstruct_batch.argtypes = [_P, ctypes.c_int32, _P, _P, _P]
+    lib.hdr_tune_batch.argtypes = [_P, ctypes.c_int32, _P, _P, _P]
     lib.hdr_last_error.argtypes = []
     lib.hdr_last_error.restype = ctypes.c_char_p
     for name in ("hdr_create", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_levels", "hdr_reconstruct_host",
-                 "hdr_check", "hdr_reconstruct_noalloc"):
+                 "hdr_check", "hdr_reconstruct_noalloc", "hdr_reconstruct_batch", "hdr_tune_batch"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -144,6 +156,20 @@ def hdr_check(ctx: int, stream: Optional[int] = None) -> None:
 
 def hdr_last_error() -> str:
     return load().hdr_last_error().decode()
+
+
+def hdr_reconstruct_batch(ctx: int, frames: Sequence[hdr_frame], cfg: Optional[hdr_batch_config] = None,
+                          stream: Optional[int] = None) -> None:
+    arr = (hdr_frame * len(frames))(*frames)
+    _check(load().hdr_reconstruct_batch(ctypes.c_void_p(ctx), len(frames), arr,
+                                        ctypes.byref(cfg) if cfg is not None else None, ctypes.c_void_p(stream)))
+
+
+def hdr_tune_batch(ctx: int, frames: Sequence[hdr_frame], stream: Optional[int] = None) -> hdr_batch_config:
+    arr = (hdr_frame * len(frames))(*frames)
+    best = hdr_batch_config()
+    _check(load().hdr_tune_batch(ctypes.c_void_p(ctx), len(frames), arr, ctypes.byref(best), ctypes.c_void_p(stream)))
+    return best
 
 
 HDR_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -251,6 +277,26 @@ class Context:
             hdr_reconstruct(self.handle, rig_id, hp, ptrs, out.data_ptr(),
                             choice.data_ptr() if choice is not None else None, self._stream(stream))
         return out
+
+    def frame(self, rig_id: int, params, raws, out, choice=None, keep: Optional[list] = None) -> hdr_frame:
+        """hdr_frame for a batch; `keep` collects the ctypes objects the frame points at."""
+        hp = params if isinstance(params, hdr_params) else params_struct(params)
+        if keep is not None:
+            keep.append(hp)
+        f = hdr_frame()
+        f.rig_id = int(rig_id)
+        f.params = ctypes.addressof(hp)
+        for i, r in enumerate(raws):
+            f.raw_dev[i] = int(r.data_ptr())
+        f.out_dev = out.data_ptr()
+        f.choice_dev = choice.data_ptr() if choice is not None else None
+        return f
+
+    def reconstruct_batch(self, frames: Sequence[hdr_frame], cfg: Optional[hdr_batch_config] = None, stream=None):
+        hdr_reconstruct_batch(self.handle, frames, cfg, self._stream(stream))
+
+    def tune_batch(self, frames: Sequence[hdr_frame], stream=None) -> hdr_batch_config:
+        return hdr_tune_batch(self.handle, frames, self._stream(stream))
 
     def reconstruct_host(self, rig_id: int, params, raws_host: Sequence[np.ndarray], out_host: np.ndarray,
                          choice_host: Optional[np.ndarray] = None, stream=None):

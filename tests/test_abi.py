@@ -31,7 +31,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for n in ("hdr_create", "hdr_destroy", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_host",
-              "hdr_check", "hdr_last_error", "hdr_params_default", "hdr_reconstruct_levels"):
+              "hdr_check", "hdr_last_error", "hdr_params_default", "hdr_reconstruct_levels",
+              "hdr_reconstruct_batch", "hdr_tune_batch"):
         assert n in names
 
 
@@ -52,17 +53,19 @@ def test_struct_layout_matches_the_header(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hdr_params), sizeof(hdr_sensor_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hdr_params), sizeof(hdr_sensor_desc),
          offsetof(hdr_params, cond_fallback), offsetof(hdr_params, out_affine), offsetof(hdr_params, accum),
-         offsetof(hdr_sensor_desc, affine), offsetof(hdr_sensor_desc, sat_frame), offsetof(hdr_sensor_desc, read_var));
+         offsetof(hdr_sensor_desc, affine), offsetof(hdr_sensor_desc, sat_frame), offsetof(hdr_sensor_desc, read_var),
+         sizeof(hdr_frame), offsetof(hdr_frame, out_dev), offsetof(hdr_frame, choice_dev), sizeof(hdr_batch_config));
   return 0;
 }}''')
     exe = tmp_path / "probe"
     subprocess.check_call(["gcc", "-std=c11", "-o", str(exe), str(src)])
     got = list(map(int, subprocess.check_output([str(exe)]).split()))
-    P, D = hdr.hdr_params, hdr.hdr_sensor_desc
+    P, D, F = hdr.hdr_params, hdr.hdr_sensor_desc, hdr.hdr_frame
     want = [ctypes.sizeof(P), ctypes.sizeof(D), P.cond_fallback.offset, P.out_affine.offset, P.accum.offset,
-            D.affine.offset, D.sat_frame.offset, D.read_var.offset]
+            D.affine.offset, D.sat_frame.offset, D.read_var.offset, ctypes.sizeof(F), F.out_dev.offset,
+            F.choice_dev.offset, ctypes.sizeof(hdr.hdr_batch_config)]
     assert got == want
 
 

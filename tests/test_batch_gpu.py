@@ -1,0 +1,128 @@
+"""Batched reconstruction: many uneven frames in one persistent, graph-recorded kernel launch.
+
+Each frame's result must equal its single-frame reconstruction (same per-pixel arithmetic), for
+every launch configuration the autotuner may pick; one frame is also checked against the oracle.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1308_4908_gb300 import synth
+from tests import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1308_4908_gb300 import hdr
+    c = hdr.Context(0)
+    yield c
+    c.close()
+
+
+def _prepare(ctx, frames, base_rig=0):
+    """Rigs, device raws and output buffers for a list of synth frames."""
+    items = []
+    for k, fr in enumerate(frames):
+        ctx.set_rig(base_rig + k, fr.sensors)
+        raws = [torch.from_numpy(s.raw).cuda() for s in fr.sensors]
+        p = fr.params
+        out = torch.full((3, p.out_h, p.out_w), -7.0, device="cuda")
+        ch = torch.empty((3, p.out_h, p.out_w), dtype=torch.uint8, device="cuda")
+        items.append((base_rig + k, fr, raws, out, ch))
+    return items
+
+
+def _single(ctx, items):
+    refs = []
+    for rig, fr, raws, _, _ in items:
+        ch = torch.empty((3, fr.params.out_h, fr.params.out_w), dtype=torch.uint8, device="cuda")
+        out = ctx.reconstruct(rig, fr.params, raws, choice=ch)
+        refs.append((out.cpu().numpy(), ch.cpu().numpy()))
+    ctx.check()
+    return refs
+
+
+def _batch(ctx, items, cfg=None):
+    keep = []
+    hf = [ctx.frame(rig, fr.params, raws, out, ch, keep) for rig, fr, raws, out, ch in items]
+    ctx.reconstruct_batch(hf, cfg)
+    ctx.check()
+    return [(out.cpu().numpy(), ch.cpu().numpy()) for _, _, _, out, ch in items]
+
+
+def _same(a, b):
+    for (oa, ca), (ob, cb) in zip(a, b):
+        np.testing.assert_array_equal(ca, cb)
+        np.testing.assert_array_equal(oa, ob)
+
+
+def test_batch_equals_single_frames_for_every_configuration(ctx):
+    """Uneven frames (sizes, sensor counts 2-4, orders 0-2, 1x and 1.5x outputs) in one launch."""
+    from paper_1308_4908_gb300 import hdr
+    frames = synth.batching(n_frames=8, size_cap=160)
+    items = _prepare(ctx, frames)
+    refs = _single(ctx, items)
+    for th in (16, 8):
+        for per_sm in (0, 1):
+            for order in (1, 0):
+                for _, _, _, out, _ in items:
+                    out.fill_(-7.0)
+                cfg = hdr.hdr_batch_config(th, per_sm, order)
+                _same(_batch(ctx, items, cfg), refs)
+
+
+def test_batch_replays_with_new_contents(ctx):
+    """The recorded graph is replayed with fresh tables: a second batch of the same shapes but other
+    frames (other rigs and raws) gives those frames' results."""
+    a = synth.batching(n_frames=4, size_cap=96, seed=2001)
+    b = synth.batching(n_frames=4, size_cap=96, seed=2002)
+    ia = _prepare(ctx, a, base_rig=10)
+    ib = _prepare(ctx, b, base_rig=20)
+    ra, rb = _single(ctx, ia), _single(ctx, ib)
+    _same(_batch(ctx, ia), ra)
+    _same(_batch(ctx, ib), rb)
+    _same(_batch(ctx, ia), ra)
+
+
+def test_tuner_picks_a_configuration_and_batch_uses_it(ctx):
+    frames = synth.batching(n_frames=6, size_cap=128, seed=2003)
+    items = _prepare(ctx, frames, base_rig=30)
+    refs = _single(ctx, items)
+    keep = []
+    hf = [ctx.frame(rig, fr.params, raws, out, ch, keep) for rig, fr, raws, out, ch in items]
+    best = ctx.tune_batch(hf)
+    assert best.tile_h in (8, 16) and 0 <= best.ctas_per_sm <= 8 and best.cost_order in (0, 1)
+    _same(_batch(ctx, items), refs)        # cfg None -> the tuned configuration
+
+
+def test_batch_frame_against_oracle(ctx):
+    frames = synth.batching(n_frames=3, size_cap=72, seed=2004)
+    items = _prepare(ctx, frames, base_rig=40)
+    got = _batch(ctx, items)
+    for (rig, fr, _, _, _), (out, ch) in zip(items, got):
+        p = fr.params
+        r = np.random.default_rng(rig)
+        pix = np.stack([r.integers(0, p.out_w, 300), r.integers(0, p.out_h, 300)], axis=1)
+        o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True)
+        parity.compare(out[:, pix[:, 1], pix[:, 0]], ch[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
+                       p.ici_gamma, p.min_pivot)
+
+
+def test_batch_rejects_bad_input(ctx):
+    from paper_1308_4908_gb300 import hdr
+    frames = synth.batching(n_frames=2, size_cap=64, seed=2005)
+    items = _prepare(ctx, frames, base_rig=50)
+    keep = []
+    hf = [ctx.frame(rig, fr.params, raws, out, ch, keep) for rig, fr, raws, out, ch in items]
+    hf[1].rig_id = 63                      # undefined rig
+    with pytest.raises(hdr.HdrError):
+        ctx.reconstruct_batch(hf)
+    with pytest.raises(hdr.HdrError):
+        ctx.reconstruct_batch(hf[:0])
+    with pytest.raises(hdr.HdrError):
+        ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(12, 0, 1))
