@@ -221,13 +221,202 @@ def run_reference(args, world, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batching and serving workloads
+
+def _make_frame(job):
+    from paper_1308_4908_gb300 import synth
+    kind, arg = job
+    if kind == "paper":
+        return synth.paper_scale(size=arg)
+    if kind == "serve":
+        return synth.serving_stream_frame(arg, 0)
+    return synth.batching_frame(arg)
+
+
+def make_frames(jobs):
+    """Generate the synthetic frames in parallel (spawned workers: safe after CUDA initialisation)."""
+    import multiprocessing as mp
+    n = min(len(jobs), os.cpu_count() or 1)
+    if n <= 1:
+        return [_make_frame(j) for j in jobs]
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(_make_frame, jobs, chunksize=1)
+
+
+def pinned(a: np.ndarray) -> np.ndarray:
+    """A copy of `a` in page-locked host memory."""
+    import torch
+    t = torch.empty(a.nbytes, dtype=torch.uint8).pin_memory()
+    out = t.numpy().view(a.dtype).reshape(a.shape)
+    out[...] = a
+    return out
+
+
+def run_batching(ctx, frames, dev, reps: int = 10):
+    """16 uneven frames in one persistent graph launch (tuned configuration) against a plain
+    per-frame launch loop of the same frames on the same stream; inputs resident, L2 flushed."""
+    import torch
+    from paper_1308_4908_gb300 import hdr
+    keep, hf, outs, items = [], [], [], []
+    for k, fr in enumerate(frames):
+        ctx.set_rig(32 + k, fr.sensors)
+        raws = [torch.from_numpy(s.raw).to(dev) for s in fr.sensors]
+        p = fr.params
+        out = torch.empty((3, p.out_h, p.out_w), dtype=torch.float32, device=dev)
+        hp = hdr.params_struct(p)
+        keep += [raws, out, hp]
+        hf.append(ctx.frame(32 + k, hp, raws, out, None, keep))
+        items.append((32 + k, hp, [int(r.data_ptr()) for r in raws], out))
+    px = sum(f.params.out_w * f.params.out_h for f in frames)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    best = ctx.tune_batch(hf, stream=stream)
+    ctx.check(stream)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            fn()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for k in range(reps):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                fn()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.check(stream)
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    def plain():
+        for rig, hp, ptrs, out in items:
+            hdr.hdr_reconstruct(ctx.handle, rig, hp, ptrs, out.data_ptr(), None, stream.cuda_stream)
+
+    t_batch = timed(lambda: ctx.reconstruct_batch(hf, None, stream))
+    t_plain = timed(plain)
+    return {"workload": "batching: 16 frames, raw sizes from {512^2, 1280x720, 1920x1080, 2048^2}, 2-4 sensors "
+                        "(ND 1, 1/8, 1/64, 1/512), order 0-2, output 1x or 1.5x, 4 scales with ICI",
+            "output_px": px, "frames": [f.name for f in frames],
+            "batched": {"ms": round(t_batch, 3), "mpx_s": round(px / t_batch / 1e3, 1), "gpu_launches": 1,
+                        "config": {"tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm,
+                                   "cost_order": best.cost_order}},
+            "per_frame": {"ms": round(t_plain, 3), "mpx_s": round(px / t_plain / 1e3, 1), "gpu_launches": len(frames)},
+            "speedup": round(t_plain / t_batch, 3), "l2": "flushed between timed repetitions"}
+
+
+def poisson_schedule(n_streams: int, fps: float, seconds: float, seed: int = 1005):
+    r = np.random.default_rng(seed)
+    ev = []
+    for m in range(n_streams):
+        t = r.exponential(1.0 / fps)
+        while t < seconds:
+            ev.append((t, m))
+            t += r.exponential(1.0 / fps)
+    ev.sort()
+    return ev
+
+
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def run_serving(ctx, frames, dev, seconds: float, step_tiles: int):
+    """8 concurrent streams at 30 fps with Poisson arrivals through the request loop (hdr_submit /
+    hdr_poll, pinned host buffers, copies included), and the same arrivals through a plain
+    per-frame loop (hdr_reconstruct_host, one frame at a time); latency is arrival -> output in host
+    memory."""
+    from paper_1308_4908_gb300 import hdr
+    R = 8
+    streams = []
+    for m, fr in enumerate(frames):
+        ctx.set_rig(8 + m, fr.sensors)
+        hp = hdr.params_struct(fr.params)
+        raws = [pinned(s.raw) for s in fr.sensors]
+        outs = [pinned(np.zeros((3, hp.out_h, hp.out_w), np.float32)) for _ in range(R)]
+        streams.append((hp, raws, outs))
+    px = [hp.out_w * hp.out_h for hp, _, _ in streams]
+    sched = poisson_schedule(len(frames), 30.0, seconds)
+    offered = sum(px[m] for _, m in sched) / seconds / 1e6
+    cfg = dict(max_frames=48, pool_bytes=6 << 30, step_tiles=step_tiles)
+
+    def serve(sched, clock=None):
+        srv = hdr.Server(ctx, **cfg)
+        slot = [[None] * R for _ in streams]
+        cnt = [0] * len(streams)
+        t0 = time.perf_counter()
+        for t, m in sched:
+            while True:
+                d = t0 + t - time.perf_counter()
+                if d <= 0:
+                    break
+                time.sleep(min(d, 0.002) if d > 0.0003 else 0)
+            i = cnt[m] % R
+            cnt[m] += 1
+            if slot[m][i] is not None:
+                srv.poll(slot[m][i], -1)
+            hp, raws, outs = streams[m]
+            slot[m][i] = srv.submit(8 + m, hp, raws, outs[i], None, stream_id=m)
+        for row in slot:
+            for tk in row:
+                if tk is not None:
+                    srv.poll(tk, -1)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return st, wall
+
+    # warm-up: every stream once (records the step graphs), also through the plain path
+    serve([(0.0, m) for m in range(len(streams))])
+    for m, (hp, raws, outs) in enumerate(streams):
+        ctx.reconstruct_host(8 + m, hp, raws, outs[0])
+    with ClockSampler(dev.index or 0) as clk:
+        st, wall = serve(sched)
+    burst = [(0.0, m) for m in range(len(streams)) for _ in range(4)]
+    cap, cap_wall = serve(burst)
+
+    def plain(sched):
+        lat, t0 = [], time.perf_counter()
+        for t, m in sched:
+            d = t0 + t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            hp, raws, outs = streams[m]
+            ctx.reconstruct_host(8 + m, hp, raws, outs[0])
+            lat.append((time.perf_counter() - t0 - t) * 1e3)
+        return lat, time.perf_counter() - t0
+
+    lat, pwall = plain(sched)
+    _, pcap_wall = plain(burst)
+    burst_px = sum(px[m] for _, m in burst)
+    return {
+        "workload": "serving: 8 streams x 30 fps Poisson (2x 1280x720 2-sensor, 3x 1920x1080 3-sensor, 2x 2048^2 "
+                    "3-sensor, 1x 2048^2 3-sensor -> 3840x2160), LPA M=2, ICI over 4 scales, fp32 output",
+        "seconds": seconds, "requests": len(sched), "offered_mpx_s": round(offered, 1),
+        "served": {"mpx_s": round(st.output_pixels / wall / 1e6, 1), "p50_ms": round(st.p50_ms, 2),
+                   "p99_ms": round(st.p99_ms, 2), "max_ms": round(st.max_ms, 2),
+                   "mean_queue_ms": round(st.mean_queue_ms, 3), "steps": int(st.steps), "completed": int(st.completed),
+                   "config": cfg},
+        "plain_per_frame": {"mpx_s": round(sum(px[m] for _, m in sched) / pwall / 1e6, 1),
+                            "p50_ms": round(_pct(lat, 50), 2), "p99_ms": round(_pct(lat, 99), 2),
+                            "max_ms": round(max(lat), 2), "api": "hdr_reconstruct_host, one frame at a time"},
+        "capacity_mpx_s": {"served": round(burst_px / cap_wall / 1e6, 1), "plain_per_frame": round(burst_px / pcap_wall / 1e6, 1),
+                           "burst": f"{len(burst)} frames submitted at once"},
+        "latency": "submission (arrival) -> output in pinned host memory; host-to-device and device-to-host copies included",
+        "clocks": clk.summary(),
+    }
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
     from paper_1308_4908_gb300 import hdr, synth
+    extras = world == 1 and not args.headline_only
+    jobs = [("paper", args.size)]
+    if extras:
+        jobs += [("serve", m) for m in range(len(synth.SERVING_STREAMS))]
+        jobs += [("batch", sp) for sp in synth.batching_specs()]
+    made = make_frames(jobs)
+    frame = made[0]
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
-    frame = synth.paper_scale(size=args.size)
     p = frame.params
     ctx = hdr.Context(local)
     ctx.set_rig(0, frame.sensors)
@@ -294,6 +483,12 @@ def run_ours(args, world, rank, local, pg):
         d2h = int(out_host.numel()) * 4
         ctx.check(stream)
 
+    serving = batching = None
+    if extras:
+        n_s = len(synth.SERVING_STREAMS)
+        batching = run_batching(ctx, made[1 + n_s:], dev)
+        serving = run_serving(ctx, made[1:1 + n_s], dev, args.serve_seconds, args.step_tiles)
+
     if rank == 0:
         pk = peaks()
         peak = fp32_peak_tflops(pk)
@@ -318,6 +513,9 @@ def run_ours(args, world, rank, local, pg):
             "kernel_ms": {"mean": round(ms, 4), "min": round(min(kern_ms), 4), "max": round(max(kern_ms), 4)},
             "wall_s_timed_region": round(t_wall, 4),
         }
+        if serving is not None:
+            line["serving"] = serving
+            line["batching"] = batching
         if args.size != 2048:
             line["config"]["workload"] = WORKLOAD.replace("2048x2048", f"{args.size}x{args.size}")
         if world == 1 and not args.no_cpu_baseline:
@@ -335,6 +533,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--size", type=int, default=2048, help="raw and output edge (2048 = the paper-scale workload)")
+    ap.add_argument("--headline-only", action="store_true", help="skip the batching and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson arrival schedule")
+    ap.add_argument("--step-tiles", type=int, default=0, help="tile budget of one serving step (0 = all pending)")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup(args)
     try:

@@ -169,6 +169,68 @@ hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame
 hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, hdr_batch_config *best,
                           void *cuda_stream);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop over one context. The paper overlaps the transfer of one frame with the
+ * reconstruction of the previous one on two streams (Section 7); this loop generalises that to
+ * many concurrent video streams. Frames of any size, rig and order are submitted from any
+ * thread. A scheduler thread admits them in arrival order while a slot and room in the server's
+ * device-memory pool are free, copies their raw frames into the pool on a copy stream, and
+ * repeatedly launches one batched step over the pending tiles of the admitted frames, oldest
+ * frame first, at most step_tiles per step, with up to two steps queued on the device: frames that
+ * arrive while a step runs join a later one (continuous batching at tile granularity). A frame
+ * whose tiles are all done is copied back to its host buffers on a second copy stream and its
+ * memory returns to the pool. Each pixel is computed as hdr_reconstruct computes it, whatever
+ * else shares the step. The server uses its context exclusively until hdr_server_destroy (no
+ * other call on that context meanwhile); rigs must be set before serving starts. A device-side
+ * error fails every request whose tiles were on the device when it was seen. */
+typedef struct hdr_server hdr_server;
+
+typedef struct {
+  int32_t max_frames;           /* frames admitted at once (slots), >= 1                         */
+  uint64_t pool_bytes;          /* device pool for raw frames, outputs and level maps            */
+  int32_t step_tiles;           /* tile budget of one step; 0 = every pending tile               */
+  hdr_batch_config batch;       /* launch configuration of the steps (tile_h 0 = default)        */
+} hdr_server_config;
+
+typedef struct {
+  int32_t rig_id;
+  hdr_params params;            /* copied at submission                                           */
+  const uint16_t *raw_host[HDR_MAX_SENSORS]; /* host raw frames [height][pitch_elems]; read until
+                                   the request completes (pinned memory copies fastest)           */
+  void *out_host;               /* host output [3][out_h][out_w] of out_dtype, written at completion */
+  uint8_t *choice_host;         /* optional host level map, NULL = not produced                  */
+  int32_t stream_id;            /* caller's video stream, for its own bookkeeping               */
+} hdr_request;
+
+typedef struct {
+  hdr_status status;            /* HDR_OK once the output is in out_host                         */
+  double queue_ms;              /* submission -> admission                                       */
+  double total_ms;              /* submission -> output in host memory                           */
+  int32_t steps;                /* batched steps the frame's tiles ran in                        */
+} hdr_result;
+
+typedef struct {
+  uint64_t completed, submitted;
+  double p50_ms, p99_ms, max_ms;    /* of total_ms over completed requests                    */
+  double mean_queue_ms;
+  uint64_t steps, output_pixels;
+  double busy_s;                    /* wall time between the first admission and the last completion */
+} hdr_server_stats;
+
+/* Start a server on `ctx` (allocates the pool, streams and the scheduler thread). */
+hdr_status hdr_server_create(hdr_ctx *ctx, const hdr_server_config *cfg, hdr_server **out);
+/* Queue one frame and return its ticket; the request is validated here (HDR_E_INVALID) and
+ * HDR_E_UNSUPPORTED is returned if the frame can never fit the pool. */
+hdr_status hdr_submit(hdr_server *srv, const hdr_request *req, uint64_t *ticket);
+/* Wait up to timeout_ms (< 0 = forever) for a ticket. HDR_E_BUSY if it is not done by then; the
+ * result of a finished ticket is returned once and then forgotten. */
+hdr_status hdr_poll(hdr_server *srv, uint64_t ticket, int32_t timeout_ms, hdr_result *result);
+/* Latency and throughput of every request completed so far. */
+hdr_status hdr_server_stats_get(hdr_server *srv, hdr_server_stats *stats);
+/* Finish every submitted request, stop the scheduler and free the server (not the context);
+ * results not yet polled are discarded. */
+void hdr_server_destroy(hdr_server *srv);
+
 /* Wait for `cuda_stream`, then read and clear the context's device status word.
  * Returns HDR_E_TIMEOUT or HDR_E_INTERNAL if a kernel recorded one, HDR_E_CUDA on a
  * CUDA error, else HDR_OK. */

@@ -21,7 +21,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-diag-suppress", "1160", f"-I{CSRC}", f"-I{INCLUDE}"]
-SOURCES = ["lpa_host.cu", "lpa_m0.cu", "lpa_m1.cu", "lpa_m2.cu", "lpa_batch.cu"]
+SOURCES = ["lpa_host.cu", "lpa_m0.cu", "lpa_m1.cu", "lpa_m2.cu", "lpa_serve.cu"]
 
 
 def _deps_mtime() -> float:
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)

@@ -8,7 +8,22 @@ cudaError_t lpa_launch_order0(const LpaLaunch &L, bool comp, bool diag, cudaStre
 cudaError_t lpa_launch_order1(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
 cudaError_t lpa_launch_order2(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
 
-// Persistent launch over the tiles of several frames (tile height 8 or 16).
-cudaError_t lpa_launch_batch(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st);
-// Resident CTAs per SM of the batch kernel for that configuration (0 on error).
-int lpa_batch_ctas_per_sm(bool comp, int tile_h, uint32_t smem_bytes);
+// Persistent launch of order M over its segment of a many-frame tile list (tile height 8 or 16).
+cudaError_t lpa_launch_batch_order0(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st);
+cudaError_t lpa_launch_batch_order1(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st);
+cudaError_t lpa_launch_batch_order2(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st);
+// Resident CTAs per SM of that kernel with that much dynamic shared memory (0 on error).
+int lpa_batch_ctas_per_sm_order0(bool comp, int tile_h, uint32_t smem_bytes);
+int lpa_batch_ctas_per_sm_order1(bool comp, int tile_h, uint32_t smem_bytes);
+int lpa_batch_ctas_per_sm_order2(bool comp, int tile_h, uint32_t smem_bytes);
+
+inline cudaError_t lpa_launch_batch(int order, const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st) {
+  return order == 0   ? lpa_launch_batch_order0(B, comp, tile_h, grid, st)
+         : order == 1 ? lpa_launch_batch_order1(B, comp, tile_h, grid, st)
+                      : lpa_launch_batch_order2(B, comp, tile_h, grid, st);
+}
+inline int lpa_batch_ctas_per_sm(int order, bool comp, int tile_h, uint32_t smem_bytes) {
+  return order == 0   ? lpa_batch_ctas_per_sm_order0(comp, tile_h, smem_bytes)
+         : order == 1 ? lpa_batch_ctas_per_sm_order1(comp, tile_h, smem_bytes)
+                      : lpa_batch_ctas_per_sm_order2(comp, tile_h, smem_bytes);
+}

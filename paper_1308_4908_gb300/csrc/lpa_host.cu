@@ -16,6 +16,7 @@
 
 #include "hdr_lpa.h"
 #include "lpa_dispatch.h"
+#include "lpa_internal.h"
 #include "lpa_launch.h"
 
 static_assert(HDR_MAX_SENSORS == LPA_MAX_SENSORS, "sensor limits differ");
@@ -62,22 +63,31 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 }  // namespace
 
-// Device tables and recorded graphs of the batched launch.
+// Device tables and recorded graphs of the batched launch. The host staging is double-buffered:
+// a launch may be prepared while the previous one still runs (each buffer has its own graphs).
 struct BatchState {
   size_t cap_frames = 0, cap_tiles = 0;
-  LpaLaunch *frames_dev = nullptr, *frames_host = nullptr;   // host side is pinned staging
-  int2 *tiles_dev = nullptr, *tiles_host = nullptr;
-  int *ntiles_dev = nullptr, *ntiles_host = nullptr;
-  unsigned int *counter_dev = nullptr;
-  cudaEvent_t tables_read = nullptr;                          // the last graph finished reading staging
-  bool pending = false;
+  LpaLaunch *frames_dev = nullptr;
+  int2 *tiles_dev = nullptr;
+  int *bounds_dev = nullptr;                                  // [4] segment bounds per order
+  unsigned int *counters_dev = nullptr;                       // [3]
+  struct Staging {
+    LpaLaunch *frames = nullptr;                              // pinned
+    int2 *tiles = nullptr;
+    int *bounds = nullptr;
+    cudaEvent_t done = nullptr;                               // the launch that read this buffer ended
+    bool pending = false;
+  } stage[2];
+  int cur = 0;
   struct Key {
-    int comp, tile_h, grid;
-    uint32_t smem;
+    int comp, tile_h, buf;
+    int grid[3];                                              // per order; 0 = no tiles of that order
+    uint32_t smem[3];
     size_t cap_frames, cap_tiles;
     bool operator<(const Key &o) const {
-      return std::tie(comp, tile_h, grid, smem, cap_frames, cap_tiles) <
-             std::tie(o.comp, o.tile_h, o.grid, o.smem, o.cap_frames, o.cap_tiles);
+      return std::tie(comp, tile_h, buf, grid[0], grid[1], grid[2], smem[0], smem[1], smem[2], cap_frames, cap_tiles) <
+             std::tie(o.comp, o.tile_h, o.buf, o.grid[0], o.grid[1], o.grid[2], o.smem[0], o.smem[1], o.smem[2],
+                      o.cap_frames, o.cap_tiles);
     }
   };
   std::map<Key, cudaGraphExec_t> graphs;
@@ -397,13 +407,15 @@ void hdr_destroy(hdr_ctx *ctx) {
   cudaFree(ctx->status);
   for (auto &g : ctx->batch.graphs) cudaGraphExecDestroy(g.second);
   cudaFree(ctx->batch.frames_dev);
-  cudaFreeHost(ctx->batch.frames_host);
   cudaFree(ctx->batch.tiles_dev);
-  cudaFreeHost(ctx->batch.tiles_host);
-  cudaFree(ctx->batch.ntiles_dev);
-  cudaFreeHost(ctx->batch.ntiles_host);
-  cudaFree(ctx->batch.counter_dev);
-  if (ctx->batch.tables_read) cudaEventDestroy(ctx->batch.tables_read);
+  cudaFree(ctx->batch.bounds_dev);
+  cudaFree(ctx->batch.counters_dev);
+  for (auto &S : ctx->batch.stage) {
+    cudaFreeHost(S.frames);
+    cudaFreeHost(S.tiles);
+    cudaFreeHost(S.bounds);
+    if (S.done) cudaEventDestroy(S.done);
+  }
   delete ctx;
 }
 
@@ -570,48 +582,64 @@ hdr_status check_batch(hdr_ctx *ctx, int32_t n, const hdr_frame *frames) {
   return HDR_OK;
 }
 
-// Grow the device tables and pinned staging of the batched launch.
+// Grow the device tables and both pinned staging buffers of the batched launch (waits for the
+// launches in flight first; graphs recorded on the old tables are dropped).
 hdr_status batch_reserve(hdr_ctx *ctx, size_t n_frames, size_t n_tiles) {
   BatchState &B = ctx->batch;
-  if (!B.tables_read) CUDA_TRY(cudaEventCreateWithFlags(&B.tables_read, cudaEventDisableTiming));
-  if (!B.counter_dev) {
-    CUDA_TRY(cudaMalloc(&B.counter_dev, sizeof(unsigned int)));
-    CUDA_TRY(cudaMalloc(&B.ntiles_dev, sizeof(int)));
-    CUDA_TRY(cudaMallocHost(&B.ntiles_host, sizeof(int)));
+  if (!B.counters_dev) {
+    CUDA_TRY(cudaMalloc(&B.counters_dev, 3 * sizeof(unsigned int)));
+    CUDA_TRY(cudaMalloc(&B.bounds_dev, 4 * sizeof(int)));
+    for (auto &S : B.stage) {
+      CUDA_TRY(cudaMallocHost(&S.bounds, 4 * sizeof(int)));
+      CUDA_TRY(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming));
+    }
   }
+  if (n_frames <= B.cap_frames && n_tiles <= B.cap_tiles) return HDR_OK;
+  for (auto &S : B.stage)
+    if (S.pending) {
+      CUDA_TRY(cudaEventSynchronize(S.done));
+      S.pending = false;
+    }
+  for (auto &g : B.graphs) cudaGraphExecDestroy(g.second);
+  B.graphs.clear();
   if (n_frames > B.cap_frames) {
     size_t cap = std::max<size_t>(n_frames, 2 * B.cap_frames);
     cudaFree(B.frames_dev);
-    cudaFreeHost(B.frames_host);
     B.frames_dev = nullptr;
-    B.frames_host = nullptr;
     B.cap_frames = 0;
+    for (auto &S : B.stage) {
+      cudaFreeHost(S.frames);
+      S.frames = nullptr;
+    }
     CUDA_TRY(cudaMalloc(&B.frames_dev, cap * sizeof(LpaLaunch)));
-    CUDA_TRY(cudaMallocHost(&B.frames_host, cap * sizeof(LpaLaunch)));
+    for (auto &S : B.stage) CUDA_TRY(cudaMallocHost(&S.frames, cap * sizeof(LpaLaunch)));
     B.cap_frames = cap;
   }
   if (n_tiles > B.cap_tiles) {
     size_t cap = std::max<size_t>(n_tiles, 2 * B.cap_tiles);
     cudaFree(B.tiles_dev);
-    cudaFreeHost(B.tiles_host);
     B.tiles_dev = nullptr;
-    B.tiles_host = nullptr;
     B.cap_tiles = 0;
+    for (auto &S : B.stage) {
+      cudaFreeHost(S.tiles);
+      S.tiles = nullptr;
+    }
     CUDA_TRY(cudaMalloc(&B.tiles_dev, cap * sizeof(int2)));
-    CUDA_TRY(cudaMallocHost(&B.tiles_host, cap * sizeof(int2)));
+    for (auto &S : B.stage) CUDA_TRY(cudaMallocHost(&S.tiles, cap * sizeof(int2)));
     B.cap_tiles = cap;
   }
   return HDR_OK;
 }
 
-// Plan every frame into the pinned staging and write the tile list. Returns the shared memory
-// the launch needs.
-hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const hdr_batch_config &cfg, uint32_t *smem,
-                      int *n_tiles_out) {
+// Plan every frame into the pinned staging and write the tile list (all tiles of each frame, or
+// the tiles [ranges[f].x, ranges[f].y) when ranges is given), grouped by polynomial order. Returns
+// each order's tile count and the shared memory its kernel needs.
+hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *ranges, const hdr_batch_config &cfg,
+                      uint32_t smem[3], int n_tiles[3]) {
   BatchState &B = ctx->batch;
   std::vector<LpaLaunch> plans(n);
   size_t total = 0;
-  uint32_t sm = 0;
+  for (int o = 0; o < 3; o++) smem[o] = 0, n_tiles[o] = 0;
   for (int f = 0; f < n; f++) {
     const hdr_frame &F = frames[f];
     hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
@@ -620,40 +648,51 @@ hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const hdr_ba
     plans[f].out = F.out_dev;
     plans[f].choice = F.choice_dev;
     plans[f].levels = nullptr;
-    total += (size_t)plans[f].tiles_x * plans[f].tiles_y;
-    sm = std::max(sm, plans[f].smem_bytes);
+    const int nt = plans[f].tiles_x * plans[f].tiles_y;
+    if (ranges && (ranges[f].x < 0 || ranges[f].y > nt || ranges[f].x > ranges[f].y))
+      return fail(HDR_E_INVALID, "frame %d: tile range [%d, %d) outside [0, %d)", f, ranges[f].x, ranges[f].y, nt);
+    const size_t cnt = ranges ? (size_t)(ranges[f].y - ranges[f].x) : (size_t)nt;
+    total += cnt;
+    if (cnt) smem[plans[f].order] = std::max(smem[plans[f].order], plans[f].smem_bytes);
   }
   if (total > (size_t)INT32_MAX) return fail(HDR_E_UNSUPPORTED, "too many tiles in one batch");
   hdr_status st = batch_reserve(ctx, n, std::max<size_t>(total, 1));
   if (st) return st;
-  if (B.pending) {  // the previous graph may still be reading the staging
-    CUDA_TRY(cudaEventSynchronize(B.tables_read));
-    B.pending = false;
+  BatchState::Staging &S = B.stage[B.cur];
+  if (S.pending) {  // the launch before the previous one may still be reading this buffer
+    CUDA_TRY(cudaEventSynchronize(S.done));
+    S.pending = false;
   }
   std::vector<int> order(n);
   for (int f = 0; f < n; f++) order[f] = f;
-  if (cfg.cost_order) {
-    std::vector<double> cost(n);
+  std::vector<double> cost(n, 0.0);
+  if (cfg.cost_order)
     for (int f = 0; f < n; f++) cost[f] = frame_cost(*frames[f].params, ctx->rigs[frames[f].rig_id].n);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (plans[a].order != plans[b].order) return plans[a].order < plans[b].order;
+    return cost[a] > cost[b];
+  });
   size_t t = 0;
+  S.bounds[0] = 0;
   for (int k = 0; k < n; k++) {
     const int f = order[k];
-    B.frames_host[f] = plans[f];
-    const int nt = plans[f].tiles_x * plans[f].tiles_y;
-    for (int i = 0; i < nt; i++) B.tiles_host[t++] = make_int2(f, i);
+    S.frames[f] = plans[f];
+    const int t0 = ranges ? ranges[f].x : 0;
+    const int t1 = ranges ? ranges[f].y : plans[f].tiles_x * plans[f].tiles_y;
+    for (int i = t0; i < t1; i++) S.tiles[t++] = make_int2(f, i);
+    n_tiles[plans[f].order] += t1 - t0;
   }
-  *B.ntiles_host = (int)total;
-  *smem = sm;
-  *n_tiles_out = (int)total;
+  S.bounds[1] = n_tiles[0];
+  S.bounds[2] = n_tiles[0] + n_tiles[1];
+  S.bounds[3] = (int)total;
   return HDR_OK;
 }
 
 }  // namespace
 
-extern "C" hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames,
-                                            const hdr_batch_config *cfg_in, void *cuda_stream) {
+// One persistent launch over the listed tiles of several frames (see hdr_reconstruct_batch).
+hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, const int2 *ranges,
+                         const hdr_batch_config *cfg_in, cudaStream_t stream) {
   hdr_status st = check_batch(ctx, n_frames, frames);
   if (st) return st;
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -666,50 +705,120 @@ extern "C" hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, cons
   }
   if (cfg.tile_h != 8 && cfg.tile_h != 16) return fail(HDR_E_INVALID, "tile_h must be 8 or 16");
   if (cfg.ctas_per_sm < 0 || cfg.ctas_per_sm > 8) return fail(HDR_E_INVALID, "ctas_per_sm must be in [0, 8]");
-  uint32_t smem = 0;
-  int n_tiles = 0;
-  st = batch_plan(ctx, n_frames, frames, cfg, &smem, &n_tiles);
+  uint32_t smem[3];
+  int n_tiles[3];
+  st = batch_plan(ctx, n_frames, frames, ranges, cfg, smem, n_tiles);
   if (st) return st;
   BatchState &B = ctx->batch;
   const bool comp = frames[0].params->accum != 0;
-  int fit = lpa_batch_ctas_per_sm(comp, cfg.tile_h, smem);
-  if (fit < 1) return fail(HDR_E_UNSUPPORTED, "the batched kernel does not fit an SM with %u bytes of shared memory", smem);
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, fit) : fit;
-  const int grid = std::max(1, std::min(sms * per_sm, std::max(n_tiles, 1)));
-  cudaStream_t stream = (cudaStream_t)cuda_stream;
-  BatchState::Key key{comp ? 1 : 0, cfg.tile_h, grid, smem, B.cap_frames, B.cap_tiles};
+  const int buf = B.cur;
+  BatchState::Staging &S = B.stage[buf];
+  BatchState::Key key{comp ? 1 : 0, cfg.tile_h, buf, {0, 0, 0}, {0, 0, 0}, B.cap_frames, B.cap_tiles};
+  for (int o = 0; o < 3; o++) {
+    if (n_tiles[o] == 0) continue;
+    const int fit = lpa_batch_ctas_per_sm(o, comp, cfg.tile_h, smem[o]);
+    if (fit < 1)
+      return fail(HDR_E_UNSUPPORTED, "the order-%d batched kernel does not fit an SM with %u bytes of shared memory", o,
+                  smem[o]);
+    const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, fit) : fit;
+    // Small segments get a power-of-two grid (extra CTAs find no tile and leave), so the number
+    // of recorded graphs stays small when the tile counts change from launch to launch.
+    int grid = sms * per_sm;
+    if (n_tiles[o] < grid) {
+      int g = 1;
+      while (g < n_tiles[o]) g *= 2;
+      grid = std::min(grid, g);
+    }
+    key.grid[o] = grid;
+    key.smem[o] = smem[o];
+  }
   auto it = B.graphs.find(key);
   if (it == B.graphs.end()) {
-    // record: tables from pinned staging, counter to zero, one persistent kernel
-    cudaStream_t cap;
-    CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(B.frames_dev, B.frames_host, B.cap_frames * sizeof(LpaLaunch), cudaMemcpyHostToDevice, cap);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(B.tiles_dev, B.tiles_host, B.cap_tiles * sizeof(int2), cudaMemcpyHostToDevice, cap);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(B.ntiles_dev, B.ntiles_host, sizeof(int), cudaMemcpyHostToDevice, cap);
-    if (e == cudaSuccess) e = cudaMemsetAsync(B.counter_dev, 0, sizeof(unsigned int), cap);
-    if (e == cudaSuccess) {
-      LpaBatch lb{B.frames_dev, B.tiles_dev, B.ntiles_dev, B.counter_dev, smem};
-      e = lpa_launch_batch(lb, comp, cfg.tile_h, grid, cap);
+    // record: tables from this buffer's pinned staging, counters to zero, then one persistent
+    // kernel per order present, as parallel branches so that one order's tail overlaps the next
+    cudaStream_t cap = nullptr, side[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    for (int o = 0; o < 3 && e == cudaSuccess; o++) {
+      e = cudaStreamCreateWithFlags(&side[o], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[o], cudaEventDisableTiming);
     }
-    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
-    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    cudaGraph_t g = nullptr;
+    bool capturing = false;
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      capturing = e == cudaSuccess;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(B.frames_dev, S.frames, B.cap_frames * sizeof(LpaLaunch), cudaMemcpyHostToDevice, cap);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(B.tiles_dev, S.tiles, B.cap_tiles * sizeof(int2), cudaMemcpyHostToDevice, cap);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.bounds_dev, S.bounds, 4 * sizeof(int), cudaMemcpyHostToDevice, cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.counters_dev, 0, 3 * sizeof(unsigned int), cap);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, cap);
+    for (int o = 0; o < 3 && e == cudaSuccess; o++) {
+      if (!key.grid[o]) continue;
+      e = cudaStreamWaitEvent(side[o], fork, 0);
+      LpaBatch lb{B.frames_dev, B.tiles_dev, B.bounds_dev, B.counters_dev, smem[o]};
+      if (e == cudaSuccess) e = lpa_launch_batch(o, lb, comp, cfg.tile_h, key.grid[o], side[o]);
+      if (e == cudaSuccess) e = cudaEventRecord(join[o], side[o]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join[o], 0);
+    }
+    if (capturing) {
+      cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+      if (e == cudaSuccess) e = e2;
+    }
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
     if (g) cudaGraphDestroy(g);
-    cudaStreamDestroy(cap);
+    for (int o = 0; o < 3; o++) {
+      if (side[o]) cudaStreamDestroy(side[o]);
+      if (join[o]) cudaEventDestroy(join[o]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cap) cudaStreamDestroy(cap);
     if (e != cudaSuccess) return fail(HDR_E_CUDA, "recording the batch graph failed: %s", cudaGetErrorString(e));
     it = B.graphs.emplace(key, exec).first;
   }
+  // The device tables are shared by both buffers: a launch on another stream must not overwrite
+  // them while the previous launch still runs.
+  const BatchState::Staging &prev = B.stage[buf ^ 1];
+  if (prev.pending) CUDA_TRY(cudaStreamWaitEvent(stream, prev.done, 0));
   CUDA_TRY(cudaGraphLaunch(it->second, stream));
-  CUDA_TRY(cudaEventRecord(B.tables_read, stream));
-  B.pending = true;
+  CUDA_TRY(cudaEventRecord(S.done, stream));
+  S.pending = true;
+  B.cur = buf ^ 1;
   return HDR_OK;
+}
+
+int lpa_ctx_device(const hdr_ctx *ctx) { return ctx->device; }
+int lpa_ctx_rig_sensors(const hdr_ctx *ctx, int rig_id) {
+  return (rig_id >= 0 && rig_id < kMaxRigs) ? ctx->rigs[rig_id].n : 0;
+}
+void lpa_ctx_rig_sizes(const hdr_ctx *ctx, int rig_id, int *pitch, int *height) {
+  const Rig &r = ctx->rigs[rig_id];
+  for (int s = 0; s < r.n; s++) {
+    pitch[s] = r.s[s].d.pitch_elems;
+    height[s] = r.s[s].d.height;
+  }
+}
+hdr_status lpa_fail(hdr_status st, const char *msg) { return fail(st, "%s", msg); }
+hdr_status lpa_check_params(const hdr_params *p) { return check_params(p); }
+hdr_status lpa_take_status(hdr_ctx *ctx) {
+  unsigned int word = 0;
+  CUDA_TRY(cudaMemcpy(&word, ctx->status, sizeof(word), cudaMemcpyDeviceToHost));
+  if (word) CUDA_TRY(cudaMemset(ctx->status, 0, sizeof(word)));
+  if (word & LPA_ERR_TIMEOUT) return fail(HDR_E_TIMEOUT, "a bounded device wait ran out (status 0x%x)", word);
+  if (word & LPA_ERR_BOUNDS) return fail(HDR_E_INTERNAL, "a window left the staged footprint (status 0x%x)", word);
+  return HDR_OK;
+}
+
+extern "C" hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames,
+                                            const hdr_batch_config *cfg_in, void *cuda_stream) {
+  return lpa_batch_run(ctx, n_frames, frames, nullptr, cfg_in, (cudaStream_t)cuda_stream);
 }
 
 extern "C" hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, hdr_batch_config *best,

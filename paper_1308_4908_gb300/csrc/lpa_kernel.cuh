@@ -603,32 +603,36 @@ __global__ void __launch_bounds__(LPA_TILE *TH, 16 / TH * 2) lpa_reconstruct(con
   process_tile<ORDER, COMP, DIAG, TH, false>(L, blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0, anchors);
 }
 
-// Many frames in one launch: persistent CTAs take tiles from a device-wide counter over the
-// tile list (frame index, tile index), most expensive frames first as ordered by the host.
-template <bool COMP, int TH>
-__global__ void __launch_bounds__(LPA_TILE *TH, 16 / TH * 2) lpa_reconstruct_batch(const __grid_constant__ LpaBatch B) {
+// Resident CTAs per SM the persistent kernel is compiled for (register cap 64K / (threads x this)):
+// the lower orders need fewer registers, so they can keep more warps resident to hide staging.
+template <int ORDER, int TH>
+struct BatchOccupancy {
+  static constexpr int value = (ORDER == 0 ? 4 : ORDER == 1 ? 3 : 2) * 16 / TH;
+};
+
+// Many frames in one launch, one kernel per polynomial order: persistent CTAs take tiles from
+// the order's device-wide counter over its segment of the tile list (frame index, tile index),
+// most expensive frames first as ordered by the host.
+template <int ORDER, bool COMP, int TH>
+__global__ void __launch_bounds__(LPA_TILE *TH, (BatchOccupancy<ORDER, TH>::value)) lpa_reconstruct_batch(const __grid_constant__ LpaBatch B) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
   __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ int next;
   if (threadIdx.x == 0) mbar_init(&mbar, 1);
-  const int n_tiles = *B.n_tiles;
+  const int t_end = B.bounds[ORDER + 1];
+  const int t_begin = B.bounds[ORDER];
   uint32_t phase = 0;
   for (;;) {
     __syncthreads();  // every thread is done with the previous tile's staging
-    if (threadIdx.x == 0) next = (int)atomicAdd(B.counter, 1u);
+    if (threadIdx.x == 0) next = t_begin + (int)atomicAdd(B.counters + ORDER, 1u);
     __syncthreads();
     const int t = next;
-    if (t >= n_tiles) break;
+    if (t >= t_end) break;
     const int2 ft = B.tiles[t];
-    const LpaLaunch &F = B.frames[ft.x];
-    bool ok;
-    switch (F.order) {
-      case 0: ok = process_tile<0, COMP, false, TH, true>(F, ft.y, smem, &mbar, phase, fp_x0, fp_y0, anchors); break;
-      case 1: ok = process_tile<1, COMP, false, TH, true>(F, ft.y, smem, &mbar, phase, fp_x0, fp_y0, anchors); break;
-      default: ok = process_tile<2, COMP, false, TH, true>(F, ft.y, smem, &mbar, phase, fp_x0, fp_y0, anchors); break;
-    }
+    const bool ok = process_tile<ORDER, COMP, false, TH, true>(B.frames[ft.x], ft.y, smem, &mbar, phase, fp_x0,
+                                                               fp_y0, anchors);
     if (!__syncthreads_and(ok)) break;
     phase ^= 1u;
   }

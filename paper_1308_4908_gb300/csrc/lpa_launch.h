@@ -58,12 +58,14 @@ struct LpaLaunch {
   int tile_h;                    // tile height the plan was made for
 };
 
-// Several frames in one persistent launch. The tile list, its length and the counter live in
-// device memory so that a captured graph of the launch stays valid when the frames change.
+// Several frames in one graph launch: the tile list is grouped by polynomial order and each
+// order's persistent kernel takes tiles from its own segment. The tile list, the segment bounds
+// and the counters live in device memory so that a recorded graph stays valid when the frames
+// change.
 struct LpaBatch {
   const LpaLaunch *frames;       // [n_frames] (device)
   const int2 *tiles;             // [n_tiles] (frame index, tile index within the frame) (device)
-  const int *n_tiles;            // (device)
-  unsigned int *counter;         // tile counter, zero at launch (device)
-  uint32_t smem_bytes;           // max over the frames
+  const int *bounds;             // [4]: the tiles of order M are [bounds[M], bounds[M+1]) (device)
+  unsigned int *counters;        // [3] tile counters, zero at launch (device)
+  uint32_t smem_bytes;           // max over the frames of the kernel's order
 };

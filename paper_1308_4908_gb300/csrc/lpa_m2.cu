@@ -1,4 +1,5 @@
-// Instantiations of the single-frame reconstruction kernel for polynomial order M = 2.
+// Instantiations of the single-frame and the persistent many-frame reconstruction kernels for
+// polynomial order M = 2.
 #include "lpa_dispatch.h"
 #include "lpa_kernel.cuh"
 
@@ -19,4 +20,32 @@ static cudaError_t launch_th(const LpaLaunch &L, bool comp, bool diag, cudaStrea
 
 cudaError_t lpa_launch_order2(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st) {
   return L.tile_h == 8 ? launch_th<8>(L, comp, diag, st) : launch_th<16>(L, comp, diag, st);
+}
+
+template <bool COMP, int TH>
+static cudaError_t launch_batch_t(const LpaBatch &B, int grid, cudaStream_t st) {
+  auto k = lpa::lpa_reconstruct_batch<2, COMP, TH>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem_bytes);
+  if (e != cudaSuccess) return e;
+  k<<<grid, LPA_TILE * TH, B.smem_bytes, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t lpa_launch_batch_order2(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st) {
+  if (tile_h == 8) return comp ? launch_batch_t<true, 8>(B, grid, st) : launch_batch_t<false, 8>(B, grid, st);
+  return comp ? launch_batch_t<true, 16>(B, grid, st) : launch_batch_t<false, 16>(B, grid, st);
+}
+
+template <bool COMP, int TH>
+static int fit_t(uint32_t smem_bytes) {
+  auto k = lpa::lpa_reconstruct_batch<2, COMP, TH>;
+  int n = 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, LPA_TILE * TH, smem_bytes) != cudaSuccess) return 0;
+  return n;
+}
+
+int lpa_batch_ctas_per_sm_order2(bool comp, int tile_h, uint32_t smem_bytes) {
+  if (tile_h == 8) return comp ? fit_t<true, 8>(smem_bytes) : fit_t<false, 8>(smem_bytes);
+  return comp ? fit_t<true, 16>(smem_bytes) : fit_t<false, 16>(smem_bytes);
 }

@@ -1,0 +1,497 @@
+// Serving loop of the C ABI (hdr_server_*): memory-based admission, copy streams and tile-level
+// continuous batching over the persistent batched kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "hdr_lpa.h"
+#include "lpa_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+// First-fit allocator over one device allocation.
+class Pool {
+ public:
+  void init(unsigned char *base, size_t bytes) {
+    base_ = base;
+    free_.clear();
+    free_[0] = bytes;
+  }
+  bool alloc(size_t bytes, size_t *off) {
+    bytes = align256(bytes);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      const size_t o = it->first, rest = it->second - bytes;
+      free_.erase(it);
+      if (rest) free_[o + bytes] = rest;
+      *off = o;
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    auto it = free_.emplace(off, align256(bytes)).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  unsigned char *base() const { return base_; }
+
+ private:
+  unsigned char *base_ = nullptr;
+  std::map<size_t, size_t> free_;
+};
+
+enum class State { Queued, CopyIn, Ready, CopyOut, Done };
+
+struct Job {
+  uint64_t ticket = 0;
+  hdr_request req{};
+  State state = State::Queued;
+  Clock::time_point t_submit, t_admit, t_done;
+  size_t off = 0, bytes = 0;
+  int n_sensors = 0;
+  const uint16_t *raw_dev[HDR_MAX_SENSORS] = {};
+  size_t raw_bytes[HDR_MAX_SENSORS] = {};
+  void *out_dev = nullptr;
+  size_t out_bytes = 0;
+  uint8_t *choice_dev = nullptr;
+  size_t choice_bytes = 0;
+  int tiles = 0, next_tile = 0, steps = 0;
+  int inflight = 0;                 // launched steps holding tiles of this frame, not yet complete
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  hdr_status status = HDR_OK;       // final status (State::Done)
+  hdr_status error = HDR_OK;        // first failure seen; finished once nothing is in flight
+  std::string message;
+};
+
+struct Step {
+  cudaEvent_t ev = nullptr;
+  std::vector<uint64_t> members;
+};
+
+}  // namespace
+
+struct hdr_server {
+  hdr_ctx *ctx = nullptr;
+  hdr_server_config cfg{};
+  int device = 0;
+  void *pool_mem = nullptr;
+  Pool pool;
+  cudaStream_t compute = nullptr, h2d = nullptr, d2h = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  std::deque<uint64_t> queue;        // submitted, not admitted (arrival order)
+  std::vector<uint64_t> active;      // admitted, not done (admission order)
+  std::map<uint64_t, Job> jobs;
+  std::deque<Step> steps;            // launched, not yet observed complete
+  std::vector<cudaEvent_t> spare_events;
+  // statistics
+  std::vector<double> total_ms;
+  double queue_ms_sum = 0.0;
+  uint64_t submitted = 0, n_steps = 0, out_px = 0;
+  bool have_first = false;
+  Clock::time_point t_first, t_last;
+  std::thread worker;
+
+  cudaEvent_t event() {
+    if (!spare_events.empty()) {
+      cudaEvent_t e = spare_events.back();
+      spare_events.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return e;
+  }
+  void recycle(cudaEvent_t &e) {
+    if (e) spare_events.push_back(e);
+    e = nullptr;
+  }
+
+
+  void finish(Job &j, hdr_status st) {
+    j.status = st;
+    if (st != HDR_OK && j.message.empty()) j.message = hdr_last_error();
+    j.state = State::Done;
+    j.t_done = Clock::now();
+    pool.release(j.off, j.bytes);
+    recycle(j.ev_in);
+    recycle(j.ev_out);
+    active.erase(std::remove(active.begin(), active.end(), j.ticket), active.end());
+    if (st == HDR_OK) {
+      total_ms.push_back(ms_between(j.t_submit, j.t_done));
+      queue_ms_sum += ms_between(j.t_submit, j.t_admit);
+      out_px += (uint64_t)j.req.params.out_w * j.req.params.out_h;
+      t_last = j.t_done;
+    }
+    cv_done.notify_all();
+  }
+
+  // Record a failure; the frame's memory is released only once no launched step still uses it.
+  void fail_job(Job &j, hdr_status st) {
+    if (j.state == State::Done) return;
+    if (j.error == HDR_OK) {
+      j.error = st;
+      j.message = hdr_last_error();
+    }
+    if (j.inflight == 0) finish(j, j.error);
+  }
+
+  // Admit queued frames in arrival order while a slot and pool memory are free.
+  bool admit() {
+    bool did = false;
+    while (!queue.empty() && (int)active.size() < cfg.max_frames) {
+      Job &j = jobs[queue.front()];
+      size_t off = 0;
+      if (!pool.alloc(j.bytes, &off)) break;
+      queue.pop_front();
+      j.off = off;
+      unsigned char *p = pool.base() + off;
+      size_t o = 0;
+      for (int s = 0; s < j.n_sensors; s++) {
+        j.raw_dev[s] = reinterpret_cast<const uint16_t *>(p + o);
+        o += align256(j.raw_bytes[s]);
+      }
+      j.out_dev = p + o;
+      o += align256(j.out_bytes);
+      j.choice_dev = j.req.choice_host ? reinterpret_cast<uint8_t *>(p + o) : nullptr;
+      j.t_admit = Clock::now();
+      if (!have_first) {
+        have_first = true;
+        t_first = j.t_admit;
+      }
+      j.ev_in = event();
+      cudaError_t e = j.ev_in ? cudaSuccess : cudaErrorMemoryAllocation;
+      for (int s = 0; s < j.n_sensors && e == cudaSuccess; s++)
+        e = cudaMemcpyAsync(const_cast<uint16_t *>(j.raw_dev[s]), j.req.raw_host[s], j.raw_bytes[s],
+                            cudaMemcpyHostToDevice, h2d);
+      if (e == cudaSuccess) e = cudaEventRecord(j.ev_in, h2d);
+      active.push_back(j.ticket);
+      if (e != cudaSuccess) {
+        lpa_fail(HDR_E_CUDA, cudaGetErrorString(e));
+        finish(j, HDR_E_CUDA);
+      } else {
+        j.state = State::CopyIn;
+      }
+      did = true;
+    }
+    return did;
+  }
+
+  bool poll_inputs() {
+    bool did = false;
+    for (uint64_t t : active) {
+      Job &j = jobs[t];
+      if (j.state == State::CopyIn && cudaEventQuery(j.ev_in) == cudaSuccess) {
+        j.state = State::Ready;
+        did = true;
+      }
+    }
+    for (size_t k = 0; k < active.size();) {   // empty outputs: nothing to compute or copy back
+      Job &j = jobs[active[k]];
+      if (j.state == State::Ready && j.tiles == 0) {
+        finish(j, HDR_OK);                       // removes it from active
+      } else {
+        k++;
+      }
+    }
+    return did;
+  }
+
+  // Launch one batched step over pending tiles of ready frames (admission order, within budget).
+  // Two steps may be queued: the next one is prepared while the device runs the current one.
+  bool launch_step() {
+    if (steps.size() >= 2) return false;
+    std::vector<hdr_frame> frames;
+    std::vector<int2> ranges;
+    Step st;
+    long budget = cfg.step_tiles > 0 ? cfg.step_tiles : (1L << 40);
+    for (uint64_t t : active) {
+      Job &j = jobs[t];
+      if (j.state != State::Ready || j.error || j.next_tile >= j.tiles || budget <= 0) continue;
+      const int take = (int)std::min<long>(budget, j.tiles - j.next_tile);
+      hdr_frame f{};
+      f.rig_id = j.req.rig_id;
+      f.params = &j.req.params;
+      for (int s = 0; s < j.n_sensors; s++) f.raw_dev[s] = j.raw_dev[s];
+      f.out_dev = j.out_dev;
+      f.choice_dev = j.choice_dev;
+      frames.push_back(f);
+      ranges.push_back(make_int2(j.next_tile, j.next_tile + take));
+      budget -= take;
+      st.members.push_back(t);
+    }
+    if (frames.empty()) return false;
+    hdr_status s = lpa_batch_run(ctx, (int)frames.size(), frames.data(), ranges.data(), &cfg.batch, compute);
+    st.ev = event();
+    if (s == HDR_OK && !st.ev) s = lpa_fail(HDR_E_CUDA, "cudaEventCreate failed");
+    if (s == HDR_OK) {
+      cudaError_t e = cudaEventRecord(st.ev, compute);
+      if (e != cudaSuccess) s = lpa_fail(HDR_E_CUDA, cudaGetErrorString(e));
+    }
+    if (s != HDR_OK) {
+      for (uint64_t t : st.members) fail_job(jobs[t], s);
+      recycle(st.ev);
+      return true;
+    }
+    for (size_t k = 0; k < st.members.size(); k++) {
+      Job &j = jobs[st.members[k]];
+      j.next_tile = ranges[k].y;
+      j.steps++;
+      j.inflight++;
+    }
+    n_steps++;
+    steps.push_back(st);
+    return true;
+  }
+
+  // A completed step: check the device status, then copy finished frames back.
+  bool poll_steps() {
+    bool did = false;
+    while (!steps.empty() && cudaEventQuery(steps.front().ev) == cudaSuccess) {
+      Step st = steps.front();
+      steps.pop_front();
+      for (uint64_t t : st.members) jobs[t].inflight--;
+      hdr_status dev = lpa_take_status(ctx);
+      if (dev != HDR_OK) {
+        // the word may have been set by this step or the one queued behind it: fail both
+        for (uint64_t t : st.members) fail_job(jobs[t], dev);
+        for (const Step &q : steps)
+          for (uint64_t t : q.members) fail_job(jobs[t], dev);
+      }
+      for (uint64_t t : st.members) {
+        Job &j = jobs[t];
+        if (j.state == State::Done) continue;
+        if (j.error) {
+          if (j.inflight == 0) finish(j, j.error);
+          continue;
+        }
+        if (j.next_tile < j.tiles || j.inflight > 0) continue;
+        j.ev_out = event();
+        cudaError_t e = j.ev_out ? cudaStreamWaitEvent(d2h, st.ev, 0) : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(j.req.out_host, j.out_dev, j.out_bytes, cudaMemcpyDeviceToHost, d2h);
+        if (e == cudaSuccess && j.choice_dev)
+          e = cudaMemcpyAsync(j.req.choice_host, j.choice_dev, j.choice_bytes, cudaMemcpyDeviceToHost, d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(j.ev_out, d2h);
+        if (e != cudaSuccess) {
+          lpa_fail(HDR_E_CUDA, cudaGetErrorString(e));
+          fail_job(j, HDR_E_CUDA);
+        } else {
+          j.state = State::CopyOut;
+        }
+      }
+      recycle(st.ev);
+      did = true;
+    }
+    return did;
+  }
+
+  bool poll_outputs() {
+    bool did = false;
+    std::vector<uint64_t> act = active;
+    for (uint64_t t : act) {
+      Job &j = jobs[t];
+      if (j.state == State::CopyOut && cudaEventQuery(j.ev_out) == cudaSuccess) {
+        finish(j, HDR_OK);
+        did = true;
+      }
+    }
+    return did;
+  }
+
+  void run() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lock(mu);
+    for (;;) {
+      if (stop && queue.empty() && active.empty() && steps.empty()) break;
+      bool did = admit();
+      did |= poll_inputs();
+      did |= poll_steps();
+      did |= poll_outputs();
+      did |= launch_step();
+      if (!did) cv_work.wait_for(lock, std::chrono::microseconds(50));
+    }
+  }
+};
+
+extern "C" {
+
+hdr_status hdr_server_create(hdr_ctx *ctx, const hdr_server_config *cfg, hdr_server **out) {
+  if (!ctx || !cfg || !out) return lpa_fail(HDR_E_INVALID, "ctx, cfg and out must be non-NULL");
+  *out = nullptr;
+  if (cfg->max_frames < 1) return lpa_fail(HDR_E_INVALID, "max_frames must be >= 1");
+  if (cfg->pool_bytes < 4096) return lpa_fail(HDR_E_INVALID, "pool_bytes too small");
+  if (cfg->step_tiles < 0) return lpa_fail(HDR_E_INVALID, "step_tiles must be >= 0");
+  if (cfg->batch.tile_h != 0 && cfg->batch.tile_h != 8 && cfg->batch.tile_h != 16)
+    return lpa_fail(HDR_E_INVALID, "batch.tile_h must be 0, 8 or 16");
+  if (cfg->batch.ctas_per_sm < 0 || cfg->batch.ctas_per_sm > 8)
+    return lpa_fail(HDR_E_INVALID, "batch.ctas_per_sm must be in [0, 8]");
+  hdr_server *s = new (std::nothrow) hdr_server();
+  if (!s) return lpa_fail(HDR_E_NOMEM, "host allocation failed");
+  s->ctx = ctx;
+  s->cfg = *cfg;
+  if (s->cfg.batch.tile_h == 0) s->cfg.batch.tile_h = 16;   // tile counts are fixed at submission
+  s->device = lpa_ctx_device(ctx);
+  cudaError_t e = cudaSetDevice(s->device);
+  if (e == cudaSuccess) e = cudaMalloc(&s->pool_mem, cfg->pool_bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    hdr_status st = e == cudaErrorMemoryAllocation ? HDR_E_NOMEM : HDR_E_CUDA;
+    cudaFree(s->pool_mem);
+    if (s->compute) cudaStreamDestroy(s->compute);
+    if (s->h2d) cudaStreamDestroy(s->h2d);
+    if (s->d2h) cudaStreamDestroy(s->d2h);
+    delete s;
+    return lpa_fail(st, cudaGetErrorString(e));
+  }
+  s->pool.init(static_cast<unsigned char *>(s->pool_mem), cfg->pool_bytes);
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return HDR_OK;
+}
+
+hdr_status hdr_submit(hdr_server *srv, const hdr_request *req, uint64_t *ticket) {
+  if (!srv || !req || !ticket) return lpa_fail(HDR_E_INVALID, "srv, req and ticket must be non-NULL");
+  const int ns = lpa_ctx_rig_sensors(srv->ctx, req->rig_id);
+  if (ns == 0) return lpa_fail(HDR_E_INVALID, "rig is not defined");
+  hdr_status st = lpa_check_params(&req->params);
+  if (st) return st;
+  if (!req->out_host) return lpa_fail(HDR_E_INVALID, "out_host is NULL");
+  for (int s = 0; s < ns; s++)
+    if (!req->raw_host[s]) return lpa_fail(HDR_E_INVALID, "raw_host pointer is NULL");
+  Job j;
+  j.req = *req;
+  j.n_sensors = ns;
+  int pitch[HDR_MAX_SENSORS], height[HDR_MAX_SENSORS];
+  lpa_ctx_rig_sizes(srv->ctx, req->rig_id, pitch, height);
+  size_t bytes = 0;
+  for (int s = 0; s < ns; s++) {
+    j.raw_bytes[s] = (size_t)pitch[s] * height[s] * 2;
+    bytes += align256(j.raw_bytes[s]);
+  }
+  const size_t px = (size_t)req->params.out_w * req->params.out_h * 3;
+  j.out_bytes = px * (req->params.out_dtype ? 2 : 4);
+  j.choice_bytes = req->choice_host ? px : 0;
+  bytes += align256(j.out_bytes) + align256(j.choice_bytes);
+  j.bytes = std::max<size_t>(bytes, 256);
+  if (j.bytes > srv->cfg.pool_bytes) return lpa_fail(HDR_E_UNSUPPORTED, "the frame needs more memory than the pool holds");
+  const int th = srv->cfg.batch.tile_h;
+  j.tiles = ((req->params.out_w + 15) / 16) * ((req->params.out_h + th - 1) / th);
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (srv->stop) return lpa_fail(HDR_E_BUSY, "the server is stopping");
+    j.ticket = srv->next_ticket++;
+    j.t_submit = Clock::now();
+    const uint64_t t = j.ticket;
+    srv->jobs.emplace(t, j);
+    srv->queue.push_back(t);
+    srv->submitted++;
+    *ticket = t;
+  }
+  srv->cv_work.notify_one();
+  return HDR_OK;
+}
+
+hdr_status hdr_poll(hdr_server *srv, uint64_t ticket, int32_t timeout_ms, hdr_result *result) {
+  if (!srv) return lpa_fail(HDR_E_INVALID, "srv is NULL");
+  std::unique_lock<std::mutex> lock(srv->mu);
+  auto done = [&] {
+    auto it = srv->jobs.find(ticket);
+    return it == srv->jobs.end() || it->second.state == State::Done;
+  };
+  if (timeout_ms < 0) srv->cv_done.wait(lock, done);
+  else srv->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms), done);
+  auto it = srv->jobs.find(ticket);
+  if (it == srv->jobs.end()) return lpa_fail(HDR_E_INVALID, "unknown ticket (or its result was already returned)");
+  Job &j = it->second;
+  if (j.state != State::Done) return lpa_fail(HDR_E_BUSY, "the request has not finished");
+  hdr_status st = j.status;
+  if (result) {
+    result->status = st;
+    result->queue_ms = ms_between(j.t_submit, j.t_admit);
+    result->total_ms = ms_between(j.t_submit, j.t_done);
+    result->steps = j.steps;
+  }
+  const std::string msg = "the request failed: " + j.message;
+  srv->jobs.erase(it);
+  if (st == HDR_OK) return HDR_OK;
+  return lpa_fail(st, msg.c_str());
+}
+
+hdr_status hdr_server_stats_get(hdr_server *srv, hdr_server_stats *stats) {
+  if (!srv || !stats) return lpa_fail(HDR_E_INVALID, "srv and stats must be non-NULL");
+  std::lock_guard<std::mutex> lock(srv->mu);
+  memset(stats, 0, sizeof(*stats));
+  std::vector<double> v = srv->total_ms;
+  stats->completed = v.size();
+  stats->submitted = srv->submitted;
+  stats->steps = srv->n_steps;
+  stats->output_pixels = srv->out_px;
+  if (!v.empty()) {
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5))]; };
+    stats->p50_ms = pct(0.5);
+    stats->p99_ms = pct(0.99);
+    stats->max_ms = v.back();
+    stats->mean_queue_ms = srv->queue_ms_sum / (double)v.size();
+    stats->busy_s = std::chrono::duration<double>(srv->t_last - srv->t_first).count();
+  }
+  return HDR_OK;
+}
+
+void hdr_server_destroy(hdr_server *srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_work.notify_all();
+  if (srv->worker.joinable()) srv->worker.join();
+  cudaSetDevice(srv->device);
+  cudaStreamSynchronize(srv->compute);
+  cudaStreamSynchronize(srv->h2d);
+  cudaStreamSynchronize(srv->d2h);
+  for (auto &kv : srv->jobs) {
+    if (kv.second.ev_in) cudaEventDestroy(kv.second.ev_in);
+    if (kv.second.ev_out) cudaEventDestroy(kv.second.ev_out);
+  }
+  for (cudaEvent_t e : srv->spare_events) cudaEventDestroy(e);
+  cudaStreamDestroy(srv->compute);
+  cudaStreamDestroy(srv->h2d);
+  cudaStreamDestroy(srv->d2h);
+  cudaFree(srv->pool_mem);
+  delete srv;
+}
+
+}  // extern "C"

@@ -51,6 +51,28 @@ class hdr_batch_config(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("cost_order", ctypes.c_int32)]
 
 
+class hdr_server_config(ctypes.Structure):
+    _fields_ = [("max_frames", ctypes.c_int32), ("pool_bytes", ctypes.c_uint64), ("step_tiles", ctypes.c_int32),
+                ("batch", hdr_batch_config)]
+
+
+class hdr_request(ctypes.Structure):
+    _fields_ = [("rig_id", ctypes.c_int32), ("params", hdr_params),
+                ("raw_host", ctypes.c_void_p * HDR_MAX_SENSORS), ("out_host", ctypes.c_void_p),
+                ("choice_host", ctypes.c_void_p), ("stream_id", ctypes.c_int32)]
+
+
+class hdr_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("queue_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("steps", ctypes.c_int32)]
+
+
+class hdr_server_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("submitted", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_queue_ms", ctypes.c_double),
+                ("steps", ctypes.c_uint64), ("output_pixels", ctypes.c_uint64), ("busy_s", ctypes.c_double)]
+
+
 class HdrError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -89,10 +111,17 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.hdr_reconstruct_noalloc.argtypes = [ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
     lib.hdr_reconstruct_batch.argtypes = [_P, ctypes.c_int32, _P, _P, _P]
     lib.hdr_tune_batch.argtypes = [_P, ctypes.c_int32, _P, _P, _P]
+    lib.hdr_server_create.argtypes = [_P, _P, _P]
+    lib.hdr_submit.argtypes = [_P, _P, _P]
+    lib.hdr_poll.argtypes = [_P, ctypes.c_uint64, ctypes.c_int32, _P]
+    lib.hdr_server_stats_get.argtypes = [_P, _P]
+    lib.hdr_server_destroy.argtypes = [_P]
+    lib.hdr_server_destroy.restype = None
     lib.hdr_last_error.argtypes = []
     lib.hdr_last_error.restype = ctypes.c_char_p
     for name in ("hdr_create", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_levels", "hdr_reconstruct_host",
-                 "hdr_check", "hdr_reconstruct_noalloc", "hdr_reconstruct_batch", "hdr_tune_batch"):
+                 "hdr_check", "hdr_reconstruct_noalloc", "hdr_reconstruct_batch", "hdr_tune_batch",
+                 "hdr_server_create", "hdr_submit", "hdr_poll", "hdr_server_stats_get"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -184,6 +213,38 @@ def hdr_reconstruct_noalloc(device: int, sensors: Sequence[hdr_sensor_desc], par
     _check(load().hdr_reconstruct_noalloc(int(device), len(sensors), arr, ctypes.byref(params), _ptr_array(raw_dev),
                                           ctypes.c_void_p(out_dev), ctypes.c_void_p(choice_dev),
                                           ctypes.c_void_p(stream)))
+
+
+def hdr_server_create(ctx: int, cfg: hdr_server_config) -> int:
+    h = ctypes.c_void_p()
+    _check(load().hdr_server_create(ctypes.c_void_p(ctx), ctypes.byref(cfg), ctypes.byref(h)))
+    return int(h.value)
+
+
+def hdr_submit(srv: int, req: hdr_request) -> int:
+    t = ctypes.c_uint64()
+    _check(load().hdr_submit(ctypes.c_void_p(srv), ctypes.byref(req), ctypes.byref(t)))
+    return int(t.value)
+
+
+def hdr_poll(srv: int, ticket: int, timeout_ms: int = -1) -> Optional[hdr_result]:
+    """The request's result, or None while it is still running (HDR_E_BUSY)."""
+    r = hdr_result()
+    st = load().hdr_poll(ctypes.c_void_p(srv), ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(r))
+    if st == HDR_E_BUSY:
+        return None
+    _check(st)
+    return r
+
+
+def hdr_server_stats_get(srv: int) -> hdr_server_stats:
+    s = hdr_server_stats()
+    _check(load().hdr_server_stats_get(ctypes.c_void_p(srv), ctypes.byref(s)))
+    return s
+
+
+def hdr_server_destroy(srv: int) -> None:
+    load().hdr_server_destroy(ctypes.c_void_p(srv))
 
 
 # ------------------------------------------------------------------ marshalling helpers
@@ -307,3 +368,56 @@ class Context:
 
     def check(self, stream=None):
         hdr_check(self.handle, self._stream(stream))
+
+
+class Server:
+    """Request loop over one Context (see hdr_server_create). Host arrays given to submit() are kept
+    alive here until their result has been polled."""
+
+    def __init__(self, ctx: Context, max_frames: int = 16, pool_bytes: int = 4 << 30, step_tiles: int = 0,
+                 batch: Optional[hdr_batch_config] = None):
+        cfg = hdr_server_config()
+        cfg.max_frames, cfg.pool_bytes, cfg.step_tiles = int(max_frames), int(pool_bytes), int(step_tiles)
+        cfg.batch = batch if batch is not None else hdr_batch_config(0, 0, 0)
+        self.ctx = ctx
+        self.handle = hdr_server_create(ctx.handle, cfg)
+        self._held = {}
+
+    def submit(self, rig_id: int, params, raws_host: Sequence[np.ndarray], out_host: np.ndarray,
+               choice_host: Optional[np.ndarray] = None, stream_id: int = 0) -> int:
+        req = hdr_request()
+        req.rig_id = int(rig_id)
+        req.params = params if isinstance(params, hdr_params) else params_struct(params)
+        for i, r in enumerate(raws_host):
+            req.raw_host[i] = int(r.ctypes.data)
+        req.out_host = out_host.ctypes.data
+        req.choice_host = choice_host.ctypes.data if choice_host is not None else None
+        req.stream_id = int(stream_id)
+        t = hdr_submit(self.handle, req)
+        self._held[t] = (list(raws_host), out_host, choice_host)
+        return t
+
+    def poll(self, ticket: int, timeout_ms: int = -1) -> Optional[hdr_result]:
+        try:
+            r = hdr_poll(self.handle, ticket, timeout_ms)
+        except HdrError:
+            self._held.pop(ticket, None)
+            raise
+        if r is not None:
+            self._held.pop(ticket, None)
+        return r
+
+    def stats(self) -> hdr_server_stats:
+        return hdr_server_stats_get(self.handle)
+
+    def close(self):
+        if self.handle:
+            hdr_server_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -228,8 +228,8 @@ class Frame:
 def _build_frame(seed: int, n_sensors: int, w: int, h: int, nds: Sequence[float],
                  trans: float, rot_deg: float, scale_eps: float, params: Params,
                  name: str, noise: bool = True, scene: Optional[Scene] = None,
-                 frame_index: int = 0) -> Frame:
-    r = _rng(seed, 0, frame_index)
+                 frame_index: int = 0, rig_index: Optional[int] = None) -> Frame:
+    r = _rng(seed, 0, frame_index if rig_index is None else rig_index)
     scene = scene if scene is not None else make_scene(seed, w, h)
     sensors = []
     for s in range(n_sensors):
@@ -273,10 +273,10 @@ BATCH_SIZES = ((512, 512), (1280, 720), (1920, 1080), (2048, 2048))
 BATCH_NDS = (1.0, 1 / 8, 1 / 64, 1 / 512)
 
 
-def batching(seed: int = 1004, n_frames: int = 16, size_cap: Optional[int] = None) -> List[Frame]:
-    """16 frames of drawn size, 2-4 sensors, order 0-2, output scale 1 or 1.5; 4 scales with ICI."""
+def batching_specs(seed: int = 1004, n_frames: int = 16, size_cap: Optional[int] = None) -> List[tuple]:
+    """The drawn shape of each batching frame: (seed, k, sensors, w, h, order, output scale)."""
     r = _rng(seed, 5)
-    frames = []
+    specs = []
     for k in range(n_frames):
         w, h = BATCH_SIZES[r.integers(0, len(BATCH_SIZES))]
         if size_cap:
@@ -284,11 +284,21 @@ def batching(seed: int = 1004, n_frames: int = 16, size_cap: Optional[int] = Non
         ns = int(r.integers(2, 5))
         order = int(r.integers(0, 3))
         osc = (1.0, 1.5)[r.integers(0, 2)]
-        ow, oh = int(round(w * osc)), int(round(h * osc))
-        p = Params(order=order, sigmas=PAPER_SCALES, out_w=ow, out_h=oh, out_affine=output_affine(w, h, ow, oh))
-        frames.append(_build_frame(seed * 100 + k, ns, w, h, BATCH_NDS[:ns], 1.5, 0.2, 1e-3, p,
-                                   f"batch{k}-{ns}x{w}x{h}-M{order}-x{osc}", frame_index=k))
-    return frames
+        specs.append((seed, k, ns, int(w), int(h), order, osc))
+    return specs
+
+
+def batching_frame(spec: tuple) -> Frame:
+    seed, k, ns, w, h, order, osc = spec
+    ow, oh = int(round(w * osc)), int(round(h * osc))
+    p = Params(order=order, sigmas=PAPER_SCALES, out_w=ow, out_h=oh, out_affine=output_affine(w, h, ow, oh))
+    return _build_frame(seed * 100 + k, ns, w, h, BATCH_NDS[:ns], 1.5, 0.2, 1e-3, p,
+                        f"batch{k}-{ns}x{w}x{h}-M{order}-x{osc}", frame_index=k)
+
+
+def batching(seed: int = 1004, n_frames: int = 16, size_cap: Optional[int] = None) -> List[Frame]:
+    """16 frames of drawn size, 2-4 sensors, order 0-2, output scale 1 or 1.5; 4 scales with ICI."""
+    return [batching_frame(sp) for sp in batching_specs(seed, n_frames, size_cap)]
 
 
 SERVING_STREAMS = (
@@ -301,11 +311,12 @@ SERVING_STREAMS = (
 
 
 def serving_stream_frame(stream: int, k: int, seed: int = 1005, size_cap: Optional[int] = None) -> Frame:
-    """Frame k of serving stream m (seed 1000*5 + 100*m + k): order 2, 4 scales with ICI."""
+    """Frame k of serving stream m: one scene and one rig geometry per stream (seed 100*seed + m),
+    fresh noise per frame; order 2, 4 scales with ICI. size_cap shrinks the raw and output sizes."""
     w, h, ns, ow, oh = SERVING_STREAMS[stream]
     if size_cap:
         sx, sy = min(1.0, size_cap / w), min(1.0, size_cap / h)
         w, h, ow, oh = int(w * sx) // 8 * 8, int(h * sy) // 2 * 2, int(ow * sx) // 8 * 8, int(oh * sy) // 2 * 2
     p = Params(order=2, sigmas=PAPER_SCALES, out_w=ow, out_h=oh, out_affine=output_affine(w, h, ow, oh))
-    return _build_frame(1000 * 5 + 100 * stream + k, ns, w, h, (1.0, 1 / 16, 1 / 256)[:ns], 1.5, 0.2, 1e-3, p,
-                        f"serve{stream}.{k}", frame_index=k)
+    return _build_frame(100 * seed + stream, ns, w, h, (1.0, 1 / 16, 1 / 256)[:ns], 1.5, 0.2, 1e-3, p,
+                        f"serve{stream}.{k}", frame_index=k, rig_index=0)

@@ -32,7 +32,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for n in ("hdr_create", "hdr_destroy", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_host",
               "hdr_check", "hdr_last_error", "hdr_params_default", "hdr_reconstruct_levels",
-              "hdr_reconstruct_batch", "hdr_tune_batch"):
+              "hdr_reconstruct_batch", "hdr_tune_batch", "hdr_server_create", "hdr_submit", "hdr_poll",
+              "hdr_server_stats_get", "hdr_server_destroy"):
         assert n in names
 
 
@@ -46,26 +47,31 @@ def test_binding_uses_the_c_names(lib):
         assert hasattr(hdr, n), n
 
 
+STRUCTS = ("hdr_sensor_desc", "hdr_params", "hdr_frame", "hdr_batch_config", "hdr_server_config", "hdr_request",
+           "hdr_result", "hdr_server_stats")
+
+
 def test_struct_layout_matches_the_header(tmp_path):
-    """ctypes mirrors of hdr_params / hdr_sensor_desc agree with the C compiler's layout."""
+    """Every ctypes mirror agrees with the C compiler's layout: size and the offset of every field."""
+    lines, want = [], []
+    for name in STRUCTS:
+        cls = getattr(hdr, name)
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        want.append(ctypes.sizeof(cls))
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {field}));')
+            want.append(getattr(cls, field).offset)
     src = tmp_path / "probe.c"
     src.write_text(f'''#include <stdio.h>
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hdr_params), sizeof(hdr_sensor_desc),
-         offsetof(hdr_params, cond_fallback), offsetof(hdr_params, out_affine), offsetof(hdr_params, accum),
-         offsetof(hdr_sensor_desc, affine), offsetof(hdr_sensor_desc, sat_frame), offsetof(hdr_sensor_desc, read_var),
-         sizeof(hdr_frame), offsetof(hdr_frame, out_dev), offsetof(hdr_frame, choice_dev), sizeof(hdr_batch_config));
+{chr(10).join(lines)}
   return 0;
 }}''')
     exe = tmp_path / "probe"
     subprocess.check_call(["gcc", "-std=c11", "-o", str(exe), str(src)])
     got = list(map(int, subprocess.check_output([str(exe)]).split()))
-    P, D, F = hdr.hdr_params, hdr.hdr_sensor_desc, hdr.hdr_frame
-    want = [ctypes.sizeof(P), ctypes.sizeof(D), P.cond_fallback.offset, P.out_affine.offset, P.accum.offset,
-            D.affine.offset, D.sat_frame.offset, D.read_var.offset, ctypes.sizeof(F), F.out_dev.offset,
-            F.choice_dev.offset, ctypes.sizeof(hdr.hdr_batch_config)]
     assert got == want
 
 
