@@ -296,7 +296,8 @@ def run_batching(ctx, frames, dev, reps: int = 10):
                         "(ND 1, 1/8, 1/64, 1/512), order 0-2, output 1x or 1.5x, 4 scales with ICI",
             "output_px": px, "frames": [f.name for f in frames],
             "batched": {"ms": round(t_batch, 3), "mpx_s": round(px / t_batch / 1e3, 1), "gpu_launches": 1,
-                        "config": {"tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm,
+                        "config": {"form": ("graph of per-frame grids", "persistent per-order kernels")[best.form],
+                                   "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm,
                                    "cost_order": best.cost_order}},
             "per_frame": {"ms": round(t_plain, 3), "mpx_s": round(px / t_plain / 1e3, 1), "gpu_launches": len(frames)},
             "speedup": round(t_plain / t_batch, 3), "l2": "flushed between timed repetitions"}
@@ -535,7 +536,7 @@ def main():
     ap.add_argument("--size", type=int, default=2048, help="raw and output edge (2048 = the paper-scale workload)")
     ap.add_argument("--headline-only", action="store_true", help="skip the batching and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson arrival schedule")
-    ap.add_argument("--step-tiles", type=int, default=0, help="tile budget of one serving step (0 = all pending)")
+    ap.add_argument("--step-tiles", type=int, default=8192, help="tile budget of one serving step (0 = all pending)")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup(args)
     try:

@@ -144,26 +144,30 @@ typedef struct {
   uint8_t *choice_dev;          /* optional level map, NULL = not written */
 } hdr_frame;
 
-/* Launch configuration of the batched kernel. */
+/* Launch configuration of a batched reconstruction. Both forms run as one CUDA-graph launch:
+ *  form 0: one grid per frame (the single-frame kernel over that frame's tiles), all frames as
+ *          independent branches of one graph, so that small frames fill the tails of large ones;
+ *  form 1: one persistent kernel per polynomial order whose CTAs take tiles of every frame of that
+ *          order from a device-wide queue (tile list and counters in device memory). */
 typedef struct {
   int32_t tile_h;               /* output rows per tile: 8 (128-thread CTAs) or 16 (256 threads) */
-  int32_t ctas_per_sm;          /* persistent CTAs per SM; 0 = as many as fit                    */
-  int32_t cost_order;           /* 1 = tiles of the most expensive frames first, 0 = given order  */
+  int32_t ctas_per_sm;          /* form 1: persistent CTAs per SM; 0 = as many as fit            */
+  int32_t cost_order;           /* 1 = the most expensive frames first, 0 = the given order      */
+  int32_t form;                 /* 0 or 1, see above                                              */
 } hdr_batch_config;
 
-/* Reconstruct n_frames (1..4096) frames of any sizes, rigs, orders and scales in ONE persistent
- * kernel launch on `cuda_stream` (A8 of the workload: batching). The launch is recorded once in a
- * CUDA graph per launch shape (configuration, grid, shared-memory size, table capacity) and
- * replayed: the graph copies the frame and tile tables from pinned staging owned by the context,
- * clears the tile counter and runs the kernel. `cfg` NULL = the configuration hdr_tune_batch found
- * for batches of this kind, else the default {16, 0, 1}. All frames must use the same `accum`.
- * Asynchronous like hdr_reconstruct; the context must not start another batch before the previous
- * one has finished reading its tables (the call waits for that). Results are identical to
- * reconstructing each frame with hdr_reconstruct. */
+/* Reconstruct n_frames (1..4096) frames of any sizes, rigs, orders and scales in one graph launch
+ * on `cuda_stream`. A graph is recorded once per launch shape and replayed: form 0 updates the
+ * kernel parameters of its nodes; form 1 copies the frame and tile tables from pinned staging
+ * owned by the context (double-buffered: the call waits only if the launch before the previous
+ * one is still reading) and clears the tile counters. `cfg` NULL = the configuration
+ * hdr_tune_batch found for batches of this kind, else the default {16, 0, 1, 0}. All frames must
+ * use the same `accum`. Asynchronous like hdr_reconstruct. Results are identical to reconstructing
+ * each frame with hdr_reconstruct. */
 hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames,
                                  const hdr_batch_config *cfg, void *cuda_stream);
 
-/* Autotuner: times every candidate configuration (tile height 8/16 x 1/2/max CTAs per SM x frame
+/* Autotuner: times every candidate configuration (form, tile height 8/16, CTAs per SM, frame
  * order) on this batch, keeps the fastest for batches of the same kind (orders present, largest
  * sensor count, scale count, output-size bucket) and writes it to *best. Synchronous. */
 hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, hdr_batch_config *best,

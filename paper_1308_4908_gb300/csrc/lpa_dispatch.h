@@ -4,9 +4,42 @@
 
 #include "lpa_launch.h"
 
+// Largest dynamic shared memory a block of the current device may opt in to.
+inline int lpa_smem_optin() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < 64) cache[dev] = v;
+  return v;
+}
+
+// Opt a kernel in to the largest dynamic shared memory its static shared memory leaves, never to
+// one launch's size: a graph recorded with a larger launch stays valid whatever smaller launches
+// of the same kernel run in between.
+inline cudaError_t lpa_opt_in(const void *fn) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, fn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              lpa_smem_optin() - (int)a.sharedSizeBytes);
+}
+
 cudaError_t lpa_launch_order0(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
 cudaError_t lpa_launch_order1(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
 cudaError_t lpa_launch_order2(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
+
+// The single-frame kernel of order M for that configuration (for graph kernel nodes).
+const void *lpa_kernel_order0(bool comp, bool diag, int tile_h);
+const void *lpa_kernel_order1(bool comp, bool diag, int tile_h);
+const void *lpa_kernel_order2(bool comp, bool diag, int tile_h);
+inline const void *lpa_kernel(int order, bool comp, bool diag, int tile_h) {
+  return order == 0   ? lpa_kernel_order0(comp, diag, tile_h)
+         : order == 1 ? lpa_kernel_order1(comp, diag, tile_h)
+                      : lpa_kernel_order2(comp, diag, tile_h);
+}
 
 // Persistent launch of order M over its segment of a many-frame tile list (tile height 8 or 16).
 cudaError_t lpa_launch_batch_order0(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st);

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -92,6 +93,14 @@ struct BatchState {
   };
   std::map<Key, cudaGraphExec_t> graphs;
   std::map<uint64_t, hdr_batch_config> tuned;
+  // form 0: one kernel node per frame, keyed by each node's (order, accum, tile height, grid,
+  // shared memory); replays update the nodes' parameters
+  struct FrameGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> nodes;
+  };
+  std::map<std::vector<std::array<int64_t, 5>>, FrameGraph> frame_graphs;
 };
 
 struct hdr_ctx {
@@ -225,6 +234,7 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
   L.out_w = p->out_w;
   L.out_h = p->out_h;
   L.tile_h = tile_h;
+  L.tile0 = 0;
   L.tiles_x = (p->out_w + LPA_TILE - 1) / LPA_TILE;
   L.tiles_y = (p->out_h + tile_h - 1) / tile_h;
   L.out_half = p->out_dtype;
@@ -406,6 +416,10 @@ void hdr_destroy(hdr_ctx *ctx) {
   cudaFree(ctx->choice_stage);
   cudaFree(ctx->status);
   for (auto &g : ctx->batch.graphs) cudaGraphExecDestroy(g.second);
+  for (auto &g : ctx->batch.frame_graphs) {
+    cudaGraphExecDestroy(g.second.exec);
+    cudaGraphDestroy(g.second.graph);
+  }
   cudaFree(ctx->batch.frames_dev);
   cudaFree(ctx->batch.tiles_dev);
   cudaFree(ctx->batch.bounds_dev);
@@ -688,15 +702,91 @@ hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *
   return HDR_OK;
 }
 
+// Form 0 of a batched launch: one grid per frame (tiles [ranges[f].x, ranges[f].y) of frame f, or
+// all of them) as independent kernel nodes of one graph, recorded once per shape; a replay only
+// updates the nodes' parameters.
+hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *ranges,
+                            const hdr_batch_config &cfg, cudaStream_t stream) {
+  BatchState &B = ctx->batch;
+  std::vector<LpaLaunch> plans(n);
+  std::vector<int> grid(n, 0);
+  for (int f = 0; f < n; f++) {
+    const hdr_frame &F = frames[f];
+    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
+                             plans[f], cfg.tile_h);
+    if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
+    plans[f].out = F.out_dev;
+    plans[f].choice = F.choice_dev;
+    plans[f].levels = nullptr;
+    const int nt = plans[f].tiles_x * plans[f].tiles_y;
+    if (ranges && (ranges[f].x < 0 || ranges[f].y > nt || ranges[f].x > ranges[f].y))
+      return fail(HDR_E_INVALID, "frame %d: tile range [%d, %d) outside [0, %d)", f, ranges[f].x, ranges[f].y, nt);
+    plans[f].tile0 = ranges ? ranges[f].x : 0;
+    grid[f] = ranges ? ranges[f].y - ranges[f].x : nt;
+  }
+  std::vector<int> order;
+  for (int f = 0; f < n; f++)
+    if (grid[f] > 0) order.push_back(f);
+  if (cfg.cost_order) {
+    std::vector<double> cost(n);
+    for (int f = 0; f < n; f++) cost[f] = frame_cost(*frames[f].params, ctx->rigs[frames[f].rig_id].n) * grid[f];
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  }
+  if (order.empty()) return HDR_OK;
+  const bool comp = frames[0].params->accum != 0;
+  std::vector<std::array<int64_t, 5>> key;
+  std::vector<cudaKernelNodeParams> kp(order.size());
+  std::vector<void *> args(order.size());
+  for (size_t k = 0; k < order.size(); k++) {
+    const LpaLaunch &L = plans[order[k]];
+    const void *fn = lpa_kernel(L.order, comp, false, cfg.tile_h);
+    CUDA_TRY(lpa_opt_in(fn));
+    key.push_back({L.order, comp ? 1 : 0, cfg.tile_h, grid[order[k]], (int64_t)L.smem_bytes});
+    args[k] = &plans[order[k]];
+    kp[k] = cudaKernelNodeParams{};
+    kp[k].func = const_cast<void *>(fn);
+    kp[k].gridDim = dim3((unsigned)grid[order[k]]);
+    kp[k].blockDim = dim3((unsigned)(LPA_TILE * cfg.tile_h));
+    kp[k].sharedMemBytes = L.smem_bytes;
+    kp[k].kernelParams = &args[k];
+  }
+  auto it = B.frame_graphs.find(key);
+  if (it != B.frame_graphs.end()) {
+    for (size_t k = 0; k < order.size(); k++)
+      CUDA_TRY(cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.nodes[k], &kp[k]));
+  } else {
+    if (B.frame_graphs.size() >= 256) {  // shapes that never repeat (serving steps): start over
+      for (auto &g : B.frame_graphs) {
+        cudaGraphExecDestroy(g.second.exec);
+        cudaGraphDestroy(g.second.graph);
+      }
+      B.frame_graphs.clear();
+    }
+    BatchState::FrameGraph fg;
+    cudaError_t e = cudaGraphCreate(&fg.graph, 0);
+    fg.nodes.resize(order.size());
+    for (size_t k = 0; k < order.size() && e == cudaSuccess; k++)
+      e = cudaGraphAddKernelNode(&fg.nodes[k], fg.graph, nullptr, 0, &kp[k]);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&fg.exec, fg.graph, 0);
+    if (e != cudaSuccess) {
+      if (fg.graph) cudaGraphDestroy(fg.graph);
+      return fail(HDR_E_CUDA, "recording the batch graph failed: %s", cudaGetErrorString(e));
+    }
+    it = B.frame_graphs.emplace(key, fg).first;
+  }
+  CUDA_TRY(cudaGraphLaunch(it->second.exec, stream));
+  return HDR_OK;
+}
+
 }  // namespace
 
-// One persistent launch over the listed tiles of several frames (see hdr_reconstruct_batch).
+// One batched launch over the listed tiles of several frames (see hdr_reconstruct_batch).
 hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, const int2 *ranges,
                          const hdr_batch_config *cfg_in, cudaStream_t stream) {
   hdr_status st = check_batch(ctx, n_frames, frames);
   if (st) return st;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  hdr_batch_config cfg = {16, 0, 1};
+  hdr_batch_config cfg = {16, 0, 1, 0};
   if (cfg_in) {
     cfg = *cfg_in;
   } else {
@@ -705,6 +795,8 @@ hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames
   }
   if (cfg.tile_h != 8 && cfg.tile_h != 16) return fail(HDR_E_INVALID, "tile_h must be 8 or 16");
   if (cfg.ctas_per_sm < 0 || cfg.ctas_per_sm > 8) return fail(HDR_E_INVALID, "ctas_per_sm must be in [0, 8]");
+  if (cfg.form != 0 && cfg.form != 1) return fail(HDR_E_INVALID, "form must be 0 or 1");
+  if (cfg.form == 0) return batch_run_frames(ctx, n_frames, frames, ranges, cfg, stream);
   uint32_t smem[3];
   int n_tiles[3];
   st = batch_plan(ctx, n_frames, frames, ranges, cfg, smem, n_tiles);
@@ -830,10 +922,10 @@ extern "C" hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_f
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
-  hdr_batch_config win = {16, 0, 1};
+  hdr_batch_config win = {16, 0, 1, 0};
   float win_ms = 1e30f;
-  const hdr_batch_config cands[] = {{16, 0, 1}, {16, 1, 1}, {16, 2, 1}, {8, 0, 1}, {8, 2, 1}, {8, 4, 1},
-                                    {16, 0, 0}, {8, 0, 0}};
+  const hdr_batch_config cands[] = {{16, 0, 1, 0}, {8, 0, 1, 0}, {16, 0, 0, 0}, {16, 0, 1, 1}, {16, 1, 1, 1},
+                                    {16, 2, 1, 1}, {8, 0, 1, 1},  {8, 2, 1, 1},  {8, 4, 1, 1},  {16, 0, 0, 1}};
   for (const hdr_batch_config &c : cands) {
     st = hdr_reconstruct_batch(ctx, n_frames, frames, &c, cuda_stream);  // warm-up (and graph record)
     if (st == HDR_E_UNSUPPORTED) continue;

@@ -184,6 +184,77 @@ struct Moments {
   __device__ __forceinline__ T Kv(int i) const { return COMP ? (T)k[i] + (T)kl[i] : (T)k[i]; }
 };
 
+#ifndef LPA_PACKED_MOMENTS
+#define LPA_PACKED_MOMENTS 1
+#endif
+
+
+// The same plain FP32 moments with the Gram and variance sums of each monomial held as one pair
+// (sum w m, sum w K m): one paired FMA (fma.rn.f32x2, weights (w, w K), the monomial in both
+// halves) advances both. Every half rounds exactly as the scalar operation it replaces, so the
+// sums are bit-identical to Moments<ORDER, false>; only the instruction count drops (Blackwell
+// issues two FP32 FMAs per paired instruction).
+template <int ORDER>
+struct MomentsPacked {
+  static constexpr int NA = n_monos(ORDER);
+  static constexpr int NB = n_unknowns(ORDER);
+  float2 ak[NA];  // (sum w m_i, sum w K m_i)
+  float b[NB];
+  float cnt;
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NA; i++) ak[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < NB; i++) b[i] = 0.f;
+    cnt = 0.f;
+  }
+  __device__ __forceinline__ void add(float dx, float dy, float w, float wf, float wk) {
+    const float2 W = make_float2(w, wk);
+    float s[15];
+    s[1] = dx;
+    s[2] = dy;
+    s[3] = dx * dx;
+    s[4] = dx * dy;
+    s[5] = dy * dy;
+    if (NA > 6) {
+      s[6] = s[3] * dx;
+      s[7] = s[3] * dy;
+      s[8] = s[4] * dy;
+      s[9] = s[5] * dy;
+      s[10] = s[3] * s[3];
+      s[11] = s[3] * s[4];
+      s[12] = s[3] * s[5];
+      s[13] = s[4] * s[5];
+      s[14] = s[5] * s[5];
+    }
+    ak[0] = __fadd2_rn(ak[0], W);
+#pragma unroll
+    for (int i = 1; i < NA; i++) ak[i] = __ffma2_rn(W, make_float2(s[i], s[i]), ak[i]);
+    b[0] += wf;
+#pragma unroll
+    for (int i = 1; i < NB; i++) b[i] = fmaf(wf, s[i], b[i]);
+    cnt += 1.f;
+  }
+
+  template <typename T>
+  __device__ __forceinline__ T A(int i) const { return (T)ak[i].x; }
+  template <typename T>
+  __device__ __forceinline__ T B(int i) const { return (T)b[i]; }
+  template <typename T>
+  __device__ __forceinline__ T Kv(int i) const { return (T)ak[i].y; }
+};
+
+// The accumulator a kernel uses: paired for plain FP32 sums of order >= 1.
+template <int ORDER, bool COMP, bool PACKED = (LPA_PACKED_MOMENTS != 0) && !COMP && ORDER >= 1>
+struct MomentsSel {
+  using type = Moments<ORDER, COMP>;
+};
+template <int ORDER>
+struct MomentsSel<ORDER, false, true> {
+  using type = MomentsPacked<ORDER>;
+};
+
 // ---------------------------------------------------------------- solve
 
 struct FitOut {
@@ -345,7 +416,7 @@ struct Anchor {
 };
 
 template <int ORDER, bool COMP>
-__device__ __forceinline__ void accumulate_sensor(Moments<ORDER, COMP> &m, const LpaSensorK &S,
+__device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COMP>::type &m, const LpaSensorK &S,
                                                   const Anchor &an, int du, int dv, int c, float R, float R2,
                                                   float cexp, float taper, int x0, int y0,
                                                   const unsigned char *smem, bool active, unsigned *status) {
@@ -410,16 +481,30 @@ __device__ __forceinline__ void accumulate_sensor(Moments<ORDER, COMP> &m, const
   }
 }
 
+#ifndef LPA_BATCH_REREAD
+#define LPA_BATCH_REREAD 1
+#endif
+
+template <bool V, typename T>
+__device__ __forceinline__ T reread(const T &x) {
+  if constexpr (V) return *reinterpret_cast<const volatile T *>(&x);
+  else return x;
+}
+
 // One output tile (16 x TH pixels) of frame L, by a CTA of 16*TH threads (one per pixel).
-// GLOBAL_MAPS: L (and its tensor maps) lives in global memory rather than in kernel parameters.
+// GLOBAL_MAPS: L is a shared-memory copy of a descriptor in global memory, and `maps` is that
+// global descriptor, whose tensor maps the bulk copies use (otherwise `maps` is &L).
 // `phase` is the parity of the CTA's mbarrier use for this tile. Returns false when the CTA must
 // stop (a bounded wait ran out here or in another CTA).
 template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS>
-__device__ __forceinline__ bool process_tile(const LpaLaunch &L, int tile, unsigned char *smem, uint64_t *mbar,
+__device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch *maps, int tile, unsigned char *smem, uint64_t *mbar,
                                              uint32_t phase, int *fp_x0, int *fp_y0,
                                              Anchor (*anchors)[LPA_MAX_SENSORS]) {
   constexpr int NT = LPA_TILE * TH;
   const int tid = threadIdx.x;
+  // descriptor fields used across the pixel loops: with a shared-memory descriptor they are read
+  // again at each use rather than held in registers through the loops
+#define RD(x) reread<GLOBAL_MAPS && LPA_BATCH_REREAD>(x)
   // once any CTA's bounded wait has run out, later CTAs retire at once
   if (*reinterpret_cast<volatile unsigned int *>(L.status) & LPA_ERR_TIMEOUT) return false;
   const int tu = tile % L.tiles_x, tv = tile / L.tiles_x;
@@ -461,9 +546,9 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, int tile, unsig
     // tensor maps kept in global memory are rewritten between launches at the same addresses:
     // make this launch's contents visible to the tensor-map proxy before the copies use them
     if (GLOBAL_MAPS)
-      for (int s = 0; s < S; s++) tensormap_acquire(&L.s[s].tmap);
+      for (int s = 0; s < S; s++) tensormap_acquire(&maps->s[s].tmap);
     mbar_arrive_expect_tx(mbar, L.tx_bytes);
-    for (int s = 0; s < S; s++) tma_load_2d(smem + L.s[s].off_raw, &L.s[s].tmap, fp_x0[s], fp_y0[s], mbar);
+    for (int s = 0; s < S; s++) tma_load_2d(smem + L.s[s].off_raw, &maps->s[s].tmap, fp_x0[s], fp_y0[s], mbar);
   }
   bool landed = mbar_wait_bounded(mbar, phase, 1u << 20);
   landed = __syncthreads_and(landed);
@@ -528,41 +613,41 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, int tile, unsig
   const int par = warp & 3, hf = warp >> 2;
   const int u = u0 + 2 * (lane & 7) + (par & 1);
   const int v = v0 + 2 * ((lane >> 3) + 4 * hf) + (par >> 1);
-  const bool pix = (u < L.out_w) && (v < L.out_h);
+  const bool pix = (u < RD(L.out_w)) && (v < RD(L.out_h));
   const int ab = ((u - u0) >> 3) + 2 * ((v - v0) >> 3);  // < NA
   const int du = (u - u0) & 7, dv = (v - v0) & 7;
   constexpr int P = n_unknowns(ORDER);
-  const int J = L.n_scales;
+  const int J = RD(L.n_scales);
   const int NL = J + ORDER;
-  const size_t plane_px = (size_t)L.out_w * L.out_h;
-  const size_t opix = (size_t)v * L.out_w + u;
+  const size_t plane_px = (size_t)RD(L.out_w) * RD(L.out_h);
+  const size_t opix = (size_t)v * RD(L.out_w) + u;
   const float log2e = 1.4426950408889634f;
 
 #pragma unroll 1
   for (int c = 0; c < 3; c++) {
     Ici ici;
     ici.reset(pix);
-    Moments<ORDER, COMP> m;
-    const float gsc = (c == 1) ? L.green_ratio : 1.f;
+    typename MomentsSel<ORDER, COMP>::type m;
+    const float gsc = (c == 1) ? RD(L.green_ratio) : 1.f;
 #pragma unroll 1
     for (int j = 0; j < J; j++) {
       if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
       m.zero();
-      const float sg = L.sigma[j] * gsc;
-      const float R = L.trunc_k * sg, R2 = R * R;
+      const float sg = RD(L.sigma[j]) * gsc;
+      const float R = RD(L.trunc_k) * sg, R2 = R * R;
       const float cexp = -log2e / (2.f * sg * sg);
       const bool act = DIAG ? pix : !ici.done;
 #pragma unroll 1
       for (int s = 0; s < S; s++)
-        accumulate_sensor<ORDER, COMP>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, L.taper, fp_x0[s],
-                                       fp_y0[s], smem, act, L.status);
-      FitOut f = solve_with_fallback<P>(m, L.min_pivot, L.cond_fallback);
+        accumulate_sensor<ORDER, COMP>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, RD(L.taper), fp_x0[s],
+                                       fp_y0[s], smem, act, RD(L.status));
+      FitOut f = solve_with_fallback<P>(m, RD(L.min_pivot), RD(L.cond_fallback));
       if (DIAG && pix) {
         float *o = L.levels + (((size_t)c * NL + j) * plane_px + opix) * 2;
         o[0] = f.valid ? f.c0 : __int_as_float(0x7fffffff);
         o[1] = f.valid ? f.var : __int_as_float(0x7fffffff);
       }
-      ici.step(f, j, L.ici_gamma);
+      ici.step(f, j, RD(L.ici_gamma));
     }
     // order fallback at the largest scale (the moments still hold it when any lane needs it)
     const bool need = ici.choice == 255 && pix;
@@ -578,21 +663,22 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, int tile, unsig
           ici.val = f.c0;
         }
       };
-      if constexpr (ORDER >= 1) take(fallback_fit<ORDER, 0>(m, L.min_pivot, L.cond_fallback), 0);
-      if constexpr (ORDER >= 2) take(fallback_fit<ORDER, 1>(m, L.min_pivot, L.cond_fallback), 1);
+      if constexpr (ORDER >= 1) take(fallback_fit<ORDER, 0>(m, RD(L.min_pivot), RD(L.cond_fallback)), 0);
+      if constexpr (ORDER >= 2) take(fallback_fit<ORDER, 1>(m, RD(L.min_pivot), RD(L.cond_fallback)), 1);
     }
     if (pix) {
-      if (L.out_half)
-        reinterpret_cast<__half *>(L.out)[c * plane_px + opix] = __float2half_rn(ici.val);
+      if (RD(L.out_half))
+        reinterpret_cast<__half *>(RD(L.out))[c * plane_px + opix] = __float2half_rn(ici.val);
       else
-        reinterpret_cast<float *>(L.out)[c * plane_px + opix] = ici.val;
-      if (L.choice) L.choice[c * plane_px + opix] = (uint8_t)ici.choice;
+        reinterpret_cast<float *>(RD(L.out))[c * plane_px + opix] = ici.val;
+      if (RD(L.choice)) RD(L.choice)[c * plane_px + opix] = (uint8_t)ici.choice;
     }
   }
   return true;
+#undef RD
 }
 
-// Single frame: one CTA per tile.
+// Single frame: one CTA per tile (tiles tile0 .. tile0 + gridDim.x - 1).
 template <int ORDER, bool COMP, bool DIAG, int TH>
 __global__ void __launch_bounds__(LPA_TILE *TH, 16 / TH * 2) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -600,7 +686,7 @@ __global__ void __launch_bounds__(LPA_TILE *TH, 16 / TH * 2) lpa_reconstruct(con
   __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
   __shared__ __align__(8) uint64_t mbar;
   if (threadIdx.x == 0) mbar_init(&mbar, 1);
-  process_tile<ORDER, COMP, DIAG, TH, false>(L, blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0, anchors);
+  process_tile<ORDER, COMP, DIAG, TH, false>(L, &L, L.tile0 + blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0, anchors);
 }
 
 // Resident CTAs per SM the persistent kernel is compiled for (register cap 64K / (threads x this)):
@@ -620,19 +706,28 @@ __global__ void __launch_bounds__(LPA_TILE *TH, (BatchOccupancy<ORDER, TH>::valu
   __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ int next;
+  __shared__ LpaLaunch frame;  // the current tile's frame descriptor (kernel-parameter-like reads)
   if (threadIdx.x == 0) mbar_init(&mbar, 1);
   const int t_end = B.bounds[ORDER + 1];
   const int t_begin = B.bounds[ORDER];
   uint32_t phase = 0;
+  int cur = -1;
   for (;;) {
-    __syncthreads();  // every thread is done with the previous tile's staging
+    __syncthreads();  // every thread is done with the previous tile's staging and descriptor
     if (threadIdx.x == 0) next = t_begin + (int)atomicAdd(B.counters + ORDER, 1u);
     __syncthreads();
     const int t = next;
     if (t >= t_end) break;
     const int2 ft = B.tiles[t];
-    const bool ok = process_tile<ORDER, COMP, false, TH, true>(B.frames[ft.x], ft.y, smem, &mbar, phase, fp_x0,
-                                                               fp_y0, anchors);
+    if (ft.x != cur) {  // uniform: every thread read the same tile
+      const int4 *src = reinterpret_cast<const int4 *>(B.frames + ft.x);
+      int4 *dst = reinterpret_cast<int4 *>(&frame);
+      for (int i = threadIdx.x; i < (int)(sizeof(LpaLaunch) / sizeof(int4)); i += LPA_TILE * TH) dst[i] = src[i];
+      cur = ft.x;
+      __syncthreads();
+    }
+    const bool ok = process_tile<ORDER, COMP, false, TH, true>(frame, B.frames + ft.x, ft.y, smem, &mbar, phase,
+                                                               fp_x0, fp_y0, anchors);
     if (!__syncthreads_and(ok)) break;
     phase ^= 1u;
   }

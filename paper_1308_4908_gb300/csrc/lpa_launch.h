@@ -56,6 +56,7 @@ struct LpaLaunch {
   uint32_t tx_bytes;             // bytes landed by the bulk tensor copies of one tile
   uint32_t smem_bytes;
   int tile_h;                    // tile height the plan was made for
+  int tile0;                     // single-frame grid: CTA b reconstructs tile tile0 + b
 };
 
 // Several frames in one graph launch: the tile list is grouped by polynomial order and each

@@ -6,7 +6,7 @@
 template <bool COMP, bool DIAG, int TH>
 static cudaError_t launch_one(const LpaLaunch &L, cudaStream_t st) {
   auto k = lpa::lpa_reconstruct<1, COMP, DIAG, TH>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
+  cudaError_t e = lpa_opt_in((const void *)k);
   if (e != cudaSuccess) return e;
   k<<<L.tiles_x * L.tiles_y, LPA_TILE * TH, L.smem_bytes, st>>>(L);
   return cudaGetLastError();
@@ -25,7 +25,7 @@ cudaError_t lpa_launch_order1(const LpaLaunch &L, bool comp, bool diag, cudaStre
 template <bool COMP, int TH>
 static cudaError_t launch_batch_t(const LpaBatch &B, int grid, cudaStream_t st) {
   auto k = lpa::lpa_reconstruct_batch<1, COMP, TH>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem_bytes);
+  cudaError_t e = lpa_opt_in((const void *)k);
   if (e != cudaSuccess) return e;
   k<<<grid, LPA_TILE * TH, B.smem_bytes, st>>>(B);
   return cudaGetLastError();
@@ -40,7 +40,7 @@ template <bool COMP, int TH>
 static int fit_t(uint32_t smem_bytes) {
   auto k = lpa::lpa_reconstruct_batch<1, COMP, TH>;
   int n = 0;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) return 0;
+  if (lpa_opt_in((const void *)k) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, LPA_TILE * TH, smem_bytes) != cudaSuccess) return 0;
   return n;
 }
@@ -48,4 +48,13 @@ static int fit_t(uint32_t smem_bytes) {
 int lpa_batch_ctas_per_sm_order1(bool comp, int tile_h, uint32_t smem_bytes) {
   if (tile_h == 8) return comp ? fit_t<true, 8>(smem_bytes) : fit_t<false, 8>(smem_bytes);
   return comp ? fit_t<true, 16>(smem_bytes) : fit_t<false, 16>(smem_bytes);
+}
+
+const void *lpa_kernel_order1(bool comp, bool diag, int tile_h) {
+  if (tile_h == 8) {
+    if (comp) return diag ? (const void *)lpa::lpa_reconstruct<1, true, true, 8> : (const void *)lpa::lpa_reconstruct<1, true, false, 8>;
+    return diag ? (const void *)lpa::lpa_reconstruct<1, false, true, 8> : (const void *)lpa::lpa_reconstruct<1, false, false, 8>;
+  }
+  if (comp) return diag ? (const void *)lpa::lpa_reconstruct<1, true, true, 16> : (const void *)lpa::lpa_reconstruct<1, true, false, 16>;
+  return diag ? (const void *)lpa::lpa_reconstruct<1, false, true, 16> : (const void *)lpa::lpa_reconstruct<1, false, false, 16>;
 }

@@ -355,6 +355,7 @@ hdr_status hdr_server_create(hdr_ctx *ctx, const hdr_server_config *cfg, hdr_ser
     return lpa_fail(HDR_E_INVALID, "batch.tile_h must be 0, 8 or 16");
   if (cfg->batch.ctas_per_sm < 0 || cfg->batch.ctas_per_sm > 8)
     return lpa_fail(HDR_E_INVALID, "batch.ctas_per_sm must be in [0, 8]");
+  if (cfg->batch.form != 0 && cfg->batch.form != 1) return lpa_fail(HDR_E_INVALID, "batch.form must be 0 or 1");
   hdr_server *s = new (std::nothrow) hdr_server();
   if (!s) return lpa_fail(HDR_E_NOMEM, "host allocation failed");
   s->ctx = ctx;

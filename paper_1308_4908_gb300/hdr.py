@@ -48,7 +48,8 @@ class hdr_frame(ctypes.Structure):
 
 
 class hdr_batch_config(ctypes.Structure):
-    _fields_ = [("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("cost_order", ctypes.c_int32)]
+    _fields_ = [("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("cost_order", ctypes.c_int32),
+                ("form", ctypes.c_int32)]
 
 
 class hdr_server_config(ctypes.Structure):
@@ -378,7 +379,7 @@ class Server:
                  batch: Optional[hdr_batch_config] = None):
         cfg = hdr_server_config()
         cfg.max_frames, cfg.pool_bytes, cfg.step_tiles = int(max_frames), int(pool_bytes), int(step_tiles)
-        cfg.batch = batch if batch is not None else hdr_batch_config(0, 0, 0)
+        cfg.batch = batch if batch is not None else hdr_batch_config(0, 0, 1, 0)
         self.ctx = ctx
         self.handle = hdr_server_create(ctx.handle, cfg)
         self._held = {}

@@ -67,26 +67,28 @@ def test_batch_equals_single_frames_for_every_configuration(ctx):
     frames = synth.batching(n_frames=8, size_cap=160)
     items = _prepare(ctx, frames)
     refs = _single(ctx, items)
-    for th in (16, 8):
-        for per_sm in (0, 1):
-            for order in (1, 0):
-                for _, _, _, out, _ in items:
-                    out.fill_(-7.0)
-                cfg = hdr.hdr_batch_config(th, per_sm, order)
-                _same(_batch(ctx, items, cfg), refs)
+    cfgs = [hdr.hdr_batch_config(th, per_sm, order, 1) for th in (16, 8) for per_sm in (0, 1) for order in (1, 0)]
+    cfgs += [hdr.hdr_batch_config(th, 0, order, 0) for th in (16, 8) for order in (1, 0)]
+    for cfg in cfgs:
+        for _, _, _, out, _ in items:
+            out.fill_(-7.0)
+        _same(_batch(ctx, items, cfg), refs)
 
 
-def test_batch_replays_with_new_contents(ctx):
-    """The recorded graph is replayed with fresh tables: a second batch of the same shapes but other
-    frames (other rigs and raws) gives those frames' results."""
+@pytest.mark.parametrize("form", [0, 1])
+def test_batch_replays_with_new_contents(ctx, form):
+    """The recorded graph is replayed with fresh tables or node parameters: a second batch of the
+    same shapes but other frames (other rigs and raws) gives those frames' results."""
+    from paper_1308_4908_gb300 import hdr
     a = synth.batching(n_frames=4, size_cap=96, seed=2001)
     b = synth.batching(n_frames=4, size_cap=96, seed=2002)
     ia = _prepare(ctx, a, base_rig=10)
     ib = _prepare(ctx, b, base_rig=20)
     ra, rb = _single(ctx, ia), _single(ctx, ib)
-    _same(_batch(ctx, ia), ra)
-    _same(_batch(ctx, ib), rb)
-    _same(_batch(ctx, ia), ra)
+    cfg = hdr.hdr_batch_config(16, 0, 1, form)
+    _same(_batch(ctx, ia, cfg), ra)
+    _same(_batch(ctx, ib, cfg), rb)
+    _same(_batch(ctx, ia, cfg), ra)
 
 
 def test_tuner_picks_a_configuration_and_batch_uses_it(ctx):
@@ -96,7 +98,7 @@ def test_tuner_picks_a_configuration_and_batch_uses_it(ctx):
     keep = []
     hf = [ctx.frame(rig, fr.params, raws, out, ch, keep) for rig, fr, raws, out, ch in items]
     best = ctx.tune_batch(hf)
-    assert best.tile_h in (8, 16) and 0 <= best.ctas_per_sm <= 8 and best.cost_order in (0, 1)
+    assert best.tile_h in (8, 16) and 0 <= best.ctas_per_sm <= 8 and best.cost_order in (0, 1) and best.form in (0, 1)
     _same(_batch(ctx, items), refs)        # cfg None -> the tuned configuration
 
 
@@ -125,4 +127,6 @@ def test_batch_rejects_bad_input(ctx):
     with pytest.raises(hdr.HdrError):
         ctx.reconstruct_batch(hf[:0])
     with pytest.raises(hdr.HdrError):
-        ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(12, 0, 1))
+        ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(12, 0, 1, 0))
+    with pytest.raises(hdr.HdrError):
+        ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(16, 0, 1, 2))
