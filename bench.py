@@ -405,6 +405,80 @@ def run_serving(ctx, frames, dev, seconds: float, step_tiles: int):
     }
 
 
+def run_precision_study(args):
+    """Error of each precision variant against the FP64 oracle on the precision workload (the tiny
+    recipe's two sensors at 2048^2 raw, one scale sigma 0.7, 2x upsampled 4096^2 output), for
+    orders 0 and 2: plain vs compensated FP32 sums, FP32 vs FP16 output, the FP64 re-solve above
+    a condition estimate of 1e6 on or off, and min_pivot 1e-3 vs 1e-10. One JSON line."""
+    import dataclasses
+    import torch
+    import oracle
+    from paper_1308_4908_gb300 import hdr, synth
+    oracle.build()
+    ctx = hdr.Context(0)
+    rows = []
+    n_pix = args.study_pixels
+    for order in (0, 2):
+        fr = synth.precision(size=args.size, order=order)
+        ctx.set_rig(0, fr.sensors)
+        raws = [torch.from_numpy(s.raw).cuda() for s in fr.sensors]
+        r = np.random.default_rng(7 + order)
+        pix = np.stack([r.integers(0, fr.params.out_w, n_pix), r.integers(0, fr.params.out_h, n_pix)], axis=1)
+        variants = [dict(accum=a, out_dtype=d, cond_fallback=1e6, min_pivot=1e-3) for a in (0, 1) for d in (0, 1)]
+        if order == 2:
+            variants += [dict(accum=0, out_dtype=0, cond_fallback=0.0, min_pivot=1e-3),
+                         dict(accum=1, out_dtype=0, cond_fallback=1.0, min_pivot=1e-3),
+                         dict(accum=1, out_dtype=0, cond_fallback=1e6, min_pivot=1e-10),
+                         dict(accum=1, out_dtype=0, cond_fallback=1.0, min_pivot=1e-10),
+                         dict(accum=0, out_dtype=0, cond_fallback=0.0, min_pivot=1e-10)]
+        refs = {}
+        for v in variants:
+            p = dataclasses.replace(fr.params, **v)
+            if p.min_pivot not in refs:
+                refs[p.min_pivot] = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True)
+            o = refs[p.min_pivot]
+            # condition number of the equilibrated normal matrix at the chosen level
+            lvl = np.clip(o["choice"], 0, None)
+            kap = np.take_along_axis(o["kappa"], lvl[:, :, None], axis=2)[:, :, 0]
+            ch = torch.empty((3, p.out_h, p.out_w), dtype=torch.uint8, device="cuda")
+            out = ctx.reconstruct(0, p, raws, choice=ch)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                ctx.reconstruct(0, p, raws, choice=ch, out=out)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) / 3 * 1e3
+            ctx.check()
+            g = out.float().cpu().numpy()[:, pix[:, 1], pix[:, 0]].T           # [n, 3]
+            gc = ch.cpu().numpy()[:, pix[:, 1], pix[:, 0]].T.astype(np.int32)
+            gc[gc == 255] = -1
+            same = (gc == o["choice"]) & np.isfinite(o["out"]) & np.isfinite(g)
+            rel_all = np.abs(g - o["out"]) / np.maximum(np.abs(o["out"]), 1e-2)
+            rel = rel_all[same]
+            # the same error in units of FP32 rounding of the terms that form the value (the
+            # oracle's first-order rounding scales of the fit and of the weights at that level)
+            efit = np.take_along_axis(o["efit"], lvl[:, :, None], axis=2)[:, :, 0]
+            ew = np.take_along_axis(o["ew"], lvl[:, :, None], axis=2)[:, :, 0]
+            ulp = (np.abs(g - o["out"]) / (2.0 ** -24 * (efit + ew) + 1e-300))[same]
+            by_kappa = {}
+            for lo, hi in ((1, 1e2), (1e2, 1e4), (1e4, 1e6), (1e6, np.inf)):
+                m = same & (kap >= lo) & (kap < hi)
+                if m.any():
+                    by_kappa[f"{lo:.0e}-{hi:.0e}"] = {"n": int(m.sum()), "max": float(rel_all[m].max()),
+                                                      "median": float(np.median(rel_all[m]))}
+            rows.append({"order": order, **v, "pixels": int(same.size), "level_mismatch_frac": float(1 - same.mean()),
+                         "max_rel_err": float(rel.max()), "median_rel_err": float(np.median(rel)),
+                         "p99_rel_err": float(np.percentile(rel, 99)), "by_kappa": by_kappa,
+                         "max_err_in_u_of_terms": float(ulp.max()), "median_err_in_u_of_terms": float(np.median(ulp)),
+                         "ms_per_frame": round(ms, 3)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    ctx.close()
+    print(json.dumps({"study": "precision", "workload": f"2 x {args.size}^2 raw (ND 1, 1/8) -> "
+                      f"{2 * args.size}^2 output, sigma 0.7, orders 0 and 2",
+                      "error": "|gpu - oracle| / max(|oracle|, 1e-2) on pixels whose level choice matches",
+                      "sample_pixels": n_pix, "rows": rows}), flush=True)
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
@@ -535,9 +609,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--size", type=int, default=2048, help="raw and output edge (2048 = the paper-scale workload)")
     ap.add_argument("--headline-only", action="store_true", help="skip the batching and serving measurements")
+    ap.add_argument("--study", choices=["precision"], default=None, help="print a study instead of the bench line")
+    ap.add_argument("--study-pixels", type=int, default=20000)
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson arrival schedule")
     ap.add_argument("--step-tiles", type=int, default=8192, help="tile budget of one serving step (0 = all pending)")
     args = ap.parse_args()
+    if args.study == "precision":
+        run_precision_study(args)
+        return
     world, rank, local, pg = dist_setup(args)
     try:
         if args.impl == "reference":

@@ -17,7 +17,7 @@
  *   Section 5.2, Eq. 6 C = (Phi^T W Phi)^{-1} Phi^T W f,  output C_0
  *   Section 5.3.1, Eq. 8 Gaussian window, h_G = h_RB / sqrt(2)
  *   Section 5.3.1      a scale is usable only if Phi^T W Phi is invertible
- * plus the readings the paper leaves open (each also listed in the design doc):
+ * plus the readings the paper leaves open (the kernel follows the same ones):
  *   - noise weight 1/s2 (the Gaussian log-likelihood of Section 5.2);
  *     weight_mode = 1 keeps the printed 1/s for the record;
  *   - window exp(-|d|^2 / (2 sigma^2)) truncated at k*sigma and lowered by

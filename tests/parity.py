@@ -1,6 +1,6 @@
 """Comparison of the CUDA path's output with the FP64 oracle (test helper).
 
-Tolerance (stated here, derived in the design doc). For the level (scale, order) used at a pixel and
+Tolerance. For the level (scale, order) used at a pixel and
 channel, the GPU value g and the oracle value o must satisfy
 
     |g - o| <= REL_TOL * max(|o|, TAU) + U32 * (C_FIT * efit + C_W * ew)
