@@ -132,6 +132,8 @@ struct Moments {
     cnt = 0.f;
   }
 
+  __device__ __forceinline__ void add2(float2 D, float2 D2, float w, float wf, float wk) { add(D.x, D.y, w, wf, wk); }
+
   __device__ __forceinline__ void add(float dx, float dy, float w, float wf, float wk) {
     float m[15];
     m[0] = 1.f;
@@ -191,9 +193,10 @@ struct Moments {
 
 // The same plain FP32 moments with the Gram and variance sums of each monomial held as one pair
 // (sum w m, sum w K m): one paired FMA (fma.rn.f32x2, weights (w, w K), the monomial in both
-// halves) advances both. Every half rounds exactly as the scalar operation it replaces, so the
-// sums are bit-identical to Moments<ORDER, false>; only the instruction count drops (Blackwell
-// issues two FP32 FMAs per paired instruction).
+// halves) advances both, rounding each half as the scalar FMA would. The monomials of degree 3
+// and 4 are formed two at a time by paired products (x^3, y^3), (x^2 y, x y^2), ..., so they
+// round in another order than Moments<ORDER, false> forms them (a few units in the last place);
+// Blackwell issues two FP32 operations per paired instruction, so fewer instructions are issued.
 template <int ORDER>
 struct MomentsPacked {
   static constexpr int NA = n_monos(ORDER);
@@ -209,32 +212,40 @@ struct MomentsPacked {
     for (int i = 0; i < NB; i++) b[i] = 0.f;
     cnt = 0.f;
   }
-  __device__ __forceinline__ void add(float dx, float dy, float w, float wf, float wk) {
+
+  // one sample at offset D = (dx, dy) with squares D2 = (dx^2, dy^2): the monomials of degree 3
+  // and 4 come two at a time from paired products
+  __device__ __forceinline__ void add2(float2 D, float2 D2, float w, float wf, float wk) {
     const float2 W = make_float2(w, wk);
     float s[15];
-    s[1] = dx;
-    s[2] = dy;
-    s[3] = dx * dx;
-    s[4] = dx * dy;
-    s[5] = dy * dy;
+    s[1] = D.x;
+    s[2] = D.y;
+    s[3] = D2.x;
+    s[4] = D.x * D.y;
+    s[5] = D2.y;
     if (NA > 6) {
-      s[6] = s[3] * dx;
-      s[7] = s[3] * dy;
-      s[8] = s[4] * dy;
-      s[9] = s[5] * dy;
-      s[10] = s[3] * s[3];
-      s[11] = s[3] * s[4];
-      s[12] = s[3] * s[5];
-      s[13] = s[4] * s[5];
-      s[14] = s[5] * s[5];
+      const float2 SW = make_float2(D.y, D.x);
+      const float2 P3 = __fmul2_rn(D2, D);    // (x^3, y^3)
+      const float2 P21 = __fmul2_rn(D2, SW);  // (x^2 y, x y^2)
+      const float2 P4 = __fmul2_rn(D2, D2);   // (x^4, y^4)
+      const float2 P31 = __fmul2_rn(P3, SW);  // (x^3 y, x y^3)
+      s[6] = P3.x;
+      s[7] = P21.x;
+      s[8] = P21.y;
+      s[9] = P3.y;
+      s[10] = P4.x;
+      s[11] = P31.x;
+      s[12] = s[4] * s[4];
+      s[13] = P31.y;
+      s[14] = P4.y;
     }
     ak[0] = __fadd2_rn(ak[0], W);
 #pragma unroll
     for (int i = 1; i < NA; i++) ak[i] = __ffma2_rn(W, make_float2(s[i], s[i]), ak[i]);
     b[0] += wf;
+    cnt += 1.f;
 #pragma unroll
     for (int i = 1; i < NB; i++) b[i] = fmaf(wf, s[i], b[i]);
-    cnt += 1.f;
   }
 
   template <typename T>
@@ -462,19 +473,22 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
       }
       const float Dy = 2.f * (float)(jlo + r) - ry;
       const float dxr = fmaf(a00, Dx0, a01 * Dy), dyr = fmaf(a10, Dx0, a11 * Dy);
+      const float2 DR = make_float2(dxr, dyr);
       const float2 *rowp = pl + pr * PW + pc0;
       float qf = 0.f;
+      const float2 S2 = make_float2(sx, sy);
       // two samples in flight pay off only for the long order-2 bodies
       constexpr int kUnroll = ORDER == 2 ? 2 : 1;
 #pragma unroll kUnroll
       for (int q = 0; q < NI; q++, qf += 1.f) {
-        const float dx = fmaf(qf, sx, dxr), dy = fmaf(qf, sy, dyr);
-        const float r2 = fmaf(dx, dx, dy * dy);
+        const float2 D = __ffma2_rn(make_float2(qf, qf), S2, DR);
+        const float2 D2 = __fmul2_rn(D, D);
+        const float r2 = D2.x + D2.y;
         const float2 fv = rowp[q];
         if (r2 < R2 && fv.y > 0.f) {
           const float K = ex2_approx(r2 * cexp) - taper;  // Eq. 8, truncated and tapered
           const float w = K * fv.y;                       // window x inverse variance
-          m.add(dx, dy, w, w * fv.x, w * K);
+          m.add2(D, D2, w, w * fv.x, w * K);
         }
       }
     }
