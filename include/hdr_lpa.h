@@ -240,6 +240,14 @@ void hdr_server_destroy(hdr_server *srv);
  * CUDA error, else HDR_OK. */
 hdr_status hdr_check(hdr_ctx *ctx, void *cuda_stream);
 
+/* Self-test of failure detection (no counterpart in the paper): launches one block whose bounded
+ * wait can never complete (an mbarrier expecting bytes that no copy delivers); the wait gives up
+ * within about 0.1 s and sets the same device status a reconstruction whose staging copies never
+ * land would set. Nothing faults or hangs: the next hdr_check on that stream returns HDR_E_TIMEOUT
+ * and clears the status, reconstructions launched before that check retire without writing, and
+ * the context stays usable. Asynchronous on `cuda_stream`. */
+hdr_status hdr_selftest_timeout(hdr_ctx *ctx, void *cuda_stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *hdr_last_error(void);
 

@@ -60,3 +60,6 @@ inline int lpa_batch_ctas_per_sm(int order, bool comp, int tile_h, uint32_t smem
          : order == 1 ? lpa_batch_ctas_per_sm_order1(comp, tile_h, smem_bytes)
                       : lpa_batch_ctas_per_sm_order2(comp, tile_h, smem_bytes);
 }
+
+// One-thread self-test of the bounded wait (sets LPA_ERR_TIMEOUT in *status).
+cudaError_t lpa_launch_selftest_wait(unsigned int *status, cudaStream_t st);

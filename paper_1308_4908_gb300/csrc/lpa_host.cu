@@ -547,6 +547,13 @@ hdr_status hdr_check(hdr_ctx *ctx, void *cuda_stream) {
   return HDR_OK;
 }
 
+hdr_status hdr_selftest_timeout(hdr_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return fail(HDR_E_INVALID, "ctx is NULL");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  CUDA_TRY(lpa_launch_selftest_wait(ctx->status, (cudaStream_t)cuda_stream));
+  return HDR_OK;
+}
+
 const char *hdr_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"

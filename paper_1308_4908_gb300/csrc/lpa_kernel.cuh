@@ -82,6 +82,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase,
   return false;
 }
 
+// try_wait with a suspend-time hint in nanoseconds (the wait returns no later than about then)
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t phase, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Order this thread's later tensor-map uses after earlier generic writes of the 128-byte map at
 // `map` (global memory).
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map) {
@@ -744,6 +757,21 @@ __global__ void __launch_bounds__(LPA_TILE *TH, (BatchOccupancy<ORDER, TH>::valu
                                                                fp_x0, fp_y0, anchors);
     if (!__syncthreads_and(ok)) break;
     phase ^= 1u;
+  }
+}
+
+// Self-test of the bounded wait: an mbarrier that expects 16 bytes no copy will deliver. The wait
+// gives up after `limit` tries or `max_cycles` clock cycles, whichever comes first, and reports
+// LPA_ERR_TIMEOUT in the status word exactly as a reconstruction whose copies never land would.
+static __global__ void lpa_selftest_wait(unsigned int *status, uint32_t limit, long long max_cycles) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_arrive_expect_tx(&bar, 16);
+    const long long t0 = clock64();
+    bool done = false;
+    for (uint32_t i = 0; i < limit && !done && clock64() - t0 < max_cycles; ++i) done = mbar_try_wait_hint(&bar, 0, 1000);
+    if (!done) atomicOr(status, LPA_ERR_TIMEOUT);
   }
 }
 

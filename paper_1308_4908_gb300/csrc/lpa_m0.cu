@@ -58,3 +58,8 @@ const void *lpa_kernel_order0(bool comp, bool diag, int tile_h) {
   if (comp) return diag ? (const void *)lpa::lpa_reconstruct<0, true, true, 16> : (const void *)lpa::lpa_reconstruct<0, true, false, 16>;
   return diag ? (const void *)lpa::lpa_reconstruct<0, false, true, 16> : (const void *)lpa::lpa_reconstruct<0, false, false, 16>;
 }
+
+cudaError_t lpa_launch_selftest_wait(unsigned int *status, cudaStream_t st) {
+  lpa::lpa_selftest_wait<<<1, 32, 0, st>>>(status, 4096u, 200000000ll);  // ~0.1 s at 2 GHz at most
+  return cudaGetLastError();
+}

@@ -388,7 +388,8 @@ hdr_status hdr_submit(hdr_server *srv, const hdr_request *req, uint64_t *ticket)
   if (ns == 0) return lpa_fail(HDR_E_INVALID, "rig is not defined");
   hdr_status st = lpa_check_params(&req->params);
   if (st) return st;
-  if (!req->out_host) return lpa_fail(HDR_E_INVALID, "out_host is NULL");
+  if (!req->out_host && (long long)req->params.out_w * req->params.out_h > 0)
+    return lpa_fail(HDR_E_INVALID, "out_host is NULL");
   for (int s = 0; s < ns; s++)
     if (!req->raw_host[s]) return lpa_fail(HDR_E_INVALID, "raw_host pointer is NULL");
   Job j;

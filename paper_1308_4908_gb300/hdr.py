@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.hdr_reconstruct_levels.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
     lib.hdr_reconstruct_host.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
     lib.hdr_check.argtypes = [_P, _P]
+    lib.hdr_selftest_timeout.argtypes = [_P, _P]
     lib.hdr_reconstruct_noalloc.argtypes = [ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
     lib.hdr_reconstruct_batch.argtypes = [_P, ctypes.c_int32, _P, _P, _P]
     lib.hdr_tune_batch.argtypes = [_P, ctypes.c_int32, _P, _P, _P]
@@ -122,7 +123,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.hdr_last_error.restype = ctypes.c_char_p
     for name in ("hdr_create", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_levels", "hdr_reconstruct_host",
                  "hdr_check", "hdr_reconstruct_noalloc", "hdr_reconstruct_batch", "hdr_tune_batch",
-                 "hdr_server_create", "hdr_submit", "hdr_poll", "hdr_server_stats_get"):
+                 "hdr_server_create", "hdr_submit", "hdr_poll", "hdr_server_stats_get", "hdr_selftest_timeout"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -182,6 +183,11 @@ def hdr_reconstruct_host(ctx: int, rig_id: int, params: hdr_params, raw_host: Se
 
 def hdr_check(ctx: int, stream: Optional[int] = None) -> None:
     _check(load().hdr_check(ctypes.c_void_p(ctx), ctypes.c_void_p(stream)))
+
+
+def hdr_selftest_timeout(ctx: int, stream: Optional[int] = None) -> None:
+    """Launch the bounded-wait self-test: the next hdr_check on that stream reports HDR_E_TIMEOUT."""
+    _check(load().hdr_selftest_timeout(ctypes.c_void_p(ctx), ctypes.c_void_p(stream)))
 
 
 def hdr_last_error() -> str:
@@ -369,6 +375,9 @@ class Context:
 
     def check(self, stream=None):
         hdr_check(self.handle, self._stream(stream))
+
+    def selftest_timeout(self, stream=None):
+        hdr_selftest_timeout(self.handle, self._stream(stream))
 
 
 class Server:

@@ -130,3 +130,15 @@ def test_batch_rejects_bad_input(ctx):
         ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(12, 0, 1, 0))
     with pytest.raises(hdr.HdrError):
         ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(16, 0, 1, 2))
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_batch_with_empty_and_one_pixel_frames(ctx, form):
+    import dataclasses
+    from paper_1308_4908_gb300 import hdr
+    frames = synth.batching(n_frames=3, size_cap=64, seed=2006)
+    frames[0] = dataclasses.replace(frames[0], params=dataclasses.replace(frames[0].params, out_w=0, out_h=0))
+    frames[1] = dataclasses.replace(frames[1], params=dataclasses.replace(frames[1].params, out_w=1, out_h=1))
+    items = _prepare(ctx, frames, base_rig=56)
+    refs = _single(ctx, items)
+    _same(_batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form)), refs)

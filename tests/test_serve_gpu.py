@@ -168,3 +168,24 @@ def test_busy_until_done_and_fp16_output(ctx, streams):
     ctx.reconstruct(20, hp, [torch.from_numpy(s.raw).cuda() for s in big.sensors], out=ref)
     ctx.check()
     np.testing.assert_array_equal(out, ref.cpu().numpy())
+
+
+def test_empty_and_tiny_outputs(ctx, streams):
+    """A 0x0 output completes without a step; a 1x1 output is one ragged tile."""
+    import dataclasses
+    from paper_1308_4908_gb300 import hdr
+    fr = streams[0][0]
+    raws = [np.ascontiguousarray(s.raw) for s in fr.sensors]
+    srv = hdr.Server(ctx, pool_bytes=64 << 20)
+    try:
+        p0 = dataclasses.replace(fr.params, out_w=0, out_h=0)
+        t0 = srv.submit(0, p0, raws, np.zeros((3, 0, 0), np.float32))
+        p1 = dataclasses.replace(fr.params, out_w=1, out_h=1)
+        one = np.full((3, 1, 1), -7.0, np.float32)
+        t1 = srv.submit(0, p1, raws, one)
+        assert srv.poll(t0, -1).steps == 0
+        assert srv.poll(t1, -1).steps == 1
+    finally:
+        srv.close()
+    ref = _plain(ctx, 0, dataclasses.replace(fr, params=p1))
+    np.testing.assert_array_equal(one, ref[0])
