@@ -116,6 +116,9 @@ struct hdr_ctx {
   size_t out_cap = 0;
   uint8_t *choice_stage = nullptr;
   size_t choice_cap = 0;
+  // copy streams and band events of the host-buffer entry point (created on first use)
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_in[8] = {}, ev_done[8] = {};
 };
 
 namespace {
@@ -414,6 +417,12 @@ void hdr_destroy(hdr_ctx *ctx) {
   for (int s = 0; s < HDR_MAX_SENSORS; s++) cudaFree(ctx->raw_stage[s]);
   cudaFree(ctx->out_stage);
   cudaFree(ctx->choice_stage);
+  if (ctx->h2d) cudaStreamDestroy(ctx->h2d);
+  if (ctx->d2h) cudaStreamDestroy(ctx->d2h);
+  for (int b = 0; b < 8; b++) {
+    if (ctx->ev_in[b]) cudaEventDestroy(ctx->ev_in[b]);
+    if (ctx->ev_done[b]) cudaEventDestroy(ctx->ev_done[b]);
+  }
   cudaFree(ctx->status);
   for (auto &g : ctx->batch.graphs) cudaGraphExecDestroy(g.second);
   for (auto &g : ctx->batch.frame_graphs) {
@@ -504,11 +513,12 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
       CUDA_TRY(cudaMalloc(&ctx->raw_stage[s], bytes));
       ctx->raw_cap[s] = bytes;
     }
-    CUDA_TRY(cudaMemcpyAsync(ctx->raw_stage[s], raw_host[s], bytes, cudaMemcpyHostToDevice, stream));
     raw_dev[s] = ctx->raw_stage[s];
   }
-  const size_t npx = (size_t)params->out_w * params->out_h * 3;
-  const size_t obytes = npx * (params->out_dtype ? 2 : 4);
+  const size_t plane = (size_t)params->out_w * params->out_h;
+  const size_t npx = plane * 3;
+  const size_t esize = params->out_dtype ? 2 : 4;
+  const size_t obytes = npx * esize;
   if (ctx->out_cap < obytes) {
     CUDA_TRY(cudaStreamSynchronize(stream));
     cudaFree(ctx->out_stage);
@@ -525,11 +535,76 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
     CUDA_TRY(cudaMalloc(&ctx->choice_stage, npx));
     ctx->choice_cap = npx;
   }
-  st = reconstruct_impl(ctx, rig_id, params, raw_dev, ctx->out_stage, choice_host ? ctx->choice_stage : nullptr,
-                        nullptr, cuda_stream);
+  LpaLaunch L;
+  st = plan(ctx, rig, params, raw_dev, L);
   if (st) return st;
-  if (obytes) CUDA_TRY(cudaMemcpyAsync(out_host, ctx->out_stage, obytes, cudaMemcpyDeviceToHost, stream));
-  if (choice_host && npx) CUDA_TRY(cudaMemcpyAsync(choice_host, ctx->choice_stage, npx, cudaMemcpyDeviceToHost, stream));
+  L.out = ctx->out_stage;
+  L.choice = choice_host ? ctx->choice_stage : nullptr;
+  L.levels = nullptr;
+  if (!ctx->h2d) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking));
+    for (int b = 0; b < 8; b++) {
+      CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_in[b], cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_done[b], cudaEventDisableTiming));
+    }
+  }
+  // Bands of tile rows: the raw rows a band's windows can reach are copied in (on the copy
+  // stream) while the previous band is reconstructed, and a finished band's output rows are
+  // copied out while the next one is reconstructed.
+  const int rows = L.tiles_y;
+  const int nb = rows >= 32 ? 4 : 1;
+  size_t have[HDR_MAX_SENSORS] = {};
+  CUDA_TRY(cudaEventRecord(ctx->ev_done[0], stream));  // the copies start after earlier work on `stream`
+  CUDA_TRY(cudaStreamWaitEvent(ctx->h2d, ctx->ev_done[0], 0));
+  for (int b = 0; b < nb; b++) {
+    const int r0 = rows * b / nb, r1 = rows * (b + 1) / nb;
+    const int v0 = r0 * L.tile_h, v1 = std::min(r1 * L.tile_h, params->out_h);
+    for (int s = 0; s < rig.n; s++) {
+      const LpaSensorK &Sk = L.s[s];
+      const int H = rig.s[s].d.height;
+      size_t need = (size_t)H;
+      if (b + 1 < nb) {  // the last band takes every remaining row
+        double ymax = -1e300;
+        for (int k = 0; k < 4; k++) {
+          const double uu = (k & 1) ? params->out_w - 1 : 0, vv = (k & 2) ? v1 - 1 : v0;
+          ymax = std::max(ymax, Sk.G[3] * uu + Sk.G[4] * vv + Sk.G[5]);
+        }
+        // every staged box row of the band's tiles lies below the lowest window row + box height
+        const double lim = std::min<double>(H, std::max(0.0, std::ceil(ymax) + Sk.box_h + 2));
+        need = std::max(have[s], (size_t)lim);
+      }
+      if (need > have[s]) {
+        const size_t row_bytes = (size_t)rig.s[s].d.pitch_elems * 2;
+        CUDA_TRY(cudaMemcpyAsync(ctx->raw_stage[s] + have[s] * rig.s[s].d.pitch_elems,
+                                 raw_host[s] + have[s] * rig.s[s].d.pitch_elems, (need - have[s]) * row_bytes,
+                                 cudaMemcpyHostToDevice, ctx->h2d));
+        have[s] = need;
+      }
+    }
+    CUDA_TRY(cudaEventRecord(ctx->ev_in[b], ctx->h2d));
+    CUDA_TRY(cudaStreamWaitEvent(stream, ctx->ev_in[b], 0));
+    L.tile0 = r0 * L.tiles_x;
+    L.tile_count = (r1 - r0) * L.tiles_x;
+    if (L.tile_count > 0) {
+      st = launch(L, params->accum, false, stream);
+      if (st) return st;
+    }
+    CUDA_TRY(cudaEventRecord(ctx->ev_done[b], stream));
+    CUDA_TRY(cudaStreamWaitEvent(ctx->d2h, ctx->ev_done[b], 0));
+    if (v1 > v0) {
+      const size_t off = (size_t)v0 * params->out_w, n = (size_t)(v1 - v0) * params->out_w;
+      for (int c = 0; c < 3; c++) {
+        CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(out_host) + (c * plane + off) * esize,
+                                 static_cast<char *>(ctx->out_stage) + (c * plane + off) * esize, n * esize,
+                                 cudaMemcpyDeviceToHost, ctx->d2h));
+        if (choice_host)
+          CUDA_TRY(cudaMemcpyAsync(choice_host + c * plane + off, ctx->choice_stage + c * plane + off, n,
+                                   cudaMemcpyDeviceToHost, ctx->d2h));
+      }
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(ctx->d2h));
   CUDA_TRY(cudaStreamSynchronize(stream));
   return HDR_OK;
 }

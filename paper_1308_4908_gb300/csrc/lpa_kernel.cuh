@@ -439,6 +439,31 @@ struct Anchor {
   float fx, fy;
 };
 
+// One window cell: offset D from the pixel's point, disc test, Eq. 8 weight times inverse
+// variance, moment update.
+template <class MOM>
+__device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R2, float cexp, float taper) {
+  const float2 D2 = __fmul2_rn(D, D);
+  const float r2 = D2.x + D2.y;
+  if (r2 < R2 && fv.y > 0.f) {
+    const float K = ex2_approx(r2 * cexp) - taper;  // Eq. 8, truncated and tapered
+    const float w = K * fv.y;                       // window x inverse variance
+    m.add2(D, D2, w, w * fv.x, w * K);
+  }
+}
+
+// The n cells of one row: cell q is at D = DR + q S2. (Fully unrolled rows dispatched on n were
+// measured slower.)
+template <int ORDER, class MOM>
+__device__ __forceinline__ void row_cells(MOM &m, const float2 *rowp, int n, float2 DR, float2 S2, float R2,
+                                          float cexp, float taper) {
+  float qf = 0.f;
+  // two samples in flight pay off only for the long order-2 bodies
+  constexpr int kUnroll = ORDER == 2 ? 2 : 1;
+#pragma unroll kUnroll
+  for (int q = 0; q < n; q++, qf += 1.f) window_cell(m, __ffma2_rn(make_float2(qf, qf), S2, DR), rowp[q], R2, cexp, taper);
+}
+
 template <int ORDER, bool COMP>
 __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COMP>::type &m, const LpaSensorK &S,
                                                   const Anchor &an, int du, int dv, int c, float R, float R2,
@@ -488,22 +513,8 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
       const float dxr = fmaf(a00, Dx0, a01 * Dy), dyr = fmaf(a10, Dx0, a11 * Dy);
       const float2 DR = make_float2(dxr, dyr);
       const float2 *rowp = pl + pr * PW + pc0;
-      float qf = 0.f;
       const float2 S2 = make_float2(sx, sy);
-      // two samples in flight pay off only for the long order-2 bodies
-      constexpr int kUnroll = ORDER == 2 ? 2 : 1;
-#pragma unroll kUnroll
-      for (int q = 0; q < NI; q++, qf += 1.f) {
-        const float2 D = __ffma2_rn(make_float2(qf, qf), S2, DR);
-        const float2 D2 = __fmul2_rn(D, D);
-        const float r2 = D2.x + D2.y;
-        const float2 fv = rowp[q];
-        if (r2 < R2 && fv.y > 0.f) {
-          const float K = ex2_approx(r2 * cexp) - taper;  // Eq. 8, truncated and tapered
-          const float w = K * fv.y;                       // window x inverse variance
-          m.add2(D, D2, w, w * fv.x, w * K);
-        }
-      }
+      row_cells<ORDER>(m, rowp, NI, DR, S2, R2, cexp, taper);
     }
   }
 }

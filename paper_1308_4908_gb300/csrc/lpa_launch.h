@@ -57,6 +57,7 @@ struct LpaLaunch {
   uint32_t smem_bytes;
   int tile_h;                    // tile height the plan was made for
   int tile0;                     // single-frame grid: CTA b reconstructs tile tile0 + b
+  int tile_count;                // single-frame grid size; 0 = every tile from tile0 on
 };
 
 // Several frames in one graph launch: the tile list is grouped by polynomial order and each

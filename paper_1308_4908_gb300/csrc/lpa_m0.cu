@@ -8,7 +8,8 @@ static cudaError_t launch_one(const LpaLaunch &L, cudaStream_t st) {
   auto k = lpa::lpa_reconstruct<0, COMP, DIAG, TH>;
   cudaError_t e = lpa_opt_in((const void *)k);
   if (e != cudaSuccess) return e;
-  k<<<L.tiles_x * L.tiles_y, LPA_TILE * TH, L.smem_bytes, st>>>(L);
+  const int grid = L.tile_count > 0 ? L.tile_count : L.tiles_x * L.tiles_y - L.tile0;
+  k<<<grid, LPA_TILE * TH, L.smem_bytes, st>>>(L);
   return cudaGetLastError();
 }
 

@@ -251,6 +251,34 @@ def test_host_buffer_entry_point_matches(ctx):
     np.testing.assert_array_equal(ch, a["choice"])
 
 
+@pytest.mark.parametrize("case", ["paper", "rotated6", "upsampled", "half"])
+def test_host_buffer_bands_match_the_device_path(ctx, case):
+    """Outputs of 32+ tile rows go through the host-buffer entry point in row bands (copies in and
+    out overlapped with the reconstruction): results equal the device-buffer entry point's, also
+    for rotated rigs and resampled outputs whose windows reach rows of the next band."""
+    fr = synth.paper_scale(size=640, seed=1095)
+    W = 640
+    p = fr.params
+    if case == "rotated6":
+        affs = [synth.affine_about_center(W, W), synth.affine_about_center(W, W, 0.3, -0.2, 6.0),
+                synth.affine_about_center(W, W, -0.5, 0.1, -6.0)]
+        for s, a in zip(fr.sensors, affs):
+            s.affine = np.asarray(a)
+            s.raw = synth.simulate_raw(fr.scene, s, 1095, int(s.nd * 1000))
+    elif case == "upsampled":
+        p = dataclasses.replace(p, out_w=960, out_h=720, out_affine=synth.output_affine(W, W, 960, 720))
+    elif case == "half":
+        p = dataclasses.replace(p, out_dtype=1)
+    a = run(ctx, fr, p)
+    dt = np.float16 if case == "half" else np.float32
+    out = np.full((3, p.out_h, p.out_w), -7.0, dt)
+    ch = np.zeros((3, p.out_h, p.out_w), np.uint8)
+    ctx.reconstruct_host(0, p, [np.ascontiguousarray(s.raw) for s in fr.sensors], out, ch)
+    ctx.check()
+    np.testing.assert_array_equal(out.astype(np.float32), a["out"])
+    np.testing.assert_array_equal(ch, a["choice"])
+
+
 def test_invalid_arguments_are_rejected(ctx):
     from paper_1308_4908_gb300 import hdr
     fr = synth.tiny()
