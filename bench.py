@@ -479,6 +479,46 @@ def run_precision_study(args):
                       "sample_pixels": n_pix, "rows": rows}), flush=True)
 
 
+def run_tiny_study(args):
+    """The tiny configuration (2 x 64^2 raw, order 0, sigma 0.7, 64^2 output): GPU time per frame
+    (launch-bound at this size), the oracle on the host cores over the whole frame, and the
+    largest error against it. One JSON line."""
+    import torch
+    import oracle
+    from paper_1308_4908_gb300 import hdr, synth
+    oracle.build()
+    fr = synth.tiny()
+    p = fr.params
+    ctx = hdr.Context(0)
+    ctx.set_rig(0, fr.sensors)
+    raws = [torch.from_numpy(s.raw).cuda() for s in fr.sensors]
+    out = ctx.reconstruct(0, p, raws)
+    reps = 200
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(10):
+        ctx.reconstruct(0, p, raws, out=out)
+    e0.record(st)
+    for _ in range(reps):
+        ctx.reconstruct(0, p, raws, out=out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = e0.elapsed_time(e1) / reps
+    t0 = time.perf_counter()
+    o = oracle.reconstruct(fr.sensors, p)
+    dt = time.perf_counter() - t0
+    g = out.cpu().numpy()
+    rel = np.abs(g - o["out"]) / np.maximum(np.abs(o["out"]), 1e-2)
+    px = p.out_w * p.out_h
+    ctx.close()
+    print(json.dumps({"study": "tiny", "workload": "2 x 64^2 raw (ND 1, 1/8), order 0, sigma 0.7, 64^2 output",
+                      "gpu_ms_per_frame": round(ms, 4), "gpu_mpx_s": round(px / ms / 1e3, 2),
+                      "oracle_s": round(dt, 4), "oracle_mpx_s": round(px / dt / 1e6, 4),
+                      "oracle_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                      "max_rel_err": float(np.nanmax(rel)), "median_rel_err": float(np.nanmedian(rel))}), flush=True)
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
@@ -609,13 +649,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--size", type=int, default=2048, help="raw and output edge (2048 = the paper-scale workload)")
     ap.add_argument("--headline-only", action="store_true", help="skip the batching and serving measurements")
-    ap.add_argument("--study", choices=["precision"], default=None, help="print a study instead of the bench line")
+    ap.add_argument("--study", choices=["precision", "tiny"], default=None, help="print a study instead of the bench line")
     ap.add_argument("--study-pixels", type=int, default=20000)
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson arrival schedule")
     ap.add_argument("--step-tiles", type=int, default=8192, help="tile budget of one serving step (0 = all pending)")
     args = ap.parse_args()
     if args.study == "precision":
         run_precision_study(args)
+        return
+    if args.study == "tiny":
+        run_tiny_study(args)
         return
     world, rank, local, pg = dist_setup(args)
     try:
