@@ -146,6 +146,19 @@ struct Moments {
   }
 
   __device__ __forceinline__ void add2(float2 D, float2 D2, float w, float wf, float wk) { add(D.x, D.y, w, wf, wk); }
+  // order 0: the three sums and the sample count (`one` is 1 for a window sample, else 0)
+  __device__ __forceinline__ void add0(float w, float wf, float wk, float one) {
+    if (COMP) {
+      comp_add(a[0], al[0], w, 1.f);
+      comp_add(k[0], kl[0], wk, 1.f);
+      comp_add(b[0], bl[0], wf, 1.f);
+    } else {
+      a[0] += w;
+      k[0] += wk;
+      b[0] += wf;
+    }
+    cnt += one;
+  }
 
   __device__ __forceinline__ void add(float dx, float dy, float w, float wf, float wk) {
     float m[15];
@@ -441,13 +454,19 @@ struct Anchor {
 
 // One window cell: offset D from the pixel's point, disc test, Eq. 8 weight times inverse
 // variance, moment update.
-template <class MOM>
+template <int ORDER, class MOM>
 __device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R2, float cexp, float taper) {
   const float2 D2 = __fmul2_rn(D, D);
   const float r2 = D2.x + D2.y;
-  if (r2 < R2 && fv.y > 0.f) {
+  const bool in = r2 < R2 && fv.y > 0.f;
+  if constexpr (ORDER == 0) {
+    // four sums: cheaper to add exact zeros for cells outside the window than to branch
     const float K = ex2_approx(r2 * cexp) - taper;  // Eq. 8, truncated and tapered
-    const float w = K * fv.y;                       // window x inverse variance
+    const float w = in ? K * fv.y : 0.f;            // window x inverse variance
+    m.add0(w, w * fv.x, w * K, in ? 1.f : 0.f);
+  } else if (in) {
+    const float K = ex2_approx(r2 * cexp) - taper;
+    const float w = K * fv.y;
     m.add2(D, D2, w, w * fv.x, w * K);
   }
 }
@@ -461,7 +480,8 @@ __device__ __forceinline__ void row_cells(MOM &m, const float2 *rowp, int n, flo
   // two samples in flight pay off only for the long order-2 bodies
   constexpr int kUnroll = ORDER == 2 ? 2 : 1;
 #pragma unroll kUnroll
-  for (int q = 0; q < n; q++, qf += 1.f) window_cell(m, __ffma2_rn(make_float2(qf, qf), S2, DR), rowp[q], R2, cexp, taper);
+  for (int q = 0; q < n; q++, qf += 1.f)
+    window_cell<ORDER>(m, __ffma2_rn(make_float2(qf, qf), S2, DR), rowp[q], R2, cexp, taper);
 }
 
 template <int ORDER, bool COMP>
