@@ -300,33 +300,32 @@ struct FitOut {
   bool valid;
 };
 
-__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.f, x); }
 __device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
 
-// Eq. 6 for the first P basis functions: A = Phi^T W Phi is Jacobi-equilibrated
-// (D A D, D = diag(A)^{-1/2}) and factored LDL^T; l = A^{-1} e_0, C_0 = l^T b,
-// Var C_0 = l^T (Phi^T W S W Phi) l with S the sample variances.
-__host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
+// packed lower-triangle index (i >= j)
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// Eq. 6 for the first P basis functions: the normal matrix A = Phi^T W Phi is factored LDL^T as
+// it stands. Usability and the condition estimate are judged on the pivots of the
+// Jacobi-equilibrated matrix D A D (D = diag(A)^{-1/2}), which are d_j / A_jj: equilibration
+// changes L but scales each pivot by 1 / A_jj. l = A^{-1} e_0, C_0 = l^T b,
+// Var C_0 = l^T (Phi^T W S W Phi) l with S the sample variances.
 template <typename T, int P, class MOM>
 __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
   FitOut r;
-  T s[P];
-  bool pos = true;
-#pragma unroll
-  for (int i = 0; i < P; i++) {
-    T d = m.template A<T>(mono_index(2 * ex(i), 2 * ey(i)));
-    pos = pos && (d > T(0));
-    s[i] = d > T(0) ? rsqrt_t(d) : T(0);
-  }
-  // equilibrated matrix, lower triangle, overwritten by L (below the diagonal) and D
-  T a[P * (P + 1) / 2];
+  T a[P * (P + 1) / 2];  // lower triangle, overwritten by L (below the diagonal) and D
 #pragma unroll
   for (int i = 0; i < P; i++)
 #pragma unroll
-    for (int j = 0; j <= i; j++) a[tri(i, j)] = m.template A<T>(mono_index(ex(i) + ex(j), ey(i) + ey(j))) * s[i] * s[j];
+    for (int j = 0; j <= i; j++) a[tri(i, j)] = m.template A<T>(mono_index(ex(i) + ex(j), ey(i) + ey(j)));
+  T rdiag[P];
+  bool pos = true;
+#pragma unroll
+  for (int i = 0; i < P; i++) {
+    pos = pos && (a[tri(i, i)] > T(0));
+    rdiag[i] = a[tri(i, i)] > T(0) ? rcp_t(a[tri(i, i)]) : T(0);
+  }
   // triangular loops are written with fixed trip counts and guards so that they unroll fully
   T dinv[P];
   T dmin = T(1e30), dmax = T(0);
@@ -337,8 +336,9 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
     for (int q = 0; q < P; q++)
       if (q < j) dj -= a[tri(j, q)] * a[tri(j, q)] * a[tri(q, q)];
     a[tri(j, j)] = dj;
-    dmin = dj < dmin ? dj : dmin;
-    dmax = dj > dmax ? dj : dmax;
+    const T de = dj * rdiag[j];  // pivot of the equilibrated matrix
+    dmin = de < dmin ? de : dmin;
+    dmax = de > dmax ? de : dmax;
     dinv[j] = dj > T(0) ? rcp_t(dj) : T(0);
 #pragma unroll
     for (int i = 0; i < P; i++) {
@@ -354,11 +354,11 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
   r.dmin = (float)dmin;
   r.dmax = (float)dmax;
   r.valid = pos && (m.cnt >= (float)P) && (dmin > (T)min_pivot);
-  // l = D (D A D)^{-1} D e_0: forward (unit L), diagonal, backward (L^T)
+  // l = A^{-1} e_0: forward (unit L), diagonal, backward (L^T)
   T x[P];
 #pragma unroll
   for (int i = 0; i < P; i++) {
-    T t = (i == 0) ? s[0] : T(0);
+    T t = (i == 0) ? T(1) : T(0);
 #pragma unroll
     for (int q = 0; q < P; q++)
       if (q < i) t -= a[tri(i, q)] * x[q];
@@ -378,12 +378,11 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
   T c0 = T(0), var = T(0);
 #pragma unroll
   for (int i = 0; i < P; i++) {
-    const T li = s[i] * x[i];
-    c0 += li * m.template B<T>(i);
+    c0 += x[i] * m.template B<T>(i);
     T row = T(0);
 #pragma unroll
-    for (int j = 0; j < P; j++) row += s[j] * x[j] * m.template Kv<T>(mono_index(ex(i) + ex(j), ey(i) + ey(j)));
-    var += li * row;
+    for (int j = 0; j < P; j++) row += x[j] * m.template Kv<T>(mono_index(ex(i) + ex(j), ey(i) + ey(j)));
+    var += x[i] * row;
   }
   r.c0 = (float)c0;
   r.var = (float)var;
