@@ -519,6 +519,60 @@ def run_tiny_study(args):
                       "max_rel_err": float(np.nanmax(rel)), "median_rel_err": float(np.nanmedian(rel))}), flush=True)
 
 
+def run_tab_study(args):
+    """Tabulated window weights (Section 8) against the searched window on the translational case:
+    the paper-scale rig with pure sub-pixel translations (no rotation or scale) at 1x output, orders
+    0, 1, 2 with the interval rule over 4 scales. GPU time per frame of both paths and the largest
+    error of each against the oracle on sampled pixels. One JSON line."""
+    import dataclasses
+    import torch
+    import oracle
+    from paper_1308_4908_gb300 import hdr, synth
+    oracle.build()
+    fr = synth.paper_scale(size=args.size)
+    r = np.random.default_rng(1007)
+    for s in fr.sensors:
+        tx, ty = r.uniform(-1.5, 1.5, 2)
+        s.affine = np.asarray(synth.affine_about_center(args.size, args.size, tx, ty))
+        s.raw = synth.simulate_raw(fr.scene, s, 1007, int(s.nd * 1000))
+    ctx = hdr.Context(0)
+    ctx.set_rig(0, fr.sensors)
+    raws = [torch.from_numpy(s.raw).cuda() for s in fr.sensors]
+    pix = np.stack([r.integers(0, fr.params.out_w, 2000), r.integers(0, fr.params.out_h, 2000)], axis=1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rows = []
+    for order in (0, 1, 2):
+        row = {"order": order}
+        o = oracle.reconstruct(fr.sensors, dataclasses.replace(fr.params, order=order), pix)
+        for tab in (1, 0):
+            p = dataclasses.replace(fr.params, order=order, tab_weights=tab)
+            out = ctx.reconstruct(0, p, raws)
+            st = torch.cuda.current_stream()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for k in range(10):
+                flush.fill_(k)
+                ev[k][0].record(st)
+                ctx.reconstruct(0, p, raws, out=out)
+                ev[k][1].record(st)
+            torch.cuda.synchronize()
+            ctx.check()
+            ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+            g = out.cpu().numpy()[:, pix[:, 1], pix[:, 0]].T
+            ok = np.isfinite(o["out"]) & np.isfinite(g)
+            rel = np.abs(g - o["out"])[ok] / np.maximum(np.abs(o["out"][ok]), 1e-2)
+            key = "tabulated" if tab else "searched"
+            row[key] = {"ms": round(ms, 3), "mpx_s": round(p.out_w * p.out_h / ms / 1e3, 1),
+                        "max_rel_err": float(rel.max()), "median_rel_err": float(np.median(rel))}
+        row["speedup"] = round(row["searched"]["ms"] / row["tabulated"]["ms"], 3)
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    ctx.close()
+    print(json.dumps({"study": "tabulated weights", "workload": f"3 x {args.size}^2 RGGB, pure translations "
+                      "U(-1.5, 1.5) px, 1x output, 4 scales with the interval rule",
+                      "error": "|gpu - oracle| / max(|oracle|, 1e-2) on 2000 random pixels x 3 channels",
+                      "rows": rows}), flush=True)
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
@@ -649,7 +703,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--size", type=int, default=2048, help="raw and output edge (2048 = the paper-scale workload)")
     ap.add_argument("--headline-only", action="store_true", help="skip the batching and serving measurements")
-    ap.add_argument("--study", choices=["precision", "tiny"], default=None, help="print a study instead of the bench line")
+    ap.add_argument("--study", choices=["precision", "tiny", "tabweights"], default=None,
+                    help="print a study instead of the bench line")
     ap.add_argument("--study-pixels", type=int, default=20000)
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson arrival schedule")
     ap.add_argument("--step-tiles", type=int, default=8192, help="tile budget of one serving step (0 = all pending)")
@@ -659,6 +714,9 @@ def main():
         return
     if args.study == "tiny":
         run_tiny_study(args)
+        return
+    if args.study == "tabweights":
+        run_tab_study(args)
         return
     world, rank, local, pg = dist_setup(args)
     try:

@@ -90,11 +90,20 @@ typedef struct {
   double out_affine[6];       /* output px -> reference px, row-major 2x3 (Section 4.2)    */
   int32_t out_dtype;          /* 0 = float32, 1 = float16; planar [3][out_h][out_w]        */
   int32_t accum;              /* 0 = plain FP32 moment sums, 1 = compensated (two-sum)     */
+  int32_t tab_weights;        /* 1 = tabulated window weights where the rig allows (default),
+                                 0 = never. Section 8: when every sensor is a pure translation of
+                                 the reference frame and the output mapping is a translation at
+                                 1x, all output pixels of one parity class see the same window
+                                 offsets in each colour phase, so the window cells, offsets and
+                                 weights are tabulated once per frame and the kernel reads them
+                                 instead of searching and evaluating each window. The fit is the
+                                 same; only rounding differs. */
 } hdr_params;
 
 /* Fill *p with the defaults: order 2, scales {0.5, 0.8, 1.2, 1.8}, green_ratio 1/sqrt(2),
  * trunc_k 3, ici_gamma 2, min_pivot 1e-3, cond_fallback 1e6, identity output mapping,
- * float32 output, plain accumulation. out_w/out_h are set to 0 and must be filled. */
+ * float32 output, plain accumulation, tabulated weights allowed. out_w/out_h are set to 0 and
+ * must be filled. */
 void hdr_params_default(hdr_params *p);
 
 /* Create a context on CUDA device `device` (allocates its status word). */

@@ -32,13 +32,13 @@ cudaError_t lpa_launch_order1(const LpaLaunch &L, bool comp, bool diag, cudaStre
 cudaError_t lpa_launch_order2(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
 
 // The single-frame kernel of order M for that configuration (for graph kernel nodes).
-const void *lpa_kernel_order0(bool comp, bool diag, int tile_h);
-const void *lpa_kernel_order1(bool comp, bool diag, int tile_h);
-const void *lpa_kernel_order2(bool comp, bool diag, int tile_h);
-inline const void *lpa_kernel(int order, bool comp, bool diag, int tile_h) {
-  return order == 0   ? lpa_kernel_order0(comp, diag, tile_h)
-         : order == 1 ? lpa_kernel_order1(comp, diag, tile_h)
-                      : lpa_kernel_order2(comp, diag, tile_h);
+const void *lpa_kernel_order0(bool comp, bool diag, bool tab, int tile_h);
+const void *lpa_kernel_order1(bool comp, bool diag, bool tab, int tile_h);
+const void *lpa_kernel_order2(bool comp, bool diag, bool tab, int tile_h);
+inline const void *lpa_kernel(int order, bool comp, bool diag, bool tab, int tile_h) {
+  return order == 0   ? lpa_kernel_order0(comp, diag, tab, tile_h)
+         : order == 1 ? lpa_kernel_order1(comp, diag, tab, tile_h)
+                      : lpa_kernel_order2(comp, diag, tab, tile_h);
 }
 
 // Persistent launch of order M over its segment of a many-frame tile list (tile height 8 or 16).

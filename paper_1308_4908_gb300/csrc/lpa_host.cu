@@ -103,8 +103,16 @@ struct BatchState {
   std::map<std::vector<std::array<int64_t, 5>>, FrameGraph> frame_graphs;
 };
 
+// Device copies of tabulated-weight tables, keyed by a hash of their contents. Tables are small
+// (tens of KB) and kept until the context is destroyed (at most kMaxTables; then the context waits
+// for its work and starts over).
+struct TabCache {
+  std::map<uint64_t, void *> dev;
+};
+
 struct hdr_ctx {
   int device = 0;
+  TabCache tabs;
   unsigned int *status = nullptr;
   BatchState batch;
   Rig rigs[kMaxRigs];
@@ -209,6 +217,7 @@ hdr_status check_params(const hdr_params *p) {
   if (!finite6(p->out_affine)) return fail(HDR_E_INVALID, "out_affine not finite");
   if (p->out_dtype != 0 && p->out_dtype != 1) return fail(HDR_E_INVALID, "out_dtype must be 0 or 1");
   if (p->accum != 0 && p->accum != 1) return fail(HDR_E_INVALID, "accum must be 0 or 1");
+  if (p->tab_weights != 0 && p->tab_weights != 1) return fail(HDR_E_INVALID, "tab_weights must be 0 or 1");
   return HDR_OK;
 }
 
@@ -218,7 +227,110 @@ struct PlanEnv {
   EncodeTiledFn encode;
   unsigned int *status;
   int device;
+  TabCache *tabs;  // NULL: never tabulate (the entry point may not allocate)
 };
+
+constexpr size_t kMaxTables = 4096;
+
+bool is_identity_linear(const double *a) {
+  return std::fabs(a[0] - 1.0) <= 1e-12 && std::fabs(a[1]) <= 1e-12 && std::fabs(a[3]) <= 1e-12 &&
+         std::fabs(a[4] - 1.0) <= 1e-12;
+}
+
+int floor_div2_parity(long long v) { return (int)(((v % 2) + 2) % 2); }
+
+// Section 8: with every sensor a pure translation of the reference frame and a 1x output mapping,
+// the window of output pixel (u, v) in colour phase (ox, oy) of sensor s holds the samples
+// (bxe + ox + 2 qx, bye + oy + 2 qy), bxe = even part of u + floor(G2) - ox, at offsets
+// d = (2 qx - rx, 2 qy - ry) with rx = parity(u + floor(G2) - ox) + frac(G2): the same for every
+// pixel of one parity class. The window cells (|d| < k sigma), offsets and weights are listed once.
+hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p, LpaLaunch &L) {
+  L.tab_hdr = nullptr;
+  L.tab_cells = nullptr;
+  if (!env.tabs || p->tab_weights != 1 || !is_identity_linear(p->out_affine)) return HDR_OK;
+  for (int s = 0; s < rig.n; s++)
+    if (!is_identity_linear(rig.s[s].d.affine)) return HDR_OK;
+  const int J = p->n_scales;
+  const double taper = std::exp(-0.5 * p->trunc_k * p->trunc_k);
+  std::vector<int4> hdr((size_t)rig.n * 16 * J);
+  std::vector<float4> cells;
+  auto pack = [](int lo, int hi) { return (lo & 0xffff) | (hi << 16); };
+  for (int s = 0; s < rig.n; s++) {
+    const double gx = L.s[s].G[2], gy = L.s[s].G[5];
+    const double flx = std::floor(gx), fly = std::floor(gy);
+    L.s[s].ix_shift = (int)flx;
+    L.s[s].iy_shift = (int)fly;
+    for (int pu = 0; pu < 2; pu++)
+      for (int pv = 0; pv < 2; pv++)
+        for (int ph = 0; ph < 4; ph++) {
+          const int ox = ph & 1, oy = ph >> 1;
+          const double gscale = (ox != oy) ? p->green_ratio : 1.0;  // phases (1,0), (0,1): G
+          const double rx = floor_div2_parity((long long)pu + (long long)flx - ox) + (gx - flx);
+          const double ry = floor_div2_parity((long long)pv + (long long)fly - oy) + (gy - fly);
+          for (int j = 0; j < J; j++) {
+            const double sg = p->sigma[j] * gscale, R = p->trunc_k * sg, R2 = R * R;
+            int4 &h = hdr[((((size_t)s * 2 + pu) * 2 + pv) * 4 + ph) * J + j];
+            h.x = (int)cells.size();
+            int qxmin = 1 << 14, qxmax = -(1 << 14), qymin = 1 << 14, qymax = -(1 << 14);
+            const int x0 = (int)std::floor((rx - R) / 2) - 1, x1 = (int)std::ceil((rx + R) / 2) + 1;
+            const int y0 = (int)std::floor((ry - R) / 2) - 1, y1 = (int)std::ceil((ry + R) / 2) + 1;
+            for (int qy = y0; qy <= y1; qy++)
+              for (int qx = x0; qx <= x1; qx++) {
+                const double dx = 2.0 * qx - rx, dy = 2.0 * qy - ry, r2 = dx * dx + dy * dy;
+                if (!(r2 < R2)) continue;
+                const double K = std::exp(-r2 / (2.0 * sg * sg)) - taper;  // Eq. 8, truncated and tapered
+                float4 c;
+                c.x = (float)dx;
+                c.y = (float)dy;
+                c.z = (float)K;
+                const int q = (qy << 16) | (qx & 0xffff);
+                memcpy(&c.w, &q, 4);
+                cells.push_back(c);
+                qxmin = std::min(qxmin, qx);
+                qxmax = std::max(qxmax, qx);
+                qymin = std::min(qymin, qy);
+                qymax = std::max(qymax, qy);
+              }
+            h.y = (int)cells.size() - h.x;
+            if (h.y == 0) qxmin = qxmax = qymin = qymax = 0;
+            h.z = pack(qxmin, qxmax);
+            h.w = pack(qymin, qymax);
+          }
+        }
+  }
+  // content hash (FNV-1a) -> device copy
+  const size_t nb = hdr.size() * sizeof(int4) + cells.size() * sizeof(float4);
+  uint64_t hsh = 1469598103934665603ull;
+  auto mix = [&](const void *ptr, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(ptr);
+    for (size_t i = 0; i < n; i++) hsh = (hsh ^ b[i]) * 1099511628211ull;
+  };
+  mix(hdr.data(), hdr.size() * sizeof(int4));
+  mix(cells.data(), cells.size() * sizeof(float4));
+  hsh ^= (uint64_t)hdr.size() << 40;
+  auto it = env.tabs->dev.find(hsh);
+  if (it == env.tabs->dev.end()) {
+    if (env.tabs->dev.size() >= kMaxTables) {
+      CUDA_TRY(cudaDeviceSynchronize());
+      for (auto &t : env.tabs->dev) cudaFree(t.second);
+      env.tabs->dev.clear();
+    }
+    void *d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, std::max<size_t>(nb, 16)));
+    cudaError_t e = cudaMemcpy(d, hdr.data(), hdr.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !cells.empty())
+      e = cudaMemcpy(static_cast<int4 *>(d) + hdr.size(), cells.data(), cells.size() * sizeof(float4),
+                     cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return fail(HDR_E_CUDA, "uploading the weight table failed: %s", cudaGetErrorString(e));
+    }
+    it = env.tabs->dev.emplace(hsh, d).first;
+  }
+  L.tab_hdr = static_cast<const int4 *>(it->second);
+  L.tab_cells = reinterpret_cast<const float4 *>(static_cast<const int4 *>(it->second) + hdr.size());
+  return HDR_OK;
+}
 
 // Fill the launch descriptor for one frame. raw: device pointers per sensor.
 hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, const uint16_t *const *raw,
@@ -312,11 +424,11 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
   CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, env.device));
   if ((int)off > max_smem - 1024)
     return fail(HDR_E_UNSUPPORTED, "staging needs %u bytes of shared memory (limit %d)", off, max_smem - 1024);
-  return HDR_OK;
+  return build_tables(env, rig, p, L);
 }
 
 hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L) {
-  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device}, rig, p, raw, L);
+  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs}, rig, p, raw, L);
 }
 
 hdr_status launch(const LpaLaunch &L, int accum, bool diag, cudaStream_t st) {
@@ -378,6 +490,7 @@ void hdr_params_default(hdr_params *p) {
   p->out_affine[4] = 1.0;
   p->out_dtype = 0;
   p->accum = 0;
+  p->tab_weights = 1;
 }
 
 hdr_status hdr_create(int device, hdr_ctx **out) {
@@ -417,6 +530,7 @@ void hdr_destroy(hdr_ctx *ctx) {
   for (int s = 0; s < HDR_MAX_SENSORS; s++) cudaFree(ctx->raw_stage[s]);
   cudaFree(ctx->out_stage);
   cudaFree(ctx->choice_stage);
+  for (auto &t : ctx->tabs.dev) cudaFree(t.second);
   if (ctx->h2d) cudaStreamDestroy(ctx->h2d);
   if (ctx->d2h) cudaStreamDestroy(ctx->d2h);
   for (int b = 0; b < 8; b++) {
@@ -738,7 +852,7 @@ hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *
   for (int o = 0; o < 3; o++) smem[o] = 0, n_tiles[o] = 0;
   for (int f = 0; f < n; f++) {
     const hdr_frame &F = frames[f];
-    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
+    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
                              plans[f], cfg.tile_h);
     if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
     plans[f].out = F.out_dev;
@@ -794,7 +908,7 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
   std::vector<int> grid(n, 0);
   for (int f = 0; f < n; f++) {
     const hdr_frame &F = frames[f];
-    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
+    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
                              plans[f], cfg.tile_h);
     if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
     plans[f].out = F.out_dev;
@@ -821,9 +935,9 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
   std::vector<void *> args(order.size());
   for (size_t k = 0; k < order.size(); k++) {
     const LpaLaunch &L = plans[order[k]];
-    const void *fn = lpa_kernel(L.order, comp, false, cfg.tile_h);
+    const void *fn = lpa_kernel(L.order, comp, false, L.tab_cells != nullptr, cfg.tile_h);
     CUDA_TRY(lpa_opt_in(fn));
-    key.push_back({L.order, comp ? 1 : 0, cfg.tile_h, grid[order[k]], (int64_t)L.smem_bytes});
+    key.push_back({L.order * 2 + (L.tab_cells ? 1 : 0), comp ? 1 : 0, cfg.tile_h, grid[order[k]], (int64_t)L.smem_bytes});
     args[k] = &plans[order[k]];
     kp[k] = cudaKernelNodeParams{};
     kp[k].func = const_cast<void *>(fn);
@@ -1136,7 +1250,7 @@ extern "C" hdr_status hdr_reconstruct_noalloc(int device, int32_t n_sensors, con
     CUDA_TRY(place(rs.d.sat_frame, npx * 2, (void **)&rs.satf));
   }
   LpaLaunch L;
-  st = plan_env(PlanEnv{encode, status, device}, rig, params, raw_dev, L);
+  st = plan_env(PlanEnv{encode, status, device, nullptr}, rig, params, raw_dev, L);
   for (int s = 0; s < n_sensors; s++) rig.s[s] = RigSensor();  // the frames belong to the scratch array
   rig.n = 0;
   if (st) return st;

@@ -538,6 +538,50 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
   }
 }
 
+// The window of one pixel read from the tabulated cells (Section 8; see LpaLaunch::tab_hdr): the
+// pixel's even lattice cell in each colour phase follows from integer arithmetic, and every cell
+// carries its offset and weight, so nothing is searched or evaluated per pixel.
+template <int ORDER, class MOM>
+__device__ __forceinline__ void accumulate_table(MOM &m, const LpaLaunch &L, int s, int c, int j, int u, int v, int x0,
+                                                 int y0, const unsigned char *smem, bool active, unsigned *status) {
+  const LpaSensorK &S = L.s[s];
+  const int PW = S.box_w >> 1, PH = S.box_h >> 1;
+  const float2 *planes = reinterpret_cast<const float2 *>(smem + S.off_planes);
+  const int ix = u + S.ix_shift, iy = v + S.iy_shift;
+  const int base = ((s * 2 + (u & 1)) * 2 + (v & 1)) * 4;
+  const int nsub = (c == 1) ? 2 : 1;
+#pragma unroll 1
+  for (int sub = 0; sub < nsub; sub++) {
+    const int ox = (c == 0) ? 0 : (c == 2 ? 1 : 1 - sub);
+    const int oy = (c == 0) ? 0 : (c == 2 ? 1 : sub);
+    const int ph = ox + 2 * oy;
+    const int cb = (((ix - ox) & ~1) - x0) >> 1, rb = (((iy - oy) & ~1) - y0) >> 1;
+    const int4 h = __ldg(&L.tab_hdr[(base + ph) * L.n_scales + j]);
+    const int qx0 = (int)(short)(h.z & 0xffff), qx1 = h.z >> 16, qy0 = (int)(short)(h.w & 0xffff), qy1 = h.w >> 16;
+    if (!(cb + qx0 >= 0 && cb + qx1 < PW && rb + qy0 >= 0 && rb + qy1 < PH)) {
+      if (active && h.y > 0) atomicOr(status, LPA_ERR_BOUNDS);
+      continue;
+    }
+    const float2 *pl = planes + ph * (PW * PH) + rb * PW + cb;
+    const float4 *cell = L.tab_cells + h.x;
+#pragma unroll 2
+    for (int k = 0; k < h.y; k++) {
+      const float4 t = __ldg(cell + k);
+      const int q = __float_as_int(t.w);
+      const float2 fv = pl[(q >> 16) * PW + (int)(short)(q & 0xffff)];
+      if (active && fv.y > 0.f) {
+        const float w = t.z * fv.y;  // tabulated window weight x inverse variance
+        if constexpr (ORDER == 0) {
+          m.add0(w, w * fv.x, w * t.z, 1.f);
+        } else {
+          const float2 D = make_float2(t.x, t.y);
+          m.add2(D, __fmul2_rn(D, D), w, w * fv.x, w * t.z);
+        }
+      }
+    }
+  }
+}
+
 #ifndef LPA_BATCH_REREAD
 #define LPA_BATCH_REREAD 1
 #endif
@@ -553,7 +597,7 @@ __device__ __forceinline__ T reread(const T &x) {
 // global descriptor, whose tensor maps the bulk copies use (otherwise `maps` is &L).
 // `phase` is the parity of the CTA's mbarrier use for this tile. Returns false when the CTA must
 // stop (a bounded wait ran out here or in another CTA).
-template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS>
+template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS, bool TAB = false>
 __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch *maps, int tile, unsigned char *smem, uint64_t *mbar,
                                              uint32_t phase, int *fp_x0, int *fp_y0,
                                              Anchor (*anchors)[LPA_MAX_SENSORS]) {
@@ -695,9 +739,13 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
       const float cexp = -log2e / (2.f * sg * sg);
       const bool act = DIAG ? pix : !ici.done;
 #pragma unroll 1
-      for (int s = 0; s < S; s++)
-        accumulate_sensor<ORDER, COMP>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, RD(L.taper), fp_x0[s],
-                                       fp_y0[s], smem, act, RD(L.status));
+      for (int s = 0; s < S; s++) {
+        if constexpr (TAB)
+          accumulate_table<ORDER>(m, L, s, c, j, u, v, fp_x0[s], fp_y0[s], smem, act, L.status);
+        else
+          accumulate_sensor<ORDER, COMP>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, RD(L.taper), fp_x0[s],
+                                         fp_y0[s], smem, act, RD(L.status));
+      }
       FitOut f = solve_with_fallback<P>(m, RD(L.min_pivot), RD(L.cond_fallback));
       if (DIAG && pix) {
         float *o = L.levels + (((size_t)c * NL + j) * plane_px + opix) * 2;
@@ -736,14 +784,14 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
 }
 
 // Single frame: one CTA per tile (tiles tile0 .. tile0 + gridDim.x - 1).
-template <int ORDER, bool COMP, bool DIAG, int TH>
+template <int ORDER, bool COMP, bool DIAG, int TH, bool TAB = false>
 __global__ void __launch_bounds__(LPA_TILE *TH, 16 / TH * 2) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
   __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
   __shared__ __align__(8) uint64_t mbar;
   if (threadIdx.x == 0) mbar_init(&mbar, 1);
-  process_tile<ORDER, COMP, DIAG, TH, false>(L, &L, L.tile0 + blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0, anchors);
+  process_tile<ORDER, COMP, DIAG, TH, false, TAB>(L, &L, L.tile0 + blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0, anchors);
 }
 
 // Resident CTAs per SM the persistent kernel is compiled for (register cap 64K / (threads x this)):

@@ -28,6 +28,7 @@ struct alignas(64) LpaSensorK {
   float ext_x, ext_y;       // half extent of the window box in sensor px incl. margin (max scale)
   uint32_t off_raw;         // byte offset of the raw box in dynamic shared memory
   uint32_t off_planes;      // byte offset of the four colour-phase planes (float2 each)
+  int ix_shift, iy_shift;   // tabulated weights: floor of the translation of G (sensor px)
   const float *bias;        // optional per-pixel frames [height][width] (device)
   const float *prnu;
   const float *rvar;
@@ -58,6 +59,14 @@ struct LpaLaunch {
   int tile_h;                    // tile height the plan was made for
   int tile0;                     // single-frame grid: CTA b reconstructs tile tile0 + b
   int tile_count;                // single-frame grid size; 0 = every tile from tile0 on
+  // Tabulated window weights (NULL = the window is searched and evaluated per pixel). Entry
+  // ((((s * 2 + pu) * 2 + pv) * 4 + phase) * n_scales + j) of tab_hdr gives the first cell, the
+  // number of cells and the cell-offset bounds of sensor s, output parity (pu, pv), colour phase
+  // (ox + 2 oy) and scale j; a cell is {dx, dy, K, (qy << 16) | (qx & 0xffff)}: the offset of the
+  // sample from the pixel's point in reference px, its window weight and its lattice offset from
+  // the pixel's even lattice cell.
+  const int4 *tab_hdr;           // {first, count, (qx_min & 0xffff) | (qx_max << 16), same for qy}
+  const float4 *tab_cells;
 };
 
 // Several frames in one graph launch: the tile list is grouped by polynomial order and each

@@ -3,9 +3,9 @@
 #include "lpa_dispatch.h"
 #include "lpa_kernel.cuh"
 
-template <bool COMP, bool DIAG, int TH>
+template <bool COMP, bool DIAG, int TH, bool TAB>
 static cudaError_t launch_one(const LpaLaunch &L, cudaStream_t st) {
-  auto k = lpa::lpa_reconstruct<1, COMP, DIAG, TH>;
+  auto k = lpa::lpa_reconstruct<1, COMP, DIAG, TH, TAB>;
   cudaError_t e = lpa_opt_in((const void *)k);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_count > 0 ? L.tile_count : L.tiles_x * L.tiles_y - L.tile0;
@@ -15,8 +15,13 @@ static cudaError_t launch_one(const LpaLaunch &L, cudaStream_t st) {
 
 template <int TH>
 static cudaError_t launch_th(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st) {
-  if (comp) return diag ? launch_one<true, true, TH>(L, st) : launch_one<true, false, TH>(L, st);
-  return diag ? launch_one<false, true, TH>(L, st) : launch_one<false, false, TH>(L, st);
+  const bool tab = L.tab_cells != nullptr;  // the diagnostic (levels) path always searches
+  if (comp) {
+    if (diag) return launch_one<true, true, TH, false>(L, st);
+    return tab ? launch_one<true, false, TH, true>(L, st) : launch_one<true, false, TH, false>(L, st);
+  }
+  if (diag) return launch_one<false, true, TH, false>(L, st);
+  return tab ? launch_one<false, false, TH, true>(L, st) : launch_one<false, false, TH, false>(L, st);
 }
 
 cudaError_t lpa_launch_order1(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st) {
@@ -51,11 +56,18 @@ int lpa_batch_ctas_per_sm_order1(bool comp, int tile_h, uint32_t smem_bytes) {
   return comp ? fit_t<true, 16>(smem_bytes) : fit_t<false, 16>(smem_bytes);
 }
 
-const void *lpa_kernel_order1(bool comp, bool diag, int tile_h) {
-  if (tile_h == 8) {
-    if (comp) return diag ? (const void *)lpa::lpa_reconstruct<1, true, true, 8> : (const void *)lpa::lpa_reconstruct<1, true, false, 8>;
-    return diag ? (const void *)lpa::lpa_reconstruct<1, false, true, 8> : (const void *)lpa::lpa_reconstruct<1, false, false, 8>;
+template <int TH>
+static const void *kernel_th(bool comp, bool diag, bool tab) {
+  if (comp) {
+    if (diag) return (const void *)lpa::lpa_reconstruct<1, true, true, TH, false>;
+    return tab ? (const void *)lpa::lpa_reconstruct<1, true, false, TH, true>
+               : (const void *)lpa::lpa_reconstruct<1, true, false, TH, false>;
   }
-  if (comp) return diag ? (const void *)lpa::lpa_reconstruct<1, true, true, 16> : (const void *)lpa::lpa_reconstruct<1, true, false, 16>;
-  return diag ? (const void *)lpa::lpa_reconstruct<1, false, true, 16> : (const void *)lpa::lpa_reconstruct<1, false, false, 16>;
+  if (diag) return (const void *)lpa::lpa_reconstruct<1, false, true, TH, false>;
+  return tab ? (const void *)lpa::lpa_reconstruct<1, false, false, TH, true>
+             : (const void *)lpa::lpa_reconstruct<1, false, false, TH, false>;
+}
+
+const void *lpa_kernel_order1(bool comp, bool diag, bool tab, int tile_h) {
+  return tile_h == 8 ? kernel_th<8>(comp, diag, tab) : kernel_th<16>(comp, diag, tab);
 }

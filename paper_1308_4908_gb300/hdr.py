@@ -38,7 +38,8 @@ class hdr_params(ctypes.Structure):
                 ("sigma", ctypes.c_double * HDR_MAX_SCALES), ("green_ratio", ctypes.c_double),
                 ("trunc_k", ctypes.c_double), ("ici_gamma", ctypes.c_double), ("min_pivot", ctypes.c_double),
                 ("cond_fallback", ctypes.c_double), ("out_w", ctypes.c_int32), ("out_h", ctypes.c_int32),
-                ("out_affine", ctypes.c_double * 6), ("out_dtype", ctypes.c_int32), ("accum", ctypes.c_int32)]
+                ("out_affine", ctypes.c_double * 6), ("out_dtype", ctypes.c_int32), ("accum", ctypes.c_int32),
+                ("tab_weights", ctypes.c_int32)]
 
 
 class hdr_frame(ctypes.Structure):
@@ -293,6 +294,7 @@ def params_struct(p) -> hdr_params:
     h.out_affine[:] = [float(x) for x in np.asarray(p.out_affine, dtype=np.float64).reshape(6)]
     h.out_dtype = int(getattr(p, "out_dtype", 0))
     h.accum = int(getattr(p, "accum", 0))
+    h.tab_weights = int(getattr(p, "tab_weights", 1))
     return h
 
 

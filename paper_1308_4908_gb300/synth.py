@@ -203,6 +203,7 @@ class Params:
     cond_fallback: float = 1e6
     out_dtype: int = 0        # 0 float32, 1 float16
     accum: int = 0            # 0 plain, 1 compensated
+    tab_weights: int = 1      # 1 tabulated window weights where the rig allows, 0 never
 
     def __post_init__(self):
         if self.out_affine is None:

@@ -142,3 +142,33 @@ def test_batch_with_empty_and_one_pixel_frames(ctx, form):
     items = _prepare(ctx, frames, base_rig=56)
     refs = _single(ctx, items)
     _same(_batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form)), refs)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_batch_with_translational_frames(ctx, form):
+    """Frames whose rigs are pure translations use tabulated weights in form 0 (and the searched
+    window in the persistent form): each equals its single-frame result within the parity
+    tolerance and is bit-identical to it in form 0."""
+    import dataclasses
+    from paper_1308_4908_gb300 import hdr
+    frames = synth.batching(n_frames=3, size_cap=96, seed=2007)
+    for k, fr in enumerate(frames):
+        w, h = fr.sensors[0].width, fr.sensors[0].height
+        for i, s in enumerate(fr.sensors):
+            s.affine = np.asarray(synth.affine_about_center(w, h, 0.3 * i - 0.2, 0.1 * k))
+            s.raw = synth.simulate_raw(fr.scene, s, 2007, 100 * k + i)
+        frames[k] = dataclasses.replace(fr, params=dataclasses.replace(fr.params, out_w=w, out_h=h,
+                                                                        out_affine=synth.output_affine(w, h, w, h)))
+    items = _prepare(ctx, frames, base_rig=60 - 3)
+    refs = _single(ctx, items)
+    got = _batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form))
+    if form == 0:
+        _same(got, refs)
+    else:
+        for (rig, fr, _, _, _), (out, ch) in zip(items, got):
+            p = fr.params
+            r = np.random.default_rng(rig)
+            pix = np.stack([r.integers(0, p.out_w, 200), r.integers(0, p.out_h, 200)], axis=1)
+            o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True)
+            parity.compare(out[:, pix[:, 1], pix[:, 0]], ch[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
+                           p.ici_gamma, p.min_pivot)

@@ -152,6 +152,49 @@ def test_rigs(ctx, case):
     check_frame(ctx, fr, p)
 
 
+def translational(size, seed, shifts):
+    """The paper rig with pure translations (Section 8's aligned/translational case) at 1x output."""
+    fr = synth.paper_scale(size=size, seed=seed)
+    for s, (tx, ty) in zip(fr.sensors, shifts):
+        s.affine = np.asarray(synth.affine_about_center(size, size, tx, ty))
+        s.raw = synth.simulate_raw(fr.scene, s, seed, int(s.nd * 1000))
+    return fr
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_tabulated_weights_match_the_oracle(ctx, order):
+    """Translation-only rigs at 1x output read their windows from the per-frame table (Section 8):
+    every pixel within tolerance of the oracle; the searched path gives the same fit up to
+    rounding (the two paths are different code: their outputs are not bit-identical)."""
+    fr = translational(96, 1040 + order, [(0.0, 0.0), (0.4, 0.45), (-1.3, 0.7)])
+    p = dataclasses.replace(fr.params, order=order)
+    _, g, _ = check_frame(ctx, fr, p)
+    q = dataclasses.replace(p, tab_weights=0)
+    _, h, _ = check_frame(ctx, fr, q)
+    assert not np.array_equal(g["out"], h["out"])
+
+
+def test_tabulated_weights_other_shifts_and_scales(ctx):
+    """Integer, negative and half-pixel shifts, one scale and eight scales, FP16 output."""
+    fr = translational(80, 1050, [(-2.0, 3.0), (0.5, -0.5), (1.999, -0.001)])
+    check_frame(ctx, fr, dataclasses.replace(fr.params, sigmas=(0.7,)))
+    check_frame(ctx, fr, dataclasses.replace(fr.params, order=1, sigmas=tuple(0.5 + 0.2 * i for i in range(8))))
+    check_frame(ctx, fr, dataclasses.replace(fr.params, out_dtype=1), extra=parity.HALF_TOL)
+
+
+def test_tabulated_weights_only_for_translations(ctx):
+    """A rotated rig or a resampled output keeps the searched window: the switch changes nothing."""
+    fr = synth.paper_scale(size=64, seed=1060)
+    a = run(ctx, fr, fr.params)
+    b = run(ctx, fr, dataclasses.replace(fr.params, tab_weights=0))
+    np.testing.assert_array_equal(a["out"], b["out"])
+    fr = translational(64, 1061, [(0.3, 0.2), (0.1, -0.4), (0.0, 0.0)])
+    p = dataclasses.replace(fr.params, out_w=96, out_h=96, out_affine=synth.output_affine(64, 64, 96, 96))
+    a = run(ctx, fr, p)
+    b = run(ctx, fr, dataclasses.replace(p, tab_weights=0))
+    np.testing.assert_array_equal(a["out"], b["out"])
+
+
 def test_ragged_and_tiny_outputs(ctx):
     """Output sizes that are not multiples of the tile, a 1x1 output, and an output that
     extends past the sensors (NaN where no sample exists)."""
