@@ -321,3 +321,22 @@ def serving_stream_frame(stream: int, k: int, seed: int = 1005, size_cap: Option
     p = Params(order=2, sigmas=PAPER_SCALES, out_w=ow, out_h=oh, out_affine=output_affine(w, h, ow, oh))
     return _build_frame(100 * seed + stream, ns, w, h, (1.0, 1 / 16, 1 / 256)[:ns], 1.5, 0.2, 1e-3, p,
                         f"serve{stream}.{k}", frame_index=k, rig_index=0)
+
+
+# --------------------------------------------------------------------------- calibration stacks
+
+def flat_stack(seed: int, n_frames: int, width: int, height: int, electrons: float, gain: float = 2.0,
+               read_var: float = 9.0, bias: float = 64.0, nd: float = 1.0,
+               prnu: Optional[np.ndarray] = None) -> np.ndarray:
+    """n_frames raw frames [n, height, pitch] of a uniform flat field (Eqs. 16-17): per pixel
+    Poisson(electrons * nd * a) photo-electrons times `gain`, plus N(0, read_var) read noise and
+    the `bias` pedestal, rounded and clipped to 12 bits. electrons = 0 gives black frames."""
+    r = _rng(seed, 7)
+    pitch = pitch_for(width)
+    out = np.zeros((n_frames, height, pitch), dtype=np.uint16)
+    a = prnu if prnu is not None else 1.0
+    for k in range(n_frames):
+        e = r.poisson(electrons * nd * a * np.ones((height, width))).astype(np.float64)
+        y = gain * e + r.standard_normal((height, width)) * np.sqrt(read_var) + bias
+        out[k, :, :width] = np.clip(np.rint(y), 0, CLIP_DN).astype(np.uint16)
+    return out
