@@ -573,6 +573,52 @@ def run_tab_study(args):
                       "rows": rows}), flush=True)
 
 
+def run_calib_study(args):
+    """Calibration statistics (Section 6.2) over a stack of 64 synthetic 2048^2 raw frames resident
+    on the device: the statistics kernel reads every frame once (HBM-bound), so it is reported in
+    GB/s against the measured copy bandwidth; the FP64 oracle is timed on the host cores on the
+    same stack. One JSON line."""
+    import torch
+    from oracle import calib
+    from paper_1308_4908_gb300 import hdr
+    n, w, h = 64, args.size, args.size
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1006)
+    # flat field: 12-bit values around 2000 DN (the stack is input data, not the method)
+    frames = torch.randint(1800, 2200, (n, h, w), generator=g, device="cuda", dtype=torch.int32).to(torch.uint16)
+    ctx = hdr.Context(0)
+    mean, var = ctx.calib_stack_stats(frames, w)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for k in range(20):
+        flush.fill_(k)
+        ev[k][0].record(st)
+        hdr.hdr_calib_stack_stats(ctx.handle, frames.data_ptr(), n, w, h, w, h * w, mean.data_ptr(), var.data_ptr(),
+                                  st.cuda_stream)
+        ev[k][1].record(st)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    nbytes = n * h * w * 2 + h * w * 8
+    host = frames.cpu().numpy()
+    t0 = time.perf_counter()
+    om, ov = calib.stack_stats(host, w)
+    dt = time.perf_counter() - t0
+    exact = bool(np.array_equal(om, mean.cpu().numpy()) and np.array_equal(ov, var.cpu().numpy()))
+    pk = peaks()
+    gbs = nbytes / ms / 1e6
+    ctx.close()
+    print(json.dumps({"study": "calibration statistics", "workload": f"{n} frames of {w}x{h} uint16 -> mean and "
+                      "unbiased variance frames (float32)", "ms": round(ms, 4), "bytes": nbytes,
+                      "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk.get("hbm_gbs"),
+                                   "unit": "GB/s", "frac": round(gbs / pk["hbm_gbs"], 3) if pk.get("hbm_gbs") else None},
+                      "l2": "flushed between timed repetitions", "bit_exact_vs_oracle": exact,
+                      "cpu_baseline": {"seconds": round(dt, 3), "gb_s": round(nbytes / dt / 1e9, 3),
+                                       "kind": "oracle (numpy, one thread)"}}), flush=True)
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
@@ -703,7 +749,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--size", type=int, default=2048, help="raw and output edge (2048 = the paper-scale workload)")
     ap.add_argument("--headline-only", action="store_true", help="skip the batching and serving measurements")
-    ap.add_argument("--study", choices=["precision", "tiny", "tabweights"], default=None,
+    ap.add_argument("--study", choices=["precision", "tiny", "tabweights", "calib"], default=None,
                     help="print a study instead of the bench line")
     ap.add_argument("--study-pixels", type=int, default=20000)
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson arrival schedule")
@@ -717,6 +763,9 @@ def main():
         return
     if args.study == "tabweights":
         run_tab_study(args)
+        return
+    if args.study == "calib":
+        run_calib_study(args)
         return
     world, rank, local, pg = dist_setup(args)
     try:

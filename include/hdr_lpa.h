@@ -263,6 +263,40 @@ hdr_status hdr_selftest_timeout(hdr_ctx *ctx, void *cuda_stream);
 /* Message of the calling thread's last failed call ("" if none). */
 const char *hdr_last_error(void);
 
+/* ---------------------------------------------------------------- calibration (Section 6.2)
+ * Estimates of the camera parameters the reconstruction needs, from stacks of raw frames of one
+ * sensor: black frames (lens covered) and flat fields. All pointers are DEVICE pointers; frames
+ * are uint16 [height][pitch_elems], output and statistics frames float32 [height][width]. */
+
+/* Per-pixel mean and unbiased variance over n_frames (2..4096) frames, frame f at
+ * frames_dev + f * frame_stride_elems. From black frames these are the bias frame b_{s,i} and
+ * the read-noise variance Var r_{s,i}; from flat fields, E[y_{s,i}] and Var y_{s,i}. The sums
+ * are exact integers, so each value is one FP64 rounding of the exact statistic, then FP32.
+ * frames_dev must be 16-byte aligned; pitch_elems and frame_stride_elems multiples of 8, the
+ * pitch at least the width rounded up to 8. Asynchronous on `cuda_stream`. */
+hdr_status hdr_calib_stack_stats(hdr_ctx *ctx, const uint16_t *frames_dev, int32_t n_frames, int32_t width,
+                                 int32_t height, int32_t pitch_elems, int64_t frame_stride_elems, float *mean_dev,
+                                 float *var_dev, void *cuda_stream);
+
+/* Sensor gain by Eq. 21, (Var y - Var b) / (E[y] - E[b]) = g_s, pooled as the ratio of the sums
+ * over usable pixels: flat mean at least min_signal DN above the black mean and below max_level
+ * DN (away from saturation). *gain = NaN if no pixel is usable; *n_used (optional) = the count.
+ * Synchronous; the summation order is fixed, so repeated calls give identical results. */
+hdr_status hdr_calib_gain(hdr_ctx *ctx, const float *flat_mean, const float *flat_var, const float *black_mean,
+                          const float *black_var, int32_t width, int32_t height, double min_signal, double max_level,
+                          double *gain, int64_t *n_used, void *cuda_stream);
+
+/* Exposure scaling n_s (Section 6.2): the spatial mean over pixels usable in both sensors of
+ * rho_i = ((E y - b) / (g t))_s / ((E y - b) / (g t))_ref, the pixel-wise ratio of the radiant-power
+ * estimates of Eq. 18 (with n = a = 1) of sensor s to those of a reference sensor seeing the same
+ * flat field. When prnu_dev is non-NULL it receives the non-uniformity a_{s,i} = rho_i / n_s at
+ * usable pixels and 1 elsewhere (the reference sensor's own non-uniformity is taken as 1). Use
+ * exposure times that expose both sensors well. Synchronous; *nd = NaN if no pixel is usable. */
+hdr_status hdr_calib_exposure(hdr_ctx *ctx, const float *flat_mean, const float *black_mean, double gain,
+                              double exposure, const float *ref_flat_mean, const float *ref_black_mean,
+                              double ref_gain, double ref_exposure, int32_t width, int32_t height, double min_signal,
+                              double max_level, double *nd, float *prnu_dev, int64_t *n_used, void *cuda_stream);
+
 /* Size of the fixed device array that hdr_reconstruct_noalloc uses as scratch. */
 #define HDR_NOALLOC_SCRATCH_BYTES (4u << 20)
 

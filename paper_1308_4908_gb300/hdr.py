@@ -111,6 +111,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.hdr_reconstruct_host.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
     lib.hdr_check.argtypes = [_P, _P]
     lib.hdr_selftest_timeout.argtypes = [_P, _P]
+    lib.hdr_calib_stack_stats.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int64, _P, _P, _P]
+    lib.hdr_calib_gain.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.c_double, _P, _P, _P]
+    lib.hdr_calib_exposure.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P, _P, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_double, _P, _P, _P, _P]
     lib.hdr_reconstruct_noalloc.argtypes = [ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
     lib.hdr_reconstruct_batch.argtypes = [_P, ctypes.c_int32, _P, _P, _P]
     lib.hdr_tune_batch.argtypes = [_P, ctypes.c_int32, _P, _P, _P]
@@ -124,7 +131,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.hdr_last_error.restype = ctypes.c_char_p
     for name in ("hdr_create", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_levels", "hdr_reconstruct_host",
                  "hdr_check", "hdr_reconstruct_noalloc", "hdr_reconstruct_batch", "hdr_tune_batch",
-                 "hdr_server_create", "hdr_submit", "hdr_poll", "hdr_server_stats_get", "hdr_selftest_timeout"):
+                 "hdr_server_create", "hdr_submit", "hdr_poll", "hdr_server_stats_get", "hdr_selftest_timeout",
+                 "hdr_calib_stack_stats", "hdr_calib_gain", "hdr_calib_exposure"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -189,6 +197,38 @@ def hdr_check(ctx: int, stream: Optional[int] = None) -> None:
 def hdr_selftest_timeout(ctx: int, stream: Optional[int] = None) -> None:
     """Launch the bounded-wait self-test: the next hdr_check on that stream reports HDR_E_TIMEOUT."""
     _check(load().hdr_selftest_timeout(ctypes.c_void_p(ctx), ctypes.c_void_p(stream)))
+
+
+def hdr_calib_stack_stats(ctx: int, frames_dev: int, n_frames: int, width: int, height: int, pitch_elems: int,
+                          frame_stride_elems: int, mean_dev: int, var_dev: int, stream: Optional[int] = None) -> None:
+    _check(load().hdr_calib_stack_stats(ctypes.c_void_p(ctx), ctypes.c_void_p(frames_dev), int(n_frames), int(width),
+                                        int(height), int(pitch_elems), int(frame_stride_elems),
+                                        ctypes.c_void_p(mean_dev), ctypes.c_void_p(var_dev), ctypes.c_void_p(stream)))
+
+
+def hdr_calib_gain(ctx: int, flat_mean: int, flat_var: int, black_mean: int, black_var: int, width: int, height: int,
+                   min_signal: float, max_level: float, stream: Optional[int] = None):
+    g = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().hdr_calib_gain(ctypes.c_void_p(ctx), ctypes.c_void_p(flat_mean), ctypes.c_void_p(flat_var),
+                                 ctypes.c_void_p(black_mean), ctypes.c_void_p(black_var), int(width), int(height),
+                                 float(min_signal), float(max_level), ctypes.byref(g), ctypes.byref(n),
+                                 ctypes.c_void_p(stream)))
+    return g.value, n.value
+
+
+def hdr_calib_exposure(ctx: int, flat_mean: int, black_mean: int, gain: float, exposure: float, ref_flat_mean: int,
+                       ref_black_mean: int, ref_gain: float, ref_exposure: float, width: int, height: int,
+                       min_signal: float, max_level: float, prnu_dev: Optional[int] = None,
+                       stream: Optional[int] = None):
+    nd = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().hdr_calib_exposure(ctypes.c_void_p(ctx), ctypes.c_void_p(flat_mean), ctypes.c_void_p(black_mean),
+                                     float(gain), float(exposure), ctypes.c_void_p(ref_flat_mean),
+                                     ctypes.c_void_p(ref_black_mean), float(ref_gain), float(ref_exposure), int(width),
+                                     int(height), float(min_signal), float(max_level), ctypes.byref(nd),
+                                     ctypes.c_void_p(prnu_dev), ctypes.byref(n), ctypes.c_void_p(stream)))
+    return nd.value, n.value
 
 
 def hdr_last_error() -> str:
@@ -380,6 +420,33 @@ class Context:
 
     def selftest_timeout(self, stream=None):
         hdr_selftest_timeout(self.handle, self._stream(stream))
+
+    # ---------------------------------------------------------------- calibration (Section 6.2)
+    def calib_stack_stats(self, frames, width: int, stream=None):
+        """frames: uint16 device tensor [n, height, pitch]; returns (mean, var) float32 [height, width]."""
+        import torch
+        n, h, pitch = frames.shape
+        mean = torch.empty((h, width), dtype=torch.float32, device=frames.device)
+        var = torch.empty((h, width), dtype=torch.float32, device=frames.device)
+        hdr_calib_stack_stats(self.handle, frames.data_ptr(), n, width, h, pitch, frames.stride(0), mean.data_ptr(),
+                              var.data_ptr(), self._stream(stream))
+        return mean, var
+
+    def calib_gain(self, flat_mean, flat_var, black_mean, black_var, min_signal=20.0, max_level=3800.0, stream=None):
+        h, w = flat_mean.shape
+        return hdr_calib_gain(self.handle, flat_mean.data_ptr(), flat_var.data_ptr(), black_mean.data_ptr(),
+                              black_var.data_ptr(), w, h, min_signal, max_level, self._stream(stream))
+
+    def calib_exposure(self, flat_mean, black_mean, gain, exposure, ref_flat_mean, ref_black_mean, ref_gain,
+                       ref_exposure, min_signal=20.0, max_level=3800.0, stream=None):
+        """Returns (n_s, prnu tensor [height, width], pixels used)."""
+        import torch
+        h, w = flat_mean.shape
+        a = torch.empty((h, w), dtype=torch.float32, device=flat_mean.device)
+        nd, n = hdr_calib_exposure(self.handle, flat_mean.data_ptr(), black_mean.data_ptr(), gain, exposure,
+                                   ref_flat_mean.data_ptr(), ref_black_mean.data_ptr(), ref_gain, ref_exposure, w, h,
+                                   min_signal, max_level, a.data_ptr(), self._stream(stream))
+        return nd, a, n
 
 
 class Server:
