@@ -70,11 +70,13 @@ def _load():
     if _lib is None:
         lib = ctypes.CDLL(build())
         P = ctypes.c_void_p
-        lib.orc_reconstruct.argtypes = [P, ctypes.c_int, P, ctypes.c_int64] + [P] * 13
+        lib.orc_reconstruct.argtypes = [P, ctypes.c_int, P, ctypes.c_int64] + [P] * 14
         lib.orc_reconstruct.restype = ctypes.c_int
         lib.orc_radiometry.argtypes = [ctypes.c_double] * 8 + [P, P]
         lib.orc_radiometry.restype = ctypes.c_int
         lib.orc_ici.argtypes = [ctypes.c_int, P, P, P, ctypes.c_double, P]
+        lib.orc_gradients.argtypes = [P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int64, P, P, P, P]
+        lib.orc_gradients.restype = ctypes.c_int
         lib.orc_ici.restype = ctypes.c_int
         lib.orc_equivalent_kernel.argtypes = [P, ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_int32, ctypes.c_int32] + [P] * 7
@@ -144,12 +146,14 @@ def n_levels(params) -> int:
 
 
 def reconstruct(sensors: Sequence, params, pixels: Optional[np.ndarray] = None,
-                levels: bool = False, kappa: bool = False) -> Dict[str, np.ndarray]:
+                levels: bool = False, kappa: bool = False, metric: Optional[np.ndarray] = None) -> Dict[str, np.ndarray]:
     """Run the oracle on output pixels `pixels` ([n, 2] of (u, v); default: the whole output grid).
 
     Returns a dict with `out` [n, 3] (or [3, H, W] for the whole grid), `choice`, `margin` and, when
     `levels`, the per-level arrays `c0`, `var`, `pivot`, `count`, `valid` ([n, 3, J+M]), the
     rounding scales `efit` and `ew` (see lpa_oracle.c) and, with `kappa`, the condition numbers.
+    `metric` ([out_h, out_w, 3] of {Q11, Q12, Q22}, optional) steers the window of every pixel
+    (Section 5.4; see `steering_metric`).
     """
     lib = _load()
     grid = pixels is None
@@ -172,7 +176,11 @@ def reconstruct(sensors: Sequence, params, pixels: Optional[np.ndarray] = None,
                   efit=np.empty((n, 3, NL)), ew=np.empty((n, 3, NL)))
         if kappa:
             lv["kappa"] = np.empty((n, 3, NL))
-    rc = lib.orc_reconstruct(ctypes.byref(m.arr), m.n, ctypes.byref(m.params), n, _ptr(pu), _ptr(pv),
+    q = None
+    if metric is not None:
+        metric = np.asarray(metric, dtype=np.float64)
+        q = np.ascontiguousarray(metric[pv, pu].reshape(n, 3))
+    rc = lib.orc_reconstruct(ctypes.byref(m.arr), m.n, ctypes.byref(m.params), n, _ptr(pu), _ptr(pv), _ptr(q),
                              _ptr(out), _ptr(choice), _ptr(margin), _ptr(lv.get("c0")), _ptr(lv.get("var")),
                              _ptr(lv.get("pivot")), _ptr(lv.get("kappa")), _ptr(lv.get("count")),
                              _ptr(lv.get("valid")), _ptr(lv.get("efit")), _ptr(lv.get("ew")))
@@ -186,6 +194,77 @@ def reconstruct(sensors: Sequence, params, pixels: Optional[np.ndarray] = None,
         res["margin"] = margin.reshape(H, W, 3).transpose(2, 0, 1).copy()
     res["pixels"] = pixels
     return res
+
+
+def gradients(sensors: Sequence, params, grad_sigma: float) -> np.ndarray:
+    """First pass of the adaptive reconstruction (Section 5.4, green channel as in Section 5.5):
+    [out_h, out_w, 2] gradients of the isotropic order-1 G fit at scale grad_sigma (R/B units) at
+    every output pixel; 0 where the fit is not usable."""
+    lib = _load()
+    vv, uu = np.mgrid[0:params.out_h, 0:params.out_w]
+    pu = np.ascontiguousarray(uu.ravel(), dtype=np.int32)
+    pv = np.ascontiguousarray(vv.ravel(), dtype=np.int32)
+    n = pu.size
+    m = _Marshal(sensors, params)
+    gx = np.empty(n)
+    gy = np.empty(n)
+    rc = lib.orc_gradients(ctypes.byref(m.arr), m.n, ctypes.byref(m.params), float(grad_sigma), n, _ptr(pu), _ptr(pv),
+                           _ptr(gx), _ptr(gy))
+    if rc != 0:
+        raise ValueError(f"orc_gradients rejected its arguments (code {rc})")
+    return np.stack([gx, gy], axis=1).reshape(params.out_h, params.out_w, 2)
+
+
+def steering_metric(grad: np.ndarray, window_sigma: float, alpha: float, lambda1: float = 1.0,
+                    lambda2: float = 0.001, min_eig: float = 0.25, max_eig: float = 16.0) -> np.ndarray:
+    """Second pass (Section 5.4): per output pixel the steering matrix C_j (as {C11, C12, C22}) from
+    the gradients `grad` [H, W, 2] of the output pixels within 3 window_sigma (Gaussian weights
+    w_i, pixels inside the image only; M = their number). The singular values s1 >= s2 and right
+    singular vectors u1, u2 of the weighted gradient matrix (rows sqrt(w_i) g_i) are those of
+    T = sum_i w_i g_i g_i^T; elongation sigma_j = (s1 + lambda1) / (s2 + lambda1), scaling
+    gamma_j = ((s1 s2 + lambda2) / M)^alpha, and C_j = gamma_j (sigma_j u1 u1^T + u2 u2^T / sigma_j)
+    (reading: the window exp(-d^T C_j d / (2 sigma^2)) is narrow across the dominant gradient and
+    long along it), its two eigenvalues clamped to [min_eig, max_eig] (reading: bounds the window)."""
+    g = np.asarray(grad, dtype=np.float64)
+    H, W = g.shape[:2]
+    r = int(np.floor(3.0 * window_sigma))
+    T = np.zeros((H, W, 3))
+    M = np.zeros((H, W))
+    for dj in range(-r, r + 1):
+        for di in range(-r, r + 1):
+            if di * di + dj * dj > (3.0 * window_sigma) ** 2:
+                continue
+            w = np.exp(-(di * di + dj * dj) / (2.0 * window_sigma ** 2))
+            v0, v1 = max(0, -dj), min(H, H - dj)
+            u0, u1 = max(0, -di), min(W, W - di)
+            gs = g[v0 + dj:v1 + dj, u0 + di:u1 + di]
+            T[v0:v1, u0:u1, 0] += w * gs[..., 0] * gs[..., 0]
+            T[v0:v1, u0:u1, 1] += w * gs[..., 0] * gs[..., 1]
+            T[v0:v1, u0:u1, 2] += w * gs[..., 1] * gs[..., 1]
+            M[v0:v1, u0:u1] += 1.0
+    a, b, c = T[..., 0], T[..., 1], T[..., 2]
+    h = 0.5 * (a + c)
+    d = np.sqrt((0.5 * (a - c)) ** 2 + b * b)
+    l1, l2 = h + d, np.maximum(h - d, 0.0)
+    s1, s2 = np.sqrt(l1), np.sqrt(l2)
+    # eigenvector of l1: (b, l1 - a) or (l1 - c, b), whichever is longer; (1, 0) if T is diagonal with a >= c
+    e1x, e1y = b, l1 - a
+    f1x, f1y = l1 - c, b
+    use_f = f1x * f1x + f1y * f1y > e1x * e1x + e1y * e1y
+    ux = np.where(use_f, f1x, e1x)
+    uy = np.where(use_f, f1y, e1y)
+    nrm = np.sqrt(ux * ux + uy * uy)
+    iso = nrm == 0.0
+    ux = np.where(iso, 1.0, ux / np.where(iso, 1.0, nrm))
+    uy = np.where(iso, 0.0, uy / np.where(iso, 1.0, nrm))
+    elong = (s1 + lambda1) / (s2 + lambda1)
+    gamma = ((s1 * s2 + lambda2) / M) ** alpha
+    ea = np.clip(gamma * elong, min_eig, max_eig)   # along u1 (across the edge)
+    eb = np.clip(gamma / elong, min_eig, max_eig)   # along u2 = (-uy, ux)
+    C11 = ea * ux * ux + eb * uy * uy
+    C12 = (ea - eb) * ux * uy
+    C22 = ea * uy * uy + eb * ux * ux
+    return np.stack([C11, C12, C22], axis=2)
 
 
 def radiometry(y, b, g, t, a, n, read_var, sat):
@@ -224,3 +303,17 @@ def equivalent_kernel(sensors, params, u: int, v: int, c: int, sigma: float, ord
         raise ValueError(f"orc_equivalent_kernel rejected its arguments (code {k})")
     k = min(k, cap)
     return {key: val[:k] for key, val in bufs.items()}
+
+
+def adaptive(sensors: Sequence, params, grad_sigma: float, window_sigma: float, alpha: float,
+             lambda1: float = 1.0, lambda2: float = 0.001, min_eig: float = 0.25, max_eig: float = 16.0,
+             pixels: Optional[np.ndarray] = None, levels: bool = False, kappa: bool = False):
+    """The adaptive reconstruction of Sections 5.4-5.5 (CALPA): gradients of the green channel,
+    the steering matrix per output pixel, then the fit of every channel with the steered window.
+    Returns reconstruct()'s dict plus `grad` and `metric` (whole output grid)."""
+    g = gradients(sensors, params, grad_sigma)
+    q = steering_metric(g, window_sigma, alpha, lambda1, lambda2, min_eig, max_eig)
+    res = reconstruct(sensors, params, pixels, levels=levels, kappa=kappa, metric=q)
+    res["grad"] = g
+    res["metric"] = q
+    return res

@@ -235,14 +235,22 @@ typedef struct {
    * (its evaluation and the rounding of the sample position) by at most that x err_w. */
   double err_fit;    /* sum_k w_k L1_k (|f_k| + F1_k) */
   double err_w;      /* sum_k (G_k (1 + r_k^2 / sigma^2) / s2_k) L1_k |f_k - phi(d_k)^T c|, G the Gaussian */
+  double c1, c2;     /* fitted first-order coefficients (d/dx, d/dy of the local polynomial), order >= 1 */
 } orc_fit;
 
+/* Squared window distance of offset (dx, dy): |d|^2, or d^T Q d for the steered window of the
+ * adaptive reconstruction (Section 5.4; Q = {Q11, Q12, Q22}). */
+static double wdist2(const double *Q, double dx, double dy) {
+  return Q ? Q[0] * dx * dx + 2.0 * Q[1] * dx * dy + Q[2] * dy * dy : dx * dx + dy * dy;
+}
+
 /* Section 5.2, Eq. 6 for one channel at one scale and order, with the
- * Gaussian window of Eq. 8 (Section 5.3.1). `ell` (optional) receives the
- * equivalent kernel l_k = w_k e_0^T A^{-1} phi_k per sample (Section 5.2). */
+ * Gaussian window of Eq. 8 (Section 5.3.1), or its steered form when Q is
+ * given. `ell` (optional) receives the equivalent kernel
+ * l_k = w_k e_0^T A^{-1} phi_k per sample (Section 5.2). */
 static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int order,
-                   const orc_params *prm, int want_kappa, double *ell) {
-  orc_fit r = {0, 0, NAN, NAN, 0.0, INFINITY, NAN, NAN};
+                   const orc_params *prm, int want_kappa, double *ell, const double *Q) {
+  orc_fit r = {0, 0, NAN, NAN, 0.0, INFINITY, NAN, NAN, NAN, NAN};
   int P = n_unknowns(order);
   double k = prm->trunc_k;
   double R2 = (k * sigma_c) * (k * sigma_c);
@@ -251,7 +259,7 @@ static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int 
   for (int i = 0; i < n; i++) {
     const orc_sample *o = &smp[i];
     if (o->color != color) continue;
-    double r2 = o->dx * o->dx + o->dy * o->dy;
+    double r2 = wdist2(Q, o->dx, o->dy);
     if (!(r2 < R2)) continue;
     r.count++;
     double K = exp(-r2 / (2.0 * sigma_c * sigma_c)) - floor_w;     /* Eq. 8, truncated and tapered */
@@ -320,12 +328,16 @@ static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int 
   }
   r.c0 = c0;
   r.var = v;
+  if (P >= 3) {
+    r.c1 = cf[1];
+    r.c2 = cf[2];
+  }
   r.err_fit = 0.0;
   r.err_w = 0.0;
   for (int i = 0; i < n; i++) {
     const orc_sample *o = &smp[i];
     if (o->color != color) continue;
-    double r2 = o->dx * o->dx + o->dy * o->dy;
+    double r2 = wdist2(Q, o->dx, o->dy);
     if (!(r2 < R2)) continue;
     double G = exp(-r2 / (2.0 * sigma_c * sigma_c));
     double nw = prm->weight_mode == 1 ? 1.0 / sqrt(o->s2) : 1.0 / o->s2;
@@ -344,7 +356,7 @@ static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int 
       const orc_sample *o = &smp[i];
       ell[i] = 0.0;
       if (o->color != color) continue;
-      double r2 = o->dx * o->dx + o->dy * o->dy;
+      double r2 = wdist2(Q, o->dx, o->dy);
       if (!(r2 < R2)) continue;
       double K = exp(-r2 / (2.0 * sigma_c * sigma_c)) - floor_w;
       double w = prm->weight_mode == 1 ? K / sqrt(o->s2) : K / o->s2;
@@ -416,9 +428,18 @@ static int check_params(const orc_sensor *sens, int n_sensors, const orc_params 
  *                 (optional; lv_efit / lv_ew are the rounding scales err_fit / err_w of orc_fit)
  * Returns 0, or a negative code for invalid arguments.
  */
+/* Smallest eigenvalue of the symmetric 2x2 matrix {Q11, Q12, Q22}. */
+static double min_eig2(const double *Q) {
+  double h = 0.5 * (Q[0] + Q[2]), d = 0.5 * (Q[0] - Q[2]);
+  return h - sqrt(d * d + Q[1] * Q[1]);
+}
+
+/* metric (optional): per output pixel the steering matrix {Q11, Q12, Q22} of the adaptive
+ * reconstruction (Section 5.4): the window becomes exp(-d^T Q d / (2 sigma^2)) on the support
+ * d^T Q d < (k sigma)^2; NULL = the isotropic window. */
 int orc_reconstruct(const orc_sensor *sens, int n_sensors, const orc_params *p, int64_t n_pix,
-                    const int32_t *pu, const int32_t *pv, double *out, int32_t *choice, double *margin,
-                    double *lv_c0, double *lv_var, double *lv_pivot, double *lv_kappa,
+                    const int32_t *pu, const int32_t *pv, const double *metric, double *out, int32_t *choice,
+                    double *margin, double *lv_c0, double *lv_var, double *lv_pivot, double *lv_kappa,
                     int32_t *lv_count, int32_t *lv_valid, double *lv_efit, double *lv_ew) {
   int rc = check_params(sens, n_sensors, p);
   if (rc) return rc;
@@ -426,6 +447,9 @@ int orc_reconstruct(const orc_sensor *sens, int n_sensors, const orc_params *p, 
   const int J = p->n_scales, M = p->order, NL = n_levels(p);
   double rmax = p->trunc_k * p->sigma[J - 1];   /* R/B radius at the largest scale covers G too */
   if (p->green_ratio > 1.0) rmax *= p->green_ratio;
+  if (metric)  /* every steering matrix must be positive definite */
+    for (int64_t j = 0; j < n_pix; j++)
+      if (!(min_eig2(metric + 3 * j) > 0.0)) return -3;
 #pragma omp parallel
   {
     orc_sample *buf = NULL;
@@ -436,14 +460,16 @@ int orc_reconstruct(const orc_sensor *sens, int n_sensors, const orc_params *p, 
       double P[2];
       P[0] = p->out_affine[0] * pu[j] + p->out_affine[1] * pv[j] + p->out_affine[2];
       P[1] = p->out_affine[3] * pu[j] + p->out_affine[4] * pv[j] + p->out_affine[5];
-      int n = gather(sens, n_sensors, P, rmax, &buf, &cap);
+      const double *Q = metric ? metric + 3 * j : NULL;
+      /* the support d^T Q d < R^2 lies within |d| < R / sqrt(lambda_min(Q)) */
+      int n = gather(sens, n_sensors, P, Q ? rmax / sqrt(min_eig2(Q)) : rmax, &buf, &cap);
       for (int c = 0; c < 3; c++) {
         orc_fit lv[ORC_MAX_LEVELS];
         double sg = (c == 1) ? p->green_ratio : 1.0;
         for (int l = 0; l < J; l++)
-          lv[l] = fit(buf, n, c, p->sigma[l] * sg, M, p, lv_kappa != NULL, NULL);
+          lv[l] = fit(buf, n, c, p->sigma[l] * sg, M, p, lv_kappa != NULL, NULL, Q);
         for (int i = 0; i < M; i++)
-          lv[J + i] = fit(buf, n, c, p->sigma[J - 1] * sg, M - 1 - i, p, lv_kappa != NULL, NULL);
+          lv[J + i] = fit(buf, n, c, p->sigma[J - 1] * sg, M - 1 - i, p, lv_kappa != NULL, NULL, Q);
         double c0s[ORC_MAX_LEVELS], vars[ORC_MAX_LEVELS], mg = INFINITY;
         int val[ORC_MAX_LEVELS];
         for (int l = 0; l < NL; l++) {
@@ -497,7 +523,7 @@ int orc_equivalent_kernel(const orc_sensor *sens, int n_sensors, const orc_param
   int capb = 0;
   int n = gather(sens, n_sensors, P, p->trunc_k * sc, &buf, &capb);
   double *ell = (double *)calloc(n > 0 ? n : 1, sizeof(double));
-  orc_fit r = fit(buf, n, c, sc, order, p, 0, ell);
+  orc_fit r = fit(buf, n, c, sc, order, p, 0, ell, NULL);
   int w = 0;
   if (r.valid) {
     for (int i = 0; i < n; i++) {
@@ -519,4 +545,35 @@ int orc_equivalent_kernel(const orc_sensor *sens, int n_sensors, const orc_param
   free(ell);
   free(buf);
   return r.valid ? w : -1;
+}
+
+/*
+ * First pass of the adaptive reconstruction (Section 5.4, with the green channel as in Section
+ * 5.5): gradients (d/dx, d/dy in reference px) of an isotropic order-1 fit of the G channel at
+ * scale grad_sigma (R/B units; G uses grad_sigma * green_ratio) at each output pixel. A pixel
+ * whose fit is not usable gets gradient 0 (reading).
+ */
+int orc_gradients(const orc_sensor *sens, int n_sensors, const orc_params *p, double grad_sigma, int64_t n_pix,
+                  const int32_t *pu, const int32_t *pv, double *gx, double *gy) {
+  int rc = check_params(sens, n_sensors, p);
+  if (rc) return rc;
+  if (!(grad_sigma > 0.0) || n_pix < 0 || (n_pix > 0 && (!pu || !pv || !gx || !gy))) return -2;
+  const double sc = grad_sigma * p->green_ratio;
+#pragma omp parallel
+  {
+    orc_sample *buf = NULL;
+    int cap = 0;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t j = 0; j < n_pix; j++) {
+      double P[2];
+      P[0] = p->out_affine[0] * pu[j] + p->out_affine[1] * pv[j] + p->out_affine[2];
+      P[1] = p->out_affine[3] * pu[j] + p->out_affine[4] * pv[j] + p->out_affine[5];
+      int n = gather(sens, n_sensors, P, p->trunc_k * sc, &buf, &cap);
+      orc_fit f = fit(buf, n, 1, sc, 1, p, 0, NULL, NULL);
+      gx[j] = f.valid ? f.c1 : 0.0;
+      gy[j] = f.valid ? f.c2 : 0.0;
+    }
+    free(buf);
+  }
+  return 0;
 }
