@@ -297,6 +297,67 @@ hdr_status hdr_calib_exposure(hdr_ctx *ctx, const float *flat_mean, const float 
                               double ref_gain, double ref_exposure, int32_t width, int32_t height, double min_signal,
                               double max_level, double *nd, float *prnu_dev, int64_t *n_used, void *cuda_stream);
 
+/* ---------------------------------------------------------------- adaptive windows (Sections 5.4-5.5)
+ * CALPA: the window of every fit is steered by the local image structure. Three passes, each a
+ * kernel on the caller's stream:
+ *   1. gradients: the isotropic order-1 fit of the green channel at scale grad_sigma; its two
+ *      linear coefficients are the radiance gradient at the output pixel (Section 5.5 takes the
+ *      structure from G, which has twice the R/B sample density);
+ *   2. steering matrix: per output pixel, from the Gaussian-weighted gradients of the output
+ *      pixels within 3 window_sigma (M = the number of those inside the image), the singular
+ *      values s1 >= s2 and the dominant direction u1 of the gradient matrix give the elongation
+ *      sigma = (s1 + lambda1) / (s2 + lambda1), the scaling gamma = ((s1 s2 + lambda2) / M)^alpha
+ *      and C = gamma (sigma u1 u1^T + u2 u2^T / sigma), whose eigenvalues are then clamped to
+ *      [min_eig, max_eig];
+ *   3. the reconstruction of Sections 5.1-5.3 with the window exp(-d^T C d / (2 sigma_j^2)) on
+ *      d^T C d < (k sigma_j)^2 in place of Eq. 8's, lowered by exp(-k^2/2) as there: narrow across
+ *      an edge, long along it.
+ * Readings taken where the paper leaves the form open: C enters the exponent directly (no
+ * determinant normalisation: the fit's solution does not depend on a constant factor of the
+ * weights), the weights of pass 2 are Gaussian in the output-pixel distance, and the clamp of
+ * C's eigenvalues bounds every window between k sigma_J / sqrt(max_eig) and k sigma_J / sqrt(min_eig). */
+typedef struct {
+  double grad_sigma;   /* R/B scale of the pass-1 gradient fit (G uses green_ratio times it) */
+  double window_sigma; /* Gaussian scale of pass 2, in output pixels; 3 window_sigma <= 10   */
+  double alpha;        /* structure sensitivity, >= 0 (0: gamma = 1)                          */
+  double lambda1;      /* elongation regulariser, > 0                                         */
+  double lambda2;      /* scaling regulariser, > 0                                            */
+  double min_eig;      /* clamp of C's eigenvalues, 0 < min_eig <= max_eig; the staged window */
+  double max_eig;      /*   footprint grows by 1 / sqrt(min_eig)                              */
+} hdr_calpa_params;
+
+/* Defaults: grad_sigma 1.2, window_sigma 1, alpha 0.5, lambda1 1, lambda2 1e-3, eigenvalues
+ * clamped to [0.25, 16]. */
+void hdr_calpa_params_default(hdr_calpa_params *c);
+
+/* Pass 1. grad_dev: device [out_h][out_w][2] float32, the (x, y) gradient in radiance per output
+ * reference pixel at each output pixel; 0 where the fit is not usable (fewer than 3 samples, or
+ * a pivot at or below min_pivot). params supplies the rig geometry, output mapping, green_ratio,
+ * trunc_k, min_pivot, cond_fallback and accum; its order, scales and tab_weights are not used.
+ * Asynchronous on `cuda_stream`. */
+hdr_status hdr_calpa_gradients(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const hdr_calpa_params *calpa,
+                               const uint16_t *const *raw_dev, float *grad_dev, void *cuda_stream);
+
+/* Pass 2. grad_dev as pass 1 writes it; metric_dev: device [out_h][out_w][3] float32 = C11, C12,
+ * C22. The structure tensor is summed and decomposed in FP64. Asynchronous on `cuda_stream`. */
+hdr_status hdr_calpa_metric(hdr_ctx *ctx, int32_t out_w, int32_t out_h, const hdr_calpa_params *calpa,
+                            const float *grad_dev, float *metric_dev, void *cuda_stream);
+
+/* Pass 3: hdr_reconstruct with the steered window of metric_dev ([out_h][out_w][3], as pass 2
+ * writes it; any symmetric C whose eigenvalues are at least calpa->min_eig may be given: a window
+ * reaching beyond the footprint staged for that bound is reported by hdr_check as HDR_E_INTERNAL).
+ * Asynchronous on `cuda_stream`. */
+hdr_status hdr_reconstruct_steered(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                                   const hdr_calpa_params *calpa, const uint16_t *const *raw_dev,
+                                   const float *metric_dev, void *out_dev, uint8_t *choice_dev, void *cuda_stream);
+
+/* The three passes in one call, with the gradient and metric planes in scratch owned by the
+ * context (grown on demand, which waits for the device; calls that share a context must be
+ * serialised on one stream). Asynchronous on `cuda_stream`. */
+hdr_status hdr_reconstruct_adaptive(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                                    const hdr_calpa_params *calpa, const uint16_t *const *raw_dev, void *out_dev,
+                                    uint8_t *choice_dev, void *cuda_stream);
+
 /* Size of the fixed device array that hdr_reconstruct_noalloc uses as scratch. */
 #define HDR_NOALLOC_SCRATCH_BYTES (4u << 20)
 

@@ -75,7 +75,7 @@ def _load():
         lib.orc_radiometry.argtypes = [ctypes.c_double] * 8 + [P, P]
         lib.orc_radiometry.restype = ctypes.c_int
         lib.orc_ici.argtypes = [ctypes.c_int, P, P, P, ctypes.c_double, P]
-        lib.orc_gradients.argtypes = [P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int64, P, P, P, P]
+        lib.orc_gradients.argtypes = [P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P, P]
         lib.orc_gradients.restype = ctypes.c_int
         lib.orc_ici.restype = ctypes.c_int
         lib.orc_equivalent_kernel.argtypes = [P, ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -196,23 +196,40 @@ def reconstruct(sensors: Sequence, params, pixels: Optional[np.ndarray] = None,
     return res
 
 
-def gradients(sensors: Sequence, params, grad_sigma: float) -> np.ndarray:
+def gradients(sensors: Sequence, params, grad_sigma: float, pixels: Optional[np.ndarray] = None,
+              diagnostics: bool = False):
     """First pass of the adaptive reconstruction (Section 5.4, green channel as in Section 5.5):
-    [out_h, out_w, 2] gradients of the isotropic order-1 G fit at scale grad_sigma (R/B units) at
-    every output pixel; 0 where the fit is not usable."""
+    the gradient (c1, c2) of the isotropic order-1 G fit at scale grad_sigma (R/B units) at each
+    output pixel; 0 where the fit is not usable. Whole grid: [out_h, out_w, 2]; `pixels` ([n, 2] of
+    (u, v)): [n, 2]. With `diagnostics`, returns a dict with `grad` and, per pixel, the fit's
+    smallest equilibrated pivot `pivot`, sample `count` and the rounding scales `efit`, `ew` of c1
+    and c2 ([..., 2], as reconstruct() reports them for C_0)."""
     lib = _load()
-    vv, uu = np.mgrid[0:params.out_h, 0:params.out_w]
-    pu = np.ascontiguousarray(uu.ravel(), dtype=np.int32)
-    pv = np.ascontiguousarray(vv.ravel(), dtype=np.int32)
+    grid = pixels is None
+    if grid:
+        vv, uu = np.mgrid[0:params.out_h, 0:params.out_w]
+        pixels = np.stack([uu.ravel(), vv.ravel()], axis=1)
+    pixels = np.asarray(pixels, dtype=np.int64)
+    pu = np.ascontiguousarray(pixels[:, 0], dtype=np.int32)
+    pv = np.ascontiguousarray(pixels[:, 1], dtype=np.int32)
     n = pu.size
     m = _Marshal(sensors, params)
     gx = np.empty(n)
     gy = np.empty(n)
+    dg = {}
+    if diagnostics:
+        dg = dict(pivot=np.empty(n), count=np.empty(n, dtype=np.int32), efit=np.empty((n, 2)), ew=np.empty((n, 2)))
     rc = lib.orc_gradients(ctypes.byref(m.arr), m.n, ctypes.byref(m.params), float(grad_sigma), n, _ptr(pu), _ptr(pv),
-                           _ptr(gx), _ptr(gy))
+                           _ptr(gx), _ptr(gy), _ptr(dg.get("pivot")), _ptr(dg.get("count")), _ptr(dg.get("efit")),
+                           _ptr(dg.get("ew")))
     if rc != 0:
         raise ValueError(f"orc_gradients rejected its arguments (code {rc})")
-    return np.stack([gx, gy], axis=1).reshape(params.out_h, params.out_w, 2)
+    shape = (params.out_h, params.out_w) if grid else (n,)
+    g = np.stack([gx, gy], axis=1).reshape(*shape, 2)
+    if not diagnostics:
+        return g
+    return dict(grad=g, pivot=dg["pivot"].reshape(shape), count=dg["count"].reshape(shape),
+                efit=dg["efit"].reshape(*shape, 2), ew=dg["ew"].reshape(*shape, 2))
 
 
 def steering_metric(grad: np.ndarray, window_sigma: float, alpha: float, lambda1: float = 1.0,

@@ -236,6 +236,9 @@ typedef struct {
   double err_fit;    /* sum_k w_k L1_k (|f_k| + F1_k) */
   double err_w;      /* sum_k (G_k (1 + r_k^2 / sigma^2) / s2_k) L1_k |f_k - phi(d_k)^T c|, G the Gaussian */
   double c1, c2;     /* fitted first-order coefficients (d/dx, d/dy of the local polynomial), order >= 1 */
+  /* The same two rounding scales for c1 and c2 (order >= 1), with L1_k taken from the equivalent
+   * kernels A^{-1} e_1 and A^{-1} e_2 of those coefficients in place of l. */
+  double err_fit_c[2], err_w_c[2];
 } orc_fit;
 
 /* Squared window distance of offset (dx, dy): |d|^2, or d^T Q d for the steered window of the
@@ -305,11 +308,12 @@ static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int 
   if (!(minp > 0.0)) return r;
   /* l = A^{-1} e_0 = D (D A D)^{-1} D e_0 (and c = A^{-1} b the same way):
    * solve L z = D rhs, z /= d, L^T x = z, result D x. */
-  double l[ORC_MAX_P], cf[ORC_MAX_P];
-  for (int which = 0; which < 2; which++) {
+  double l[ORC_MAX_P], cf[ORC_MAX_P], lg[2][ORC_MAX_P];  /* lg: A^{-1} e_1, A^{-1} e_2 */
+  for (int which = 0; which < (P >= 3 ? 4 : 2); which++) {
     double z[ORC_MAX_P], x[ORC_MAX_P];
     for (int i = 0; i < P; i++) {
-      double s = D[i] * (which == 0 ? (i == 0 ? 1.0 : 0.0) : bvec[i]);
+      double e = which == 1 ? bvec[i] : (i == (which == 0 ? 0 : which - 1) ? 1.0 : 0.0);
+      double s = D[i] * e;
       for (int m = 0; m < i; m++) s -= L[i * P + m] * z[m];
       z[i] = s;
     }
@@ -319,7 +323,7 @@ static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int 
       for (int m = i + 1; m < P; m++) s -= L[m * P + i] * x[m];
       x[i] = s;
     }
-    for (int i = 0; i < P; i++) (which == 0 ? l : cf)[i] = D[i] * x[i];
+    for (int i = 0; i < P; i++) (which == 0 ? l : which == 1 ? cf : lg[which - 2])[i] = D[i] * x[i];
   }
   double c0 = 0.0, v = 0.0;
   for (int a = 0; a < P; a++) {
@@ -350,6 +354,12 @@ static orc_fit fit(const orc_sample *smp, int n, int color, double sigma_c, int 
     }
     r.err_fit += (G - floor_w) * nw * l1 * (fabs(o->f) + f1);
     r.err_w += G * (1.0 + r2 / (sigma_c * sigma_c)) * nw * l1 * fabs(o->f - fit_k);
+    for (int g = 0; g < 2 && P >= 3; g++) {
+      double lk = 0.0;
+      for (int a = 0; a < P; a++) lk += fabs(lg[g][a] * phi[a]);
+      r.err_fit_c[g] += (G - floor_w) * nw * lk * (fabs(o->f) + f1);
+      r.err_w_c[g] += G * (1.0 + r2 / (sigma_c * sigma_c)) * nw * lk * fabs(o->f - fit_k);
+    }
   }
   if (ell) {
     for (int i = 0; i < n; i++) {
@@ -554,7 +564,8 @@ int orc_equivalent_kernel(const orc_sensor *sens, int n_sensors, const orc_param
  * whose fit is not usable gets gradient 0 (reading).
  */
 int orc_gradients(const orc_sensor *sens, int n_sensors, const orc_params *p, double grad_sigma, int64_t n_pix,
-                  const int32_t *pu, const int32_t *pv, double *gx, double *gy) {
+                  const int32_t *pu, const int32_t *pv, double *gx, double *gy, double *pivot, int32_t *count,
+                  double *err_fit, double *err_w) {
   int rc = check_params(sens, n_sensors, p);
   if (rc) return rc;
   if (!(grad_sigma > 0.0) || n_pix < 0 || (n_pix > 0 && (!pu || !pv || !gx || !gy))) return -2;
@@ -572,6 +583,17 @@ int orc_gradients(const orc_sensor *sens, int n_sensors, const orc_params *p, do
       orc_fit f = fit(buf, n, 1, sc, 1, p, 0, NULL, NULL);
       gx[j] = f.valid ? f.c1 : 0.0;
       gy[j] = f.valid ? f.c2 : 0.0;
+      /* optional diagnostics: the usability test's inputs and the rounding scales of c1, c2 */
+      if (pivot) pivot[j] = f.min_pivot;
+      if (count) count[j] = f.count;
+      if (err_fit) {
+        err_fit[2 * j] = f.err_fit_c[0];
+        err_fit[2 * j + 1] = f.err_fit_c[1];
+      }
+      if (err_w) {
+        err_w[2 * j] = f.err_w_c[0];
+        err_w[2 * j + 1] = f.err_w_c[1];
+      }
     }
     free(buf);
   }

@@ -21,7 +21,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-diag-suppress", "1160", f"-I{CSRC}", f"-I{INCLUDE}"]
-SOURCES = ["lpa_host.cu", "lpa_m0.cu", "lpa_m1.cu", "lpa_m2.cu", "lpa_serve.cu", "lpa_calib.cu"]
+SOURCES = ["lpa_host.cu", "lpa_m0.cu", "lpa_m1.cu", "lpa_m2.cu", "lpa_serve.cu", "lpa_calib.cu", "lpa_calpa.cu"]
 
 
 def _deps_mtime() -> float:

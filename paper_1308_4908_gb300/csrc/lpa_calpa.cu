@@ -1,0 +1,201 @@
+// Adaptive windows (CALPA, Sections 5.4-5.5): the steering-matrix pass and the entry points of the
+// three passes. The gradient pass (isotropic order-1 green fit) and the steered reconstruction are
+// modes of the reconstruction kernel (lpa_kernel.cuh).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "hdr_lpa.h"
+#include "lpa_internal.h"
+#include "lpa_launch.h"
+
+namespace {
+
+constexpr int kRmax = 10;  // largest radius (output pixels) of the pass-2 disc
+constexpr int kBX = 32, kBY = 8;
+
+struct MetricArgs {
+  const float2 *grad;
+  float *metric;
+  int W, H, r;
+  int rw[2 * kRmax + 1];           // half width of the disc in row offset dj (|di| <= rw)
+  double w[2 * kRmax * kRmax + 1];  // Gaussian weight by di^2 + dj^2
+  double alpha, lambda1, lambda2, min_eig, max_eig;
+};
+
+__device__ __forceinline__ double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
+
+// One thread per output pixel. The gradients of the block and its halo are staged in shared
+// memory; T = sum_i w_i g_i g_i^T over the disc is summed in FP64 (T of a straight edge is nearly
+// rank one, and its small eigenvalue is the difference of large sums), then decomposed in closed
+// form: l1,2 = h +- sqrt(((a - c) / 2)^2 + b^2), s = sqrt(l), u1 the eigenvector of l1.
+__global__ void __launch_bounds__(kBX *kBY) calpa_metric(const __grid_constant__ MetricArgs A) {
+  __shared__ float2 tile[(kBY + 2 * kRmax) * (kBX + 2 * kRmax)];
+  const int r = A.r, TW = kBX + 2 * r, TH = kBY + 2 * r;
+  const int bx0 = blockIdx.x * kBX, by0 = blockIdx.y * kBY;
+  const int tid = threadIdx.y * kBX + threadIdx.x;
+  for (int e = tid; e < TW * TH; e += kBX * kBY) {
+    const int X = bx0 - r + e % TW, Y = by0 - r + e / TW;
+    tile[e] = (X >= 0 && X < A.W && Y >= 0 && Y < A.H) ? A.grad[(size_t)Y * A.W + X] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int u = bx0 + threadIdx.x, v = by0 + threadIdx.y;
+  if (u >= A.W || v >= A.H) return;
+  double a = 0.0, b = 0.0, c = 0.0;
+  int M = 0;
+  for (int dj = -r; dj <= r; dj++) {
+    const int vv = v + dj;
+    if (vv < 0 || vv >= A.H) continue;
+    const int rw = A.rw[dj + r];
+    M += min(u + rw, A.W - 1) - max(u - rw, 0) + 1;  // disc cells of this row inside the image
+    const float2 *row = tile + (threadIdx.y + r + dj) * TW + threadIdx.x + r;
+    for (int di = -rw; di <= rw; di++) {
+      const float2 g = row[di];
+      const double wt = A.w[di * di + dj * dj];
+      const double gx = g.x, gy = g.y, p = wt * gx;
+      a = fma(p, gx, a);
+      b = fma(p, gy, b);
+      c = fma(wt * gy, gy, c);
+    }
+  }
+  const double h = 0.5 * (a + c), d = sqrt(0.25 * (a - c) * (a - c) + b * b);
+  const double l1 = h + d, l2 = fmax(h - d, 0.0);
+  const double s1 = sqrt(l1), s2 = sqrt(l2);
+  // eigenvector of l1: (b, l1 - a) or (l1 - c, b), the longer; (1, 0) when T = 0
+  double ux = b, uy = l1 - a;
+  const double fx = l1 - c, fy = b;
+  if (fx * fx + fy * fy > ux * ux + uy * uy) {
+    ux = fx;
+    uy = fy;
+  }
+  const double nrm = sqrt(ux * ux + uy * uy);
+  if (nrm == 0.0) {
+    ux = 1.0;
+    uy = 0.0;
+  } else {
+    ux /= nrm;
+    uy /= nrm;
+  }
+  const double elong = (s1 + A.lambda1) / (s2 + A.lambda1);
+  const double gamma = pow((s1 * s2 + A.lambda2) / (double)M, A.alpha);
+  const double ea = clampd(gamma * elong, A.min_eig, A.max_eig);  // along u1: across the edge
+  const double eb = clampd(gamma / elong, A.min_eig, A.max_eig);  // along u2: along the edge
+  float *o = A.metric + ((size_t)v * A.W + u) * 3;
+  o[0] = (float)(ea * ux * ux + eb * uy * uy);
+  o[1] = (float)((ea - eb) * ux * uy);
+  o[2] = (float)(ea * uy * uy + eb * ux * ux);
+}
+
+hdr_status check_calpa(const hdr_calpa_params *c) {
+  if (!c) return lpa_fail(HDR_E_INVALID, "calpa is NULL");
+  auto fin = [](double x) { return std::isfinite(x); };
+  if (!(c->grad_sigma > 0.0) || !fin(c->grad_sigma))
+    return lpa_fail(HDR_E_INVALID, "grad_sigma must be finite and > 0");
+  if (!(c->window_sigma > 0.0) || !(3.0 * c->window_sigma < kRmax + 1.0))
+    return lpa_fail(HDR_E_INVALID, "window_sigma must be > 0 with 3 window_sigma < 11");
+  if (!(c->alpha >= 0.0) || !fin(c->alpha)) return lpa_fail(HDR_E_INVALID, "alpha must be finite and >= 0");
+  if (!(c->lambda1 > 0.0) || !(c->lambda2 > 0.0) || !fin(c->lambda1) || !fin(c->lambda2))
+    return lpa_fail(HDR_E_INVALID, "lambda1 and lambda2 must be finite and > 0");
+  if (!(c->min_eig > 0.0) || !(c->max_eig >= c->min_eig) || !fin(c->max_eig))
+    return lpa_fail(HDR_E_INVALID, "0 < min_eig <= max_eig < inf required");
+  return HDR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hdr_calpa_params_default(hdr_calpa_params *c) {
+  if (!c) return;
+  c->grad_sigma = 1.2;
+  c->window_sigma = 1.0;
+  c->alpha = 0.5;
+  c->lambda1 = 1.0;
+  c->lambda2 = 1e-3;
+  c->min_eig = 0.25;
+  c->max_eig = 16.0;
+}
+
+hdr_status hdr_calpa_gradients(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const hdr_calpa_params *calpa,
+                               const uint16_t *const *raw_dev, float *grad_dev, void *cuda_stream) {
+  hdr_status st = check_calpa(calpa);
+  if (st) return st;
+  if (!params) return lpa_fail(HDR_E_INVALID, "params is NULL");
+  hdr_params p = *params;  // one isotropic order-1 fit at grad_sigma
+  p.order = 1;
+  p.n_scales = 1;
+  p.sigma[0] = calpa->grad_sigma;
+  return lpa_launch_mode(ctx, rig_id, &p, raw_dev, LPA_GRADIENTS, grad_dev, 1.0, nullptr, nullptr,
+                         (cudaStream_t)cuda_stream);
+}
+
+hdr_status hdr_calpa_metric(hdr_ctx *ctx, int32_t out_w, int32_t out_h, const hdr_calpa_params *calpa,
+                            const float *grad_dev, float *metric_dev, void *cuda_stream) {
+  if (!ctx) return lpa_fail(HDR_E_INVALID, "ctx is NULL");
+  hdr_status st = check_calpa(calpa);
+  if (st) return st;
+  if (out_w < 0 || out_h < 0) return lpa_fail(HDR_E_INVALID, "negative output size");
+  if ((long long)out_w * out_h > (1LL << 31) / 4) return lpa_fail(HDR_E_UNSUPPORTED, "output too large");
+  if ((long long)out_w * out_h == 0) return HDR_OK;
+  if (!grad_dev || !metric_dev) return lpa_fail(HDR_E_INVALID, "grad_dev and metric_dev are required");
+  if (reinterpret_cast<uintptr_t>(grad_dev) % 8) return lpa_fail(HDR_E_INVALID, "grad_dev not 8-byte aligned");
+  if (cudaSetDevice(lpa_ctx_device(ctx)) != cudaSuccess) return lpa_fail(HDR_E_CUDA, "cudaSetDevice failed");
+  MetricArgs A{};
+  A.grad = reinterpret_cast<const float2 *>(grad_dev);
+  A.metric = metric_dev;
+  A.W = out_w;
+  A.H = out_h;
+  const double ws = calpa->window_sigma, R = 3.0 * ws;
+  A.r = (int)std::floor(R);
+  for (int dj = -A.r; dj <= A.r; dj++) {
+    int rw = 0;
+    while (rw + 1 <= A.r && (double)((rw + 1) * (rw + 1) + dj * dj) <= R * R) rw++;
+    A.rw[dj + A.r] = rw;
+  }
+  for (int k = 0; k <= 2 * A.r * A.r; k++) A.w[k] = std::exp(-(double)k / (2.0 * ws * ws));
+  A.alpha = calpa->alpha;
+  A.lambda1 = calpa->lambda1;
+  A.lambda2 = calpa->lambda2;
+  A.min_eig = calpa->min_eig;
+  A.max_eig = calpa->max_eig;
+  calpa_metric<<<dim3((out_w + kBX - 1) / kBX, (out_h + kBY - 1) / kBY), dim3(kBX, kBY), 0,
+                 (cudaStream_t)cuda_stream>>>(A);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return lpa_fail(HDR_E_CUDA, cudaGetErrorString(e));
+  return HDR_OK;
+}
+
+hdr_status hdr_reconstruct_steered(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                                   const hdr_calpa_params *calpa, const uint16_t *const *raw_dev,
+                                   const float *metric_dev, void *out_dev, uint8_t *choice_dev, void *cuda_stream) {
+  hdr_status st = check_calpa(calpa);
+  if (st) return st;
+  if (!params) return lpa_fail(HDR_E_INVALID, "params is NULL");
+  if (!metric_dev && (long long)params->out_w * params->out_h > 0) return lpa_fail(HDR_E_INVALID, "metric_dev is NULL");
+  return lpa_launch_mode(ctx, rig_id, params, raw_dev, LPA_STEERED, const_cast<float *>(metric_dev),
+                         1.0 / std::sqrt(calpa->min_eig), out_dev, choice_dev, (cudaStream_t)cuda_stream);
+}
+
+hdr_status hdr_reconstruct_adaptive(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                                    const hdr_calpa_params *calpa, const uint16_t *const *raw_dev, void *out_dev,
+                                    uint8_t *choice_dev, void *cuda_stream) {
+  if (!ctx) return lpa_fail(HDR_E_INVALID, "ctx is NULL");
+  hdr_status st = check_calpa(calpa);
+  if (st) return st;
+  st = lpa_check_params(params);
+  if (st) return st;
+  const size_t npx = (size_t)params->out_w * params->out_h;
+  if (npx == 0) return HDR_OK;
+  void *scratch = nullptr;
+  st = lpa_ctx_calpa_scratch(ctx, npx * 5 * sizeof(float), &scratch);
+  if (st) return st;
+  float *grad = static_cast<float *>(scratch), *metric = grad + npx * 2;
+  st = hdr_calpa_gradients(ctx, rig_id, params, calpa, raw_dev, grad, cuda_stream);
+  if (st) return st;
+  st = hdr_calpa_metric(ctx, params->out_w, params->out_h, calpa, grad, metric, cuda_stream);
+  if (st) return st;
+  return hdr_reconstruct_steered(ctx, rig_id, params, calpa, raw_dev, metric, out_dev, choice_dev, cuda_stream);
+}
+
+}  // extern "C"

@@ -27,18 +27,21 @@ inline cudaError_t lpa_opt_in(const void *fn) {
                               lpa_smem_optin() - (int)a.sharedSizeBytes);
 }
 
+// One CTA per tile of L with the kernel of L.mode (cudaErrorInvalidConfiguration where that mode
+// is not instantiated for the order or tile height).
 cudaError_t lpa_launch_order0(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
 cudaError_t lpa_launch_order1(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
 cudaError_t lpa_launch_order2(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
 
-// The single-frame kernel of order M for that configuration (for graph kernel nodes).
-const void *lpa_kernel_order0(bool comp, bool diag, bool tab, int tile_h);
-const void *lpa_kernel_order1(bool comp, bool diag, bool tab, int tile_h);
-const void *lpa_kernel_order2(bool comp, bool diag, bool tab, int tile_h);
-inline const void *lpa_kernel(int order, bool comp, bool diag, bool tab, int tile_h) {
-  return order == 0   ? lpa_kernel_order0(comp, diag, tab, tile_h)
-         : order == 1 ? lpa_kernel_order1(comp, diag, tab, tile_h)
-                      : lpa_kernel_order2(comp, diag, tab, tile_h);
+// The single-frame kernel of order M for that configuration (for graph kernel nodes); mode is one
+// of LPA_SEARCHED .. LPA_GRADIENTS; nullptr where that combination is not instantiated.
+const void *lpa_kernel_order0(bool comp, bool diag, int mode, int tile_h);
+const void *lpa_kernel_order1(bool comp, bool diag, int mode, int tile_h);
+const void *lpa_kernel_order2(bool comp, bool diag, int mode, int tile_h);
+inline const void *lpa_kernel(int order, bool comp, bool diag, int mode, int tile_h) {
+  return order == 0   ? lpa_kernel_order0(comp, diag, mode, tile_h)
+         : order == 1 ? lpa_kernel_order1(comp, diag, mode, tile_h)
+                      : lpa_kernel_order2(comp, diag, mode, tile_h);
 }
 
 // Persistent launch of order M over its segment of a many-frame tile list (tile height 8 or 16).

@@ -127,6 +127,9 @@ struct hdr_ctx {
   // copy streams and band events of the host-buffer entry point (created on first use)
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_in[8] = {}, ev_done[8] = {};
+  // gradient and steering-matrix planes of the adaptive reconstruction
+  void *calpa = nullptr;
+  size_t calpa_cap = 0;
 };
 
 namespace {
@@ -329,12 +332,15 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
   }
   L.tab_hdr = static_cast<const int4 *>(it->second);
   L.tab_cells = reinterpret_cast<const float4 *>(static_cast<const int4 *>(it->second) + hdr.size());
+  L.mode = LPA_TABULATED;
   return HDR_OK;
 }
 
 // Fill the launch descriptor for one frame. raw: device pointers per sensor.
+// reach: the largest window grows by this factor (the steered window of Section 5.4 reaches
+// 1 / sqrt(smallest eigenvalue of C) times the isotropic radius).
 hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, const uint16_t *const *raw,
-                    LpaLaunch &L, int tile_h = 16) {
+                    LpaLaunch &L, int tile_h = 16, double reach = 1.0) {
   memset(&L, 0, sizeof(L));
   L.n_sensors = rig.n;
   L.order = p->order;
@@ -354,7 +360,7 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
   L.tiles_y = (p->out_h + tile_h - 1) / tile_h;
   L.out_half = p->out_dtype;
   L.status = env.status;
-  const double rmax = p->trunc_k * p->sigma[p->n_scales - 1] * std::fmax(1.0, p->green_ratio);
+  const double rmax = reach * p->trunc_k * p->sigma[p->n_scales - 1] * std::fmax(1.0, p->green_ratio);
   uint32_t off = 0, tx = 0;
   for (int s = 0; s < rig.n; s++) {
     const hdr_sensor_desc &d = rig.s[s].d;
@@ -427,8 +433,9 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
   return build_tables(env, rig, p, L);
 }
 
-hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L) {
-  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs}, rig, p, raw, L);
+hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
+                double reach = 1.0) {
+  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs}, rig, p, raw, L, 16, reach);
 }
 
 hdr_status launch(const LpaLaunch &L, int accum, bool diag, cudaStream_t st) {
@@ -530,6 +537,7 @@ void hdr_destroy(hdr_ctx *ctx) {
   for (int s = 0; s < HDR_MAX_SENSORS; s++) cudaFree(ctx->raw_stage[s]);
   cudaFree(ctx->out_stage);
   cudaFree(ctx->choice_stage);
+  cudaFree(ctx->calpa);
   for (auto &t : ctx->tabs.dev) cudaFree(t.second);
   if (ctx->h2d) cudaStreamDestroy(ctx->h2d);
   if (ctx->d2h) cudaStreamDestroy(ctx->d2h);
@@ -935,9 +943,10 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
   std::vector<void *> args(order.size());
   for (size_t k = 0; k < order.size(); k++) {
     const LpaLaunch &L = plans[order[k]];
-    const void *fn = lpa_kernel(L.order, comp, false, L.tab_cells != nullptr, cfg.tile_h);
+    const void *fn = lpa_kernel(L.order, comp, false, L.mode, cfg.tile_h);
+    if (!fn) return fail(HDR_E_INTERNAL, "no kernel for order %d, mode %d, tile height %d", L.order, L.mode, cfg.tile_h);
     CUDA_TRY(lpa_opt_in(fn));
-    key.push_back({L.order * 2 + (L.tab_cells ? 1 : 0), comp ? 1 : 0, cfg.tile_h, grid[order[k]], (int64_t)L.smem_bytes});
+    key.push_back({L.order * 4 + L.mode, comp ? 1 : 0, cfg.tile_h, grid[order[k]], (int64_t)L.smem_bytes});
     args[k] = &plans[order[k]];
     kp[k] = cudaKernelNodeParams{};
     kp[k].func = const_cast<void *>(fn);
@@ -1094,6 +1103,34 @@ void lpa_ctx_rig_sizes(const hdr_ctx *ctx, int rig_id, int *pitch, int *height) 
   }
 }
 hdr_status lpa_fail(hdr_status st, const char *msg) { return fail(st, "%s", msg); }
+hdr_status lpa_ctx_calpa_scratch(hdr_ctx *ctx, size_t bytes, void **ptr) {
+  if (bytes > ctx->calpa_cap) {
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(ctx->calpa);
+    ctx->calpa = nullptr;
+    ctx->calpa_cap = 0;
+    CUDA_TRY(cudaMalloc(&ctx->calpa, bytes));
+    ctx->calpa_cap = bytes;
+  }
+  *ptr = ctx->calpa;
+  return HDR_OK;
+}
+hdr_status lpa_launch_mode(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_dev,
+                           int mode, float *aux, double reach, void *out_dev, uint8_t *choice_dev, cudaStream_t st) {
+  hdr_status s = common_checks(ctx, rig_id, params, raw_dev, mode == LPA_GRADIENTS ? aux : out_dev);
+  if (s) return s;
+  hdr_params p = *params;
+  p.tab_weights = 0;  // the window is searched: offsets or weights differ per pixel
+  LpaLaunch L;
+  s = plan(ctx, ctx->rigs[rig_id], &p, raw_dev, L, reach);
+  if (s) return s;
+  L.mode = mode;
+  L.aux = aux;
+  L.out = out_dev;
+  L.choice = choice_dev;
+  return launch(L, p.accum, false, st);
+}
 hdr_status lpa_check_params(const hdr_params *p) { return check_params(p); }
 hdr_status lpa_take_status(hdr_ctx *ctx) {
   unsigned int word = 0;

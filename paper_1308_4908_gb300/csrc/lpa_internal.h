@@ -18,3 +18,11 @@ hdr_status lpa_check_params(const hdr_params *p);
 // Read and clear the context's device status word without waiting for any stream (launches
 // still running may set it later); HDR_E_TIMEOUT / HDR_E_INTERNAL as hdr_check reports them.
 hdr_status lpa_take_status(hdr_ctx *ctx);
+// Plan and launch one frame with the kernel of `mode` (LPA_STEERED: aux = the steering matrices,
+// the window's reach grown by `reach`; LPA_GRADIENTS: aux receives the gradients and no output
+// is written). The window is always searched.
+hdr_status lpa_launch_mode(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_dev,
+                           int mode, float *aux, double reach, void *out_dev, uint8_t *choice_dev, cudaStream_t st);
+// Device scratch of at least `bytes` owned by the context for the adaptive reconstruction
+// (growing it waits for the device).
+hdr_status lpa_ctx_calpa_scratch(hdr_ctx *ctx, size_t bytes, void **ptr);

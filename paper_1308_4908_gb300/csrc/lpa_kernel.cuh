@@ -229,6 +229,7 @@ struct FitOut {
   float c0, var;
   float dmin, dmax;  // extreme pivots of the equilibrated LDL^T
   bool valid;
+  float c1, c2;      // first-order coefficients c = A^{-1} b (only when asked for)
 };
 
 __device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.f, x); }
@@ -242,7 +243,7 @@ __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j
 // Jacobi-equilibrated matrix D A D (D = diag(A)^{-1/2}), which are d_j / A_jj: equilibration
 // changes L but scales each pivot by 1 / A_jj. l = A^{-1} e_0, C_0 = l^T b,
 // Var C_0 = l^T (Phi^T W S W Phi) l with S the sample variances.
-template <typename T, int P, class MOM>
+template <typename T, int P, class MOM, bool COEF = false>
 __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
   FitOut r;
   T a[P * (P + 1) / 2];  // lower triangle, overwritten by L (below the diagonal) and D
@@ -317,6 +318,31 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
   }
   r.c0 = (float)c0;
   r.var = (float)var;
+  if constexpr (COEF && P >= 3) {
+    // c = A^{-1} b by the same factors: forward (unit L), diagonal, backward (L^T)
+    T y[P];
+#pragma unroll
+    for (int i = 0; i < P; i++) {
+      T t = m.template B<T>(i);
+#pragma unroll
+      for (int q = 0; q < P; q++)
+        if (q < i) t -= a[tri(i, q)] * y[q];
+      y[i] = t;
+    }
+#pragma unroll
+    for (int i = 0; i < P; i++) y[i] *= dinv[i];
+#pragma unroll
+    for (int ii = 0; ii < P; ii++) {
+      const int i = P - 1 - ii;
+      T t = y[i];
+#pragma unroll
+      for (int q = 0; q < P; q++)
+        if (q > i) t -= a[tri(q, i)] * y[q];
+      y[i] = t;
+    }
+    r.c1 = (float)y[1];
+    r.c2 = (float)y[2];
+  }
   return r;
 }
 
@@ -327,12 +353,12 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
 
 // FP32 solve; the same solve in FP64 when the FP32 pivots span more than
 // cond_fallback and the fit could still pass min_pivot in exact arithmetic.
-template <int P, class MOM>
+template <int P, class MOM, bool COEF = false>
 __device__ __forceinline__ FitOut solve_with_fallback(const MOM &m, float min_pivot, float cond_fallback) {
-  FitOut r = solve<float, P>(m, min_pivot);
+  FitOut r = solve<float, P, MOM, COEF>(m, min_pivot);
   bool redo = cond_fallback > 0.f && m.cnt >= (float)P && !(r.dmin * cond_fallback >= r.dmax) &&
               r.dmin > min_pivot - LPA_PIVOT_FP32_ERR;
-  if (redo) r = solve<double, P>(m, min_pivot);
+  if (redo) r = solve<double, P, MOM, COEF>(m, min_pivot);
   return r;
 }
 
@@ -384,10 +410,12 @@ struct Anchor {
 
 // One window cell: offset D from the pixel's point, disc test, Eq. 8 weight times inverse
 // variance, moment update.
-template <int ORDER, class MOM>
-__device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R2, float cexp, float taper) {
+template <int ORDER, bool STEER, class MOM>
+__device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R2, float cexp, float taper,
+                                            float4 Q) {
   const float2 D2 = __fmul2_rn(D, D);
-  const float r2 = D2.x + D2.y;
+  // |d|^2, or d^T C d for the steered window (Section 5.4)
+  const float r2 = STEER ? fmaf(Q.x, D2.x, fmaf(Q.z, D2.y, 2.f * Q.y * (D.x * D.y))) : D2.x + D2.y;
   const bool in = r2 < R2 && fv.y > 0.f;
   if constexpr (ORDER == 0) {
     // four sums: cheaper to add exact zeros for cells outside the window than to branch
@@ -403,32 +431,47 @@ __device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R
 
 // The n cells of one row: cell q is at D = DR + q S2. (Fully unrolled rows dispatched on n were
 // measured slower.)
-template <int ORDER, class MOM>
+template <int ORDER, bool STEER, class MOM>
 __device__ __forceinline__ void row_cells(MOM &m, const float2 *rowp, int n, float2 DR, float2 S2, float R2,
-                                          float cexp, float taper) {
+                                          float cexp, float taper, float4 Q) {
   float qf = 0.f;
   // two samples in flight pay off only for the long order-2 bodies
   constexpr int kUnroll = ORDER == 2 ? 2 : 1;
 #pragma unroll kUnroll
   for (int q = 0; q < n; q++, qf += 1.f)
-    window_cell<ORDER>(m, __ffma2_rn(make_float2(qf, qf), S2, DR), rowp[q], R2, cexp, taper);
+    window_cell<ORDER, STEER>(m, __ffma2_rn(make_float2(qf, qf), S2, DR), rowp[q], R2, cexp, taper, Q);
 }
 
-template <int ORDER, bool COMP>
+template <int ORDER, bool COMP, bool STEER = false>
 __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COMP>::type &m, const LpaSensorK &S,
                                                   const Anchor &an, int du, int dv, int c, float R, float R2,
                                                   float cexp, float taper, int x0, int y0,
-                                                  const unsigned char *smem, bool active, unsigned *status) {
+                                                  const unsigned char *smem, bool active, unsigned *status,
+                                                  float4 Q = make_float4(1.f, 0.f, 1.f, 0.f)) {
   // the pixel's point in sensor s: anchor (FP64 at the 8x8 block corner) + small FP32 step
   float px = an.fx + (float)du * S.Gf[0] + (float)dv * S.Gf[1];
   float py = an.fy + (float)du * S.Gf[2] + (float)dv * S.Gf[3];
   float flx = floorf(px), fly = floorf(py);
   const int ix = an.ix + (int)flx, iy = an.iy + (int)fly;
   const float fx = px - flx, fy = py - fly;
-  const float hx = R * S.hx_unit + 1e-3f, hy = R * S.hy_unit + 1e-3f;
   const int PW = S.box_w >> 1, PH = S.box_h >> 1;
   const float2 *planes = reinterpret_cast<const float2 *>(smem + S.off_planes);
   const float a00 = S.A[0], a01 = S.A[1], a10 = S.A[2], a11 = S.A[3];
+  float hx, hy;
+  if constexpr (STEER) {
+    // sensor-space bounding box of the support D^T B D < R^2, B = A^T C A (d = A D)
+    const float t00 = fmaf(Q.x, a00, Q.y * a10), t01 = fmaf(Q.x, a01, Q.y * a11);
+    const float t10 = fmaf(Q.y, a00, Q.z * a10), t11 = fmaf(Q.y, a01, Q.z * a11);
+    const float bxx = fmaf(a00, t00, a10 * t10), bxy = fmaf(a00, t01, a10 * t11), byy = fmaf(a01, t01, a11 * t11);
+    const float rdet = 1.f / fmaf(bxx, byy, -bxy * bxy);
+    // at most the staged box: a matrix below the planned eigenvalue bound (or not positive
+    // definite) cannot make the traversal long; cells outside the box are reported as usual
+    hx = fminf(R * sqrtf(byy * rdet) + 1e-3f, (float)S.box_w);
+    hy = fminf(R * sqrtf(bxx * rdet) + 1e-3f, (float)S.box_h);
+  } else {
+    hx = R * S.hx_unit + 1e-3f;
+    hy = R * S.hy_unit + 1e-3f;
+  }
   const float sx = 2.f * a00, sy = 2.f * a10;
   // colour phases of channel c: R (0,0); G (1,0) and (0,1); B (1,1)
   const int nsub = (c == 1) ? 2 : 1;
@@ -449,11 +492,15 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
     if (NI == 0 || NJ == 0) continue;
     const int pc0 = ((bxe - x0) >> 1) + ilo;
     const int pr0 = ((bye - y0) >> 1) + jlo;
-    const bool colok = pc0 >= 0 && pc0 + NI <= PW;
+    // isotropic windows: every lane walks the warp's longest row (the staged box leaves room for
+    // it). Steered windows differ in size and shape within a warp: each lane walks its own rows.
+    const int nw = STEER ? ni : NI;
+    const bool colok = pc0 >= 0 && pc0 + nw <= PW;
     const float2 *pl = planes + (ox + 2 * oy) * (PH * PW);
     const float Dx0 = 2.f * (float)ilo - rx;
 #pragma unroll 1
     for (int r = 0; r < NJ; r++) {
+      if (STEER && r >= nj) break;
       const int pr = pr0 + r;
       if (!(colok && pr >= 0 && pr < PH)) {
         if (active && r < nj) atomicOr(status, LPA_ERR_BOUNDS);
@@ -464,7 +511,7 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
       const float2 DR = make_float2(dxr, dyr);
       const float2 *rowp = pl + pr * PW + pc0;
       const float2 S2 = make_float2(sx, sy);
-      row_cells<ORDER>(m, rowp, NI, DR, S2, R2, cexp, taper);
+      row_cells<ORDER, STEER>(m, rowp, nw, DR, S2, R2, cexp, taper, Q);
     }
   }
 }
@@ -528,7 +575,7 @@ __device__ __forceinline__ T reread(const T &x) {
 // global descriptor, whose tensor maps the bulk copies use (otherwise `maps` is &L).
 // `phase` is the parity of the CTA's mbarrier use for this tile. Returns false when the CTA must
 // stop (a bounded wait ran out here or in another CTA).
-template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS, bool TAB = false>
+template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS, int MODE = LPA_SEARCHED>
 __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch *maps, int tile, unsigned char *smem, uint64_t *mbar,
                                              uint32_t phase, int *fp_x0, int *fp_y0,
                                              Anchor (*anchors)[LPA_MAX_SENSORS]) {
@@ -655,8 +702,13 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   const size_t opix = (size_t)v * RD(L.out_w) + u;
   const float log2e = 1.4426950408889634f;
 
+  constexpr bool TAB = MODE == LPA_TABULATED, STEER = MODE == LPA_STEERED, GRAD = MODE == LPA_GRADIENTS;
+  float4 Q = make_float4(1.f, 0.f, 1.f, 0.f);  // steering matrix of this pixel (Section 5.4)
+  if constexpr (STEER)
+    if (pix) Q = make_float4(L.aux[opix * 3], L.aux[opix * 3 + 1], L.aux[opix * 3 + 2], 0.f);
+
 #pragma unroll 1
-  for (int c = 0; c < 3; c++) {
+  for (int c = GRAD ? 1 : 0; c < (GRAD ? 2 : 3); c++) {  // the gradient pass fits the green channel only
     Ici ici;
     ici.reset(pix);
     typename MomentsSel<ORDER, COMP>::type m;
@@ -674,10 +726,17 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
         if constexpr (TAB)
           accumulate_table<ORDER>(m, L, s, c, j, u, v, fp_x0[s], fp_y0[s], smem, act, L.status);
         else
-          accumulate_sensor<ORDER, COMP>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, RD(L.taper), fp_x0[s],
-                                         fp_y0[s], smem, act, RD(L.status));
+          accumulate_sensor<ORDER, COMP, STEER>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, RD(L.taper),
+                                                fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q);
       }
-      FitOut f = solve_with_fallback<P>(m, RD(L.min_pivot), RD(L.cond_fallback));
+      FitOut f = solve_with_fallback<P, decltype(m), GRAD>(m, RD(L.min_pivot), RD(L.cond_fallback));
+      if constexpr (GRAD) {  // Section 5.4: the order-1 fit's linear coefficients; 0 if not usable
+        if (pix) {
+          L.aux[opix * 2] = f.valid ? f.c1 : 0.f;
+          L.aux[opix * 2 + 1] = f.valid ? f.c2 : 0.f;
+        }
+        break;
+      }
       if (DIAG && pix) {
         float *o = L.levels + (((size_t)c * NL + j) * plane_px + opix) * 2;
         o[0] = f.valid ? f.c0 : __int_as_float(0x7fffffff);
@@ -685,6 +744,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
       }
       ici.step(f, j, RD(L.ici_gamma));
     }
+    if constexpr (GRAD) continue;
     // order fallback at the largest scale (the moments still hold it when any lane needs it)
     const bool need = ici.choice == 255 && pix;
     if (DIAG || __any_sync(LPA_FULL, need)) {
@@ -715,14 +775,14 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
 }
 
 // Single frame: one CTA per tile (tiles tile0 .. tile0 + gridDim.x - 1).
-template <int ORDER, bool COMP, bool DIAG, int TH, bool TAB = false>
+template <int ORDER, bool COMP, bool DIAG, int TH, int MODE = LPA_SEARCHED>
 __global__ void __launch_bounds__(LPA_TILE *TH, 16 / TH * 2) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
   __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
   __shared__ __align__(8) uint64_t mbar;
   if (threadIdx.x == 0) mbar_init(&mbar, 1);
-  process_tile<ORDER, COMP, DIAG, TH, false, TAB>(L, &L, L.tile0 + blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0, anchors);
+  process_tile<ORDER, COMP, DIAG, TH, false, MODE>(L, &L, L.tile0 + blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0, anchors);
 }
 
 // Resident CTAs per SM the persistent kernel is compiled for (register cap 64K / (threads x this)):

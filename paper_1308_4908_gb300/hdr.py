@@ -42,6 +42,12 @@ class hdr_params(ctypes.Structure):
                 ("tab_weights", ctypes.c_int32)]
 
 
+class hdr_calpa_params(ctypes.Structure):
+    _fields_ = [("grad_sigma", ctypes.c_double), ("window_sigma", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("lambda1", ctypes.c_double), ("lambda2", ctypes.c_double), ("min_eig", ctypes.c_double),
+                ("max_eig", ctypes.c_double)]
+
+
 class hdr_frame(ctypes.Structure):
     _fields_ = [("rig_id", ctypes.c_int32), ("params", ctypes.c_void_p),
                 ("raw_dev", ctypes.c_void_p * HDR_MAX_SENSORS), ("out_dev", ctypes.c_void_p),
@@ -127,12 +133,19 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.hdr_server_stats_get.argtypes = [_P, _P]
     lib.hdr_server_destroy.argtypes = [_P]
     lib.hdr_server_destroy.restype = None
+    lib.hdr_calpa_params_default.argtypes = [_P]
+    lib.hdr_calpa_params_default.restype = None
+    lib.hdr_calpa_gradients.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
+    lib.hdr_calpa_metric.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]
+    lib.hdr_reconstruct_steered.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P]
+    lib.hdr_reconstruct_adaptive.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
     lib.hdr_last_error.argtypes = []
     lib.hdr_last_error.restype = ctypes.c_char_p
     for name in ("hdr_create", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_levels", "hdr_reconstruct_host",
                  "hdr_check", "hdr_reconstruct_noalloc", "hdr_reconstruct_batch", "hdr_tune_batch",
                  "hdr_server_create", "hdr_submit", "hdr_poll", "hdr_server_stats_get", "hdr_selftest_timeout",
-                 "hdr_calib_stack_stats", "hdr_calib_gain", "hdr_calib_exposure"):
+                 "hdr_calib_stack_stats", "hdr_calib_gain", "hdr_calib_exposure", "hdr_calpa_gradients",
+                 "hdr_calpa_metric", "hdr_reconstruct_steered", "hdr_reconstruct_adaptive"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -229,6 +242,44 @@ def hdr_calib_exposure(ctx: int, flat_mean: int, black_mean: int, gain: float, e
                                      int(height), float(min_signal), float(max_level), ctypes.byref(nd),
                                      ctypes.c_void_p(prnu_dev), ctypes.byref(n), ctypes.c_void_p(stream)))
     return nd.value, n.value
+
+
+def hdr_calpa_params_default(**over) -> hdr_calpa_params:
+    """Defaults of the adaptive reconstruction (Sections 5.4-5.5), with keyword overrides."""
+    c = hdr_calpa_params()
+    load().hdr_calpa_params_default(ctypes.byref(c))
+    for k, v in over.items():
+        setattr(c, k, float(v))
+    return c
+
+
+def hdr_calpa_gradients(ctx: int, rig_id: int, params: hdr_params, calpa: hdr_calpa_params, raw_dev: Sequence[int],
+                        grad_dev: int, stream: Optional[int] = None) -> None:
+    _check(load().hdr_calpa_gradients(ctypes.c_void_p(ctx), int(rig_id), ctypes.byref(params), ctypes.byref(calpa),
+                                      _ptr_array(raw_dev), ctypes.c_void_p(grad_dev), ctypes.c_void_p(stream)))
+
+
+def hdr_calpa_metric(ctx: int, out_w: int, out_h: int, calpa: hdr_calpa_params, grad_dev: int, metric_dev: int,
+                     stream: Optional[int] = None) -> None:
+    _check(load().hdr_calpa_metric(ctypes.c_void_p(ctx), int(out_w), int(out_h), ctypes.byref(calpa),
+                                   ctypes.c_void_p(grad_dev), ctypes.c_void_p(metric_dev), ctypes.c_void_p(stream)))
+
+
+def hdr_reconstruct_steered(ctx: int, rig_id: int, params: hdr_params, calpa: hdr_calpa_params,
+                            raw_dev: Sequence[int], metric_dev: int, out_dev: int, choice_dev: Optional[int] = None,
+                            stream: Optional[int] = None) -> None:
+    _check(load().hdr_reconstruct_steered(ctypes.c_void_p(ctx), int(rig_id), ctypes.byref(params),
+                                          ctypes.byref(calpa), _ptr_array(raw_dev), ctypes.c_void_p(metric_dev),
+                                          ctypes.c_void_p(out_dev), ctypes.c_void_p(choice_dev),
+                                          ctypes.c_void_p(stream)))
+
+
+def hdr_reconstruct_adaptive(ctx: int, rig_id: int, params: hdr_params, calpa: hdr_calpa_params,
+                             raw_dev: Sequence[int], out_dev: int, choice_dev: Optional[int] = None,
+                             stream: Optional[int] = None) -> None:
+    _check(load().hdr_reconstruct_adaptive(ctypes.c_void_p(ctx), int(rig_id), ctypes.byref(params),
+                                           ctypes.byref(calpa), _ptr_array(raw_dev), ctypes.c_void_p(out_dev),
+                                           ctypes.c_void_p(choice_dev), ctypes.c_void_p(stream)))
 
 
 def hdr_last_error() -> str:
@@ -420,6 +471,51 @@ class Context:
 
     def selftest_timeout(self, stream=None):
         hdr_selftest_timeout(self.handle, self._stream(stream))
+
+    # ---------------------------------------------------------------- adaptive windows (Sections 5.4-5.5)
+    def calpa_gradients(self, rig_id: int, params, calpa: hdr_calpa_params, raws, grad=None, stream=None):
+        """Pass 1: float32 [out_h, out_w, 2] gradients of the order-1 green fit."""
+        import torch
+        hp = params if isinstance(params, hdr_params) else params_struct(params)
+        if grad is None:
+            grad = torch.empty((hp.out_h, hp.out_w, 2), dtype=torch.float32, device=f"cuda:{self.device}")
+        hdr_calpa_gradients(self.handle, rig_id, hp, calpa, [int(r.data_ptr()) for r in raws], grad.data_ptr(),
+                            self._stream(stream))
+        return grad
+
+    def calpa_metric(self, calpa: hdr_calpa_params, grad, metric=None, stream=None):
+        """Pass 2: float32 [out_h, out_w, 3] steering matrices (C11, C12, C22) from `grad`."""
+        import torch
+        h, w = grad.shape[:2]
+        if metric is None:
+            metric = torch.empty((h, w, 3), dtype=torch.float32, device=grad.device)
+        hdr_calpa_metric(self.handle, w, h, calpa, grad.data_ptr(), metric.data_ptr(), self._stream(stream))
+        return metric
+
+    def reconstruct_steered(self, rig_id: int, params, calpa: hdr_calpa_params, raws, metric, out=None, choice=None,
+                            stream=None):
+        """Pass 3: the reconstruction with the steered window of `metric`; returns `out`."""
+        import torch
+        hp = params if isinstance(params, hdr_params) else params_struct(params)
+        if out is None:
+            dt = torch.float16 if hp.out_dtype == 1 else torch.float32
+            out = torch.empty((3, hp.out_h, hp.out_w), dtype=dt, device=f"cuda:{self.device}")
+        hdr_reconstruct_steered(self.handle, rig_id, hp, calpa, [int(r.data_ptr()) for r in raws],
+                                metric.data_ptr(), out.data_ptr(), choice.data_ptr() if choice is not None else None,
+                                self._stream(stream))
+        return out
+
+    def reconstruct_adaptive(self, rig_id: int, params, calpa: hdr_calpa_params, raws, out=None, choice=None,
+                             stream=None):
+        """The three passes in one call (scratch owned by the context); returns `out`."""
+        import torch
+        hp = params if isinstance(params, hdr_params) else params_struct(params)
+        if out is None:
+            dt = torch.float16 if hp.out_dtype == 1 else torch.float32
+            out = torch.empty((3, hp.out_h, hp.out_w), dtype=dt, device=f"cuda:{self.device}")
+        hdr_reconstruct_adaptive(self.handle, rig_id, hp, calpa, [int(r.data_ptr()) for r in raws], out.data_ptr(),
+                                 choice.data_ptr() if choice is not None else None, self._stream(stream))
+        return out
 
     # ---------------------------------------------------------------- calibration (Section 6.2)
     def calib_stack_stats(self, frames, width: int, stream=None):

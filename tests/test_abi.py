@@ -33,7 +33,8 @@ def test_header_declares_the_boundary():
     for n in ("hdr_create", "hdr_destroy", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_host",
               "hdr_check", "hdr_last_error", "hdr_params_default", "hdr_reconstruct_levels",
               "hdr_reconstruct_batch", "hdr_tune_batch", "hdr_server_create", "hdr_submit", "hdr_poll",
-              "hdr_server_stats_get", "hdr_server_destroy"):
+              "hdr_server_stats_get", "hdr_server_destroy", "hdr_calpa_gradients", "hdr_calpa_metric",
+              "hdr_reconstruct_steered", "hdr_reconstruct_adaptive"):
         assert n in names
 
 
@@ -48,7 +49,7 @@ def test_binding_uses_the_c_names(lib):
 
 
 STRUCTS = ("hdr_sensor_desc", "hdr_params", "hdr_frame", "hdr_batch_config", "hdr_server_config", "hdr_request",
-           "hdr_result", "hdr_server_stats")
+           "hdr_result", "hdr_server_stats", "hdr_calpa_params")
 
 
 def test_struct_layout_matches_the_header(tmp_path):
@@ -81,6 +82,9 @@ def test_defaults_without_a_gpu(lib):
     assert [p.sigma[i] for i in range(4)] == [0.5, 0.8, 1.2, 1.8]
     assert abs(p.green_ratio - 2 ** -0.5) < 1e-15 and p.trunc_k == 3.0 and p.ici_gamma == 2.0
     assert p.min_pivot == 1e-3 and p.cond_fallback == 1e6
+    c = hdr.hdr_calpa_params_default()
+    assert (c.grad_sigma, c.window_sigma, c.alpha, c.lambda1, c.lambda2, c.min_eig, c.max_eig) == \
+        (1.2, 1.0, 0.5, 1.0, 1e-3, 0.25, 16.0)
 
 
 def test_create_fails_loudly_without_a_device(lib):
