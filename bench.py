@@ -24,6 +24,7 @@ import subprocess
 import sys
 import threading
 import time
+from typing import Optional
 
 import numpy as np
 
@@ -64,19 +65,23 @@ def expected_pairs(params, sensors):
     return out
 
 
-def algorithmic_flops(params, sensors, choice: np.ndarray) -> float:
+def algorithmic_flops(params, sensors, choice: np.ndarray, area: Optional[np.ndarray] = None,
+                      per_pair: Optional[int] = None) -> float:
     """FP32 flops the method needs for one frame: per pixel and channel every scale up to the
     one at which the confidence-interval rule stops (the chosen scale and the next), times the
-    per-pair count of the order (moment FMAs, monomials, weights)."""
+    per-pair count of the order (moment FMAs, monomials, weights). `area` ([H, W], optional)
+    scales each pixel's window area (the steered window of Section 5.4 covers 1 / sqrt(det C)
+    times the disc)."""
     J = len(params.sigmas)
     pairs = expected_pairs(params, sensors)             # [3, J]
     cum = np.cumsum(pairs, axis=1)                      # pairs up to scale j
+    a = None if area is None else np.asarray(area, dtype=np.float64).ravel()
     total = 0.0
     for c in range(3):
         ch = choice[c].astype(np.int64).ravel()
         stop = np.where((ch >= 0) & (ch < J - 1), ch + 1, J - 1)   # scale index reached
-        total += cum[c][stop].sum()
-    return total * FLOPS_PER_PAIR[params.order]
+        total += cum[c][stop].sum() if a is None else (cum[c][stop] * a).sum()
+    return total * (FLOPS_PER_PAIR[params.order] if per_pair is None else per_pair)
 
 
 class ClockSampler:
@@ -619,6 +624,104 @@ def run_calib_study(args):
                                        "kind": "oracle (numpy, one thread)"}}), flush=True)
 
 
+def run_calpa_study(args):
+    """Adaptive windows (CALPA, Sections 5.4-5.5) on the paper-scale frame: GPU time of the three
+    passes, of the one-call entry point and of the isotropic reconstruction (L2 flushed between
+    repetitions); the steered pass against the FP32 roofline (its window covers 1 / sqrt(det C)
+    times the disc, and the quadratic form adds 5 flops per pair); error against the oracle on
+    sampled pixels; and the log10 error of both reconstructions against the scene's radiance, within
+    3 px of an edge and elsewhere. One JSON line."""
+    import torch
+    import oracle
+    from paper_1308_4908_gb300 import hdr, synth
+    oracle.build()
+    fr = synth.paper_scale(size=args.size)
+    p = fr.params
+    c = hdr.hdr_calpa_params_default()
+    ctx = hdr.Context(0)
+    ctx.set_rig(0, fr.sensors)
+    raws = [torch.from_numpy(s.raw).cuda() for s in fr.sensors]
+    ch_iso = torch.empty((3, p.out_h, p.out_w), dtype=torch.uint8, device="cuda")
+    ch_ada = torch.empty_like(ch_iso)
+    iso = ctx.reconstruct(0, p, raws, choice=ch_iso)
+    g = ctx.calpa_gradients(0, p, c, raws)
+    q = ctx.calpa_metric(c, g)
+    ada = ctx.reconstruct_steered(0, p, c, raws, q, choice=ch_ada)
+    torch.cuda.synchronize()
+    ctx.check()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def timed(fn, reps=10):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        fn()
+        for k in range(reps):
+            flush.fill_(k)
+            ev[k][0].record(st)
+            fn()
+            ev[k][1].record(st)
+        torch.cuda.synchronize()
+        ctx.check()
+        return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+    ms = {"isotropic": timed(lambda: ctx.reconstruct(0, p, raws, out=iso)),
+          "pass1_gradients": timed(lambda: ctx.calpa_gradients(0, p, c, raws, grad=g)),
+          "pass2_metric": timed(lambda: ctx.calpa_metric(c, g, metric=q)),
+          "pass3_steered": timed(lambda: ctx.reconstruct_steered(0, p, c, raws, q, out=ada)),
+          "adaptive_one_call": timed(lambda: ctx.reconstruct_adaptive(0, p, c, raws, out=ada))}
+    qn = q.cpu().numpy().astype(np.float64)
+    area = 1.0 / np.sqrt(np.maximum(qn[..., 0] * qn[..., 2] - qn[..., 1] ** 2, 1e-12))
+    flops = algorithmic_flops(p, fr.sensors, ch_ada.cpu().numpy(), area=area, per_pair=FLOPS_PER_PAIR[p.order] + 5)
+    pk = peaks()
+    tf = flops / (ms["pass3_steered"] * 1e-3) / 1e12
+    peak = fp32_peak_tflops(pk)
+    # parity on sampled pixels (the oracle with the GPU's steering matrices)
+    r = np.random.default_rng(1008)
+    pix = np.stack([r.integers(0, p.out_w, 1000), r.integers(0, p.out_h, 1000)], axis=1)
+    o = oracle.reconstruct(fr.sensors, p, pix, metric=qn)
+    gv = ada.cpu().numpy()
+    gs = gv[:, pix[:, 1], pix[:, 0]].T
+    ok = np.isfinite(o["out"]) & np.isfinite(gs)
+    rel = np.abs(gs - o["out"])[ok] / np.maximum(np.abs(o["out"][ok]), 1e-2)
+    # error against the scene (point-sampled radiance at each output pixel's reference point)
+    vv, uu = np.mgrid[0:p.out_h, 0:p.out_w]
+    A = np.asarray(p.out_affine, dtype=np.float64).reshape(2, 3)
+    X = A[0, 0] * uu + A[0, 1] * vv + A[0, 2]
+    Y = A[1, 0] * uu + A[1, 1] * vv + A[1, 2]
+    sc = fr.scene
+    dist = np.full(X.shape, np.inf)
+    for px, py, ang, _ in sc.edges:
+        dist = np.minimum(dist, np.abs(np.cos(ang) * (X - px * sc.width) + np.sin(ang) * (Y - py * sc.height)))
+    near = dist < 3.0
+    iv = iso.cpu().numpy()
+    quality = {}
+    for name, out in (("isotropic", iv), ("adaptive", gv)):
+        row = {}
+        for region, mask in (("edges", near), ("elsewhere", ~near)):
+            errs = []
+            for ch in range(3):
+                truth = sc.log_radiance(ch, X[mask], Y[mask])
+                val = out[ch][mask]
+                good = np.isfinite(val) & (val > 0)
+                errs.append(np.abs(np.log10(val[good]) - truth[good]))
+            e = np.concatenate(errs)
+            row[region] = {"median": round(float(np.median(e)), 5), "p90": round(float(np.quantile(e, 0.9)), 5)}
+        quality[name] = row
+    ctx.close()
+    print(json.dumps({"study": "adaptive windows (CALPA)", "workload": WORKLOAD,
+                      "calpa": {k: getattr(c, k) for k, _ in c._fields_},
+                      "ms": {k: round(v, 3) for k, v in ms.items()},
+                      "mpx_s": {"isotropic": round(p.out_w * p.out_h / ms["isotropic"] / 1e3, 1),
+                                "adaptive_one_call": round(p.out_w * p.out_h / ms["adaptive_one_call"] / 1e3, 1)},
+                      "mean_window_area_factor": round(float(area.mean()), 3),
+                      "roofline_pass3": {"bound": "alu", "achieved": round(tf, 2), "peak": round(peak, 1),
+                                         "unit": "TFLOP/s", "frac": round(tf / peak, 3)},
+                      "vs_oracle": {"pixels": int(ok.sum()), "max_rel_err": float(rel.max()),
+                                    "median_rel_err": float(np.median(rel))},
+                      "abs_log10_error_vs_scene": quality,
+                      "l2": "flushed between timed repetitions"}), flush=True)
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
@@ -749,7 +852,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--size", type=int, default=2048, help="raw and output edge (2048 = the paper-scale workload)")
     ap.add_argument("--headline-only", action="store_true", help="skip the batching and serving measurements")
-    ap.add_argument("--study", choices=["precision", "tiny", "tabweights", "calib"], default=None,
+    ap.add_argument("--study", choices=["precision", "tiny", "tabweights", "calib", "calpa"], default=None,
                     help="print a study instead of the bench line")
     ap.add_argument("--study-pixels", type=int, default=20000)
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson arrival schedule")
@@ -766,6 +869,9 @@ def main():
         return
     if args.study == "calib":
         run_calib_study(args)
+        return
+    if args.study == "calpa":
+        run_calpa_study(args)
         return
     world, rank, local, pg = dist_setup(args)
     try:

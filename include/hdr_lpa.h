@@ -319,11 +319,11 @@ hdr_status hdr_calib_exposure(hdr_ctx *ctx, const float *flat_mean, const float 
 typedef struct {
   double grad_sigma;   /* R/B scale of the pass-1 gradient fit (G uses green_ratio times it) */
   double window_sigma; /* Gaussian scale of pass 2, in output pixels; 3 window_sigma <= 10   */
-  double alpha;        /* structure sensitivity, >= 0 (0: gamma = 1)                          */
-  double lambda1;      /* elongation regulariser, > 0                                         */
-  double lambda2;      /* scaling regulariser, > 0                                            */
-  double min_eig;      /* clamp of C's eigenvalues, 0 < min_eig <= max_eig; the staged window */
-  double max_eig;      /*   footprint grows by 1 / sqrt(min_eig)                              */
+  double alpha;        /* structure sensitivity in [0, 4] (0: gamma = 1)                      */
+  double lambda1;      /* elongation regulariser in [1e-6, 1e6]                               */
+  double lambda2;      /* scaling regulariser in [1e-12, 1e12]                                */
+  double min_eig;      /* clamp of C's eigenvalues, 1e-6 <= min_eig <= max_eig <= 1e6; the   */
+  double max_eig;      /*   staged window footprint grows by 1 / sqrt(min_eig)                */
 } hdr_calpa_params;
 
 /* Defaults: grad_sigma 1.2, window_sigma 1, alpha 0.5, lambda1 1, lambda2 1e-3, eigenvalues
@@ -339,7 +339,9 @@ hdr_status hdr_calpa_gradients(hdr_ctx *ctx, int32_t rig_id, const hdr_params *p
                                const uint16_t *const *raw_dev, float *grad_dev, void *cuda_stream);
 
 /* Pass 2. grad_dev as pass 1 writes it; metric_dev: device [out_h][out_w][3] float32 = C11, C12,
- * C22. The structure tensor is summed and decomposed in FP64. Asynchronous on `cuda_stream`. */
+ * C22. The structure tensor is summed and its eigenvalues formed in FP64 (the small one of a
+ * straight edge is a difference of large sums); the rest runs in FP32, so gradients up to about
+ * 1e18 in magnitude are supported. Asynchronous on `cuda_stream`. */
 hdr_status hdr_calpa_metric(hdr_ctx *ctx, int32_t out_w, int32_t out_h, const hdr_calpa_params *calpa,
                             const float *grad_dev, float *metric_dev, void *cuda_stream);
 

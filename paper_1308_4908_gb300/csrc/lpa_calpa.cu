@@ -21,23 +21,30 @@ struct MetricArgs {
   int W, H, r;
   int rw[2 * kRmax + 1];           // half width of the disc in row offset dj (|di| <= rw)
   double w[2 * kRmax * kRmax + 1];  // Gaussian weight by di^2 + dj^2
-  double alpha, lambda1, lambda2, min_eig, max_eig;
+  float alpha, lambda1, lambda2, min_eig, max_eig;
 };
 
-__device__ __forceinline__ double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
-
 // One thread per output pixel. The gradients of the block and its halo are staged in shared
-// memory; T = sum_i w_i g_i g_i^T over the disc is summed in FP64 (T of a straight edge is nearly
-// rank one, and its small eigenvalue is the difference of large sums), then decomposed in closed
-// form: l1,2 = h +- sqrt(((a - c) / 2)^2 + b^2), s = sqrt(l), u1 the eigenvector of l1.
+// memory as the FP64 products gx^2, gx gy, gy^2 (exact: products of two FP32 values), so each
+// neighbour costs three FP64 FMAs. T = sum_i w_i g_i g_i^T over the disc is summed in FP64: T of
+// a straight edge is nearly rank one, and its small eigenvalue is the difference of large sums.
+// The eigenvalues l1,2 = h +- sqrt(((a - c) / 2)^2 + b^2) and the components of the eigenvector
+// of l1 ((b, l1 - a) or (l1 - c, b), the longer) are formed in FP64 too; what follows them (square
+// roots, the direction's normalisation, elongation, the power and the matrix) has no cancellation
+// and runs in FP32.
 __global__ void __launch_bounds__(kBX *kBY) calpa_metric(const __grid_constant__ MetricArgs A) {
-  __shared__ float2 tile[(kBY + 2 * kRmax) * (kBX + 2 * kRmax)];
+  constexpr int kTile = (kBY + 2 * kRmax) * (kBX + 2 * kRmax);
+  __shared__ double sxx[kTile], sxy[kTile], syy[kTile];
   const int r = A.r, TW = kBX + 2 * r, TH = kBY + 2 * r;
   const int bx0 = blockIdx.x * kBX, by0 = blockIdx.y * kBY;
   const int tid = threadIdx.y * kBX + threadIdx.x;
   for (int e = tid; e < TW * TH; e += kBX * kBY) {
     const int X = bx0 - r + e % TW, Y = by0 - r + e / TW;
-    tile[e] = (X >= 0 && X < A.W && Y >= 0 && Y < A.H) ? A.grad[(size_t)Y * A.W + X] : make_float2(0.f, 0.f);
+    const float2 g = (X >= 0 && X < A.W && Y >= 0 && Y < A.H) ? A.grad[(size_t)Y * A.W + X] : make_float2(0.f, 0.f);
+    const double gx = g.x, gy = g.y;
+    sxx[e] = gx * gx;
+    sxy[e] = gx * gy;
+    syy[e] = gy * gy;
   }
   __syncthreads();
   const int u = bx0 + threadIdx.x, v = by0 + threadIdx.y;
@@ -49,42 +56,44 @@ __global__ void __launch_bounds__(kBX *kBY) calpa_metric(const __grid_constant__
     if (vv < 0 || vv >= A.H) continue;
     const int rw = A.rw[dj + r];
     M += min(u + rw, A.W - 1) - max(u - rw, 0) + 1;  // disc cells of this row inside the image
-    const float2 *row = tile + (threadIdx.y + r + dj) * TW + threadIdx.x + r;
+    const int row = (threadIdx.y + r + dj) * TW + threadIdx.x + r;
     for (int di = -rw; di <= rw; di++) {
-      const float2 g = row[di];
       const double wt = A.w[di * di + dj * dj];
-      const double gx = g.x, gy = g.y, p = wt * gx;
-      a = fma(p, gx, a);
-      b = fma(p, gy, b);
-      c = fma(wt * gy, gy, c);
+      a = fma(wt, sxx[row + di], a);
+      b = fma(wt, sxy[row + di], b);
+      c = fma(wt, syy[row + di], c);
     }
   }
   const double h = 0.5 * (a + c), d = sqrt(0.25 * (a - c) * (a - c) + b * b);
   const double l1 = h + d, l2 = fmax(h - d, 0.0);
-  const double s1 = sqrt(l1), s2 = sqrt(l2);
-  // eigenvector of l1: (b, l1 - a) or (l1 - c, b), the longer; (1, 0) when T = 0
-  double ux = b, uy = l1 - a;
+  double vx = b, vy = l1 - a;
   const double fx = l1 - c, fy = b;
-  if (fx * fx + fy * fy > ux * ux + uy * uy) {
-    ux = fx;
-    uy = fy;
+  if (fx * fx + fy * fy > vx * vx + vy * vy) {
+    vx = fx;
+    vy = fy;
   }
-  const double nrm = sqrt(ux * ux + uy * uy);
-  if (nrm == 0.0) {
-    ux = 1.0;
-    uy = 0.0;
+  // the direction to FP32 with its exponent removed exactly (no underflow for tiny T)
+  int ex = 0;
+  frexp(fmax(fabs(vx), fabs(vy)), &ex);
+  float ux = (float)ldexp(vx, -ex), uy = (float)ldexp(vy, -ex);
+  const float n2 = ux * ux + uy * uy;
+  if (n2 == 0.f) {  // T = 0
+    ux = 1.f;
+    uy = 0.f;
   } else {
+    const float nrm = sqrtf(n2);
     ux /= nrm;
     uy /= nrm;
   }
-  const double elong = (s1 + A.lambda1) / (s2 + A.lambda1);
-  const double gamma = pow((s1 * s2 + A.lambda2) / (double)M, A.alpha);
-  const double ea = clampd(gamma * elong, A.min_eig, A.max_eig);  // along u1: across the edge
-  const double eb = clampd(gamma / elong, A.min_eig, A.max_eig);  // along u2: along the edge
+  const float s1 = sqrtf((float)l1), s2 = sqrtf((float)l2);
+  const float elong = (s1 + A.lambda1) / (s2 + A.lambda1);
+  const float gamma = powf((s1 * s2 + A.lambda2) / (float)M, A.alpha);
+  const float ea = fminf(fmaxf(gamma * elong, A.min_eig), A.max_eig);  // along u1: across the edge
+  const float eb = fminf(fmaxf(gamma / elong, A.min_eig), A.max_eig);  // along u2: along the edge
   float *o = A.metric + ((size_t)v * A.W + u) * 3;
-  o[0] = (float)(ea * ux * ux + eb * uy * uy);
-  o[1] = (float)((ea - eb) * ux * uy);
-  o[2] = (float)(ea * uy * uy + eb * ux * ux);
+  o[0] = ea * ux * ux + eb * uy * uy;
+  o[1] = (ea - eb) * ux * uy;
+  o[2] = ea * uy * uy + eb * ux * ux;
 }
 
 hdr_status check_calpa(const hdr_calpa_params *c) {
@@ -94,11 +103,12 @@ hdr_status check_calpa(const hdr_calpa_params *c) {
     return lpa_fail(HDR_E_INVALID, "grad_sigma must be finite and > 0");
   if (!(c->window_sigma > 0.0) || !(3.0 * c->window_sigma < kRmax + 1.0))
     return lpa_fail(HDR_E_INVALID, "window_sigma must be > 0 with 3 window_sigma < 11");
-  if (!(c->alpha >= 0.0) || !fin(c->alpha)) return lpa_fail(HDR_E_INVALID, "alpha must be finite and >= 0");
-  if (!(c->lambda1 > 0.0) || !(c->lambda2 > 0.0) || !fin(c->lambda1) || !fin(c->lambda2))
-    return lpa_fail(HDR_E_INVALID, "lambda1 and lambda2 must be finite and > 0");
-  if (!(c->min_eig > 0.0) || !(c->max_eig >= c->min_eig) || !fin(c->max_eig))
-    return lpa_fail(HDR_E_INVALID, "0 < min_eig <= max_eig < inf required");
+  // bounds keep every FP32 quantity of the matrix pass inside the normal range
+  if (!(c->alpha >= 0.0) || !(c->alpha <= 4.0)) return lpa_fail(HDR_E_INVALID, "alpha must be in [0, 4]");
+  if (!(c->lambda1 >= 1e-6 && c->lambda1 <= 1e6) || !(c->lambda2 >= 1e-12 && c->lambda2 <= 1e12))
+    return lpa_fail(HDR_E_INVALID, "lambda1 in [1e-6, 1e6] and lambda2 in [1e-12, 1e12] required");
+  if (!(c->min_eig >= 1e-6) || !(c->max_eig >= c->min_eig) || !(c->max_eig <= 1e6))
+    return lpa_fail(HDR_E_INVALID, "1e-6 <= min_eig <= max_eig <= 1e6 required");
   return HDR_OK;
 }
 
@@ -154,11 +164,11 @@ hdr_status hdr_calpa_metric(hdr_ctx *ctx, int32_t out_w, int32_t out_h, const hd
     A.rw[dj + A.r] = rw;
   }
   for (int k = 0; k <= 2 * A.r * A.r; k++) A.w[k] = std::exp(-(double)k / (2.0 * ws * ws));
-  A.alpha = calpa->alpha;
-  A.lambda1 = calpa->lambda1;
-  A.lambda2 = calpa->lambda2;
-  A.min_eig = calpa->min_eig;
-  A.max_eig = calpa->max_eig;
+  A.alpha = (float)calpa->alpha;
+  A.lambda1 = (float)calpa->lambda1;
+  A.lambda2 = (float)calpa->lambda2;
+  A.min_eig = (float)calpa->min_eig;
+  A.max_eig = (float)calpa->max_eig;
   calpa_metric<<<dim3((out_w + kBX - 1) / kBX, (out_h + kBY - 1) / kBY), dim3(kBX, kBY), 0,
                  (cudaStream_t)cuda_stream>>>(A);
   cudaError_t e = cudaGetLastError();

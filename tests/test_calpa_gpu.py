@@ -9,7 +9,10 @@ Tolerances. Pass 1: a gradient is a linear coefficient of one FP32 fit, so it ca
 rounding as C_0 does (tests/parity.py) with the coefficient's own rounding scales (the oracle
 reports them): |g - o| <= REL_TOL |o| + U32 (C_FIT efit + C_W ew); where the fit's smallest
 pivot lies within 2 % of min_pivot either usability decision is correct (0 or the gradient).
-Pass 2 is FP64 on both sides and rounded once to FP32: 4e-7 of the matrix's norm. Pass 3: the
+Pass 2 sums the structure tensor and forms its eigenvalues in FP64 like the oracle; the rest
+(square roots, normalisation, elongation, the power, the matrix) runs in FP32 with no
+cancellation: a few ulp on each eigenvalue of C and on its direction, together at most about 20
+U32 of the trace for alpha <= 1, so 32 U32 of the trace. Pass 3: the
 reconstruction tolerance of tests/parity.py (the window's FP32 quadratic form perturbs the weights
 by a few U32 relative, inside C_W).
 """
@@ -24,7 +27,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 PIVOT_BAND = 0.02
-Q_TOL = 4e-7
+Q_TOL = 32 * parity.U32
 
 
 @pytest.fixture(scope="module")
@@ -112,12 +115,12 @@ def test_pass2_metric(small_run):
     q_orc = oracle.steering_metric(g.astype(np.float64), c.window_sigma, c.alpha, c.lambda1, c.lambda2, c.min_eig,
                                    c.max_eig)
     check_metric(q, q_orc)
-    # eigenvalues inside the clamp, up to the FP32 rounding of the three entries (each moves the
-    # eigenvalues by at most its own rounding error)
+    # eigenvalues inside the clamp, up to FP32 rounding: the entries' own rounding and the unit
+    # direction's squared norm (1 within a few ulp) scale the clamped eigenvalues
     q64 = q.astype(np.float64)
     tr, det = q64[..., 0] + q64[..., 2], q64[..., 0] * q64[..., 2] - q64[..., 1] ** 2
     disc = np.sqrt(np.maximum(tr * tr / 4 - det, 0))
-    slack = 2 * parity.U32 * (np.abs(q64[..., 0]) + np.abs(q64[..., 2]) + 2 * np.abs(q64[..., 1]))
+    slack = 8 * parity.U32 * (np.abs(q64[..., 0]) + np.abs(q64[..., 2]) + 2 * np.abs(q64[..., 1]))
     assert np.all(tr / 2 - disc >= c.min_eig - slack) and np.all(tr / 2 + disc <= c.max_eig + slack)
 
 
