@@ -98,12 +98,21 @@ typedef struct {
                                  weights are tabulated once per frame and the kernel reads them
                                  instead of searching and evaluating each window. The fit is the
                                  same; only rounding differs. */
+  int32_t weight_mode;        /* noise weight of Eq. 6: 0 = K / s2, the inverse variance of the
+                                 Gaussian likelihood the paper derives it from (default); 1 = K / s
+                                 as printed in Section 5.2, for comparisons (Var C_0 then uses
+                                 w^2 s2 = K^2). weight_mode 1 is supported by hdr_reconstruct,
+                                 hdr_reconstruct_host and hdr_reconstruct_noalloc; the level maps,
+                                 batches, the serving loop and the adaptive passes reject it with
+                                 HDR_E_UNSUPPORTED. The paper's window exp(-|d|^2 / h) with
+                                 h_G = h_RB / sqrt 2 is sigma = sqrt(h / 2) with
+                                 green_ratio = 2^(-1/4). */
 } hdr_params;
 
 /* Fill *p with the defaults: order 2, scales {0.5, 0.8, 1.2, 1.8}, green_ratio 1/sqrt(2),
  * trunc_k 3, ici_gamma 2, min_pivot 1e-3, cond_fallback 1e6, identity output mapping,
- * float32 output, plain accumulation, tabulated weights allowed. out_w/out_h are set to 0 and
- * must be filled. */
+ * float32 output, plain accumulation, tabulated weights allowed, inverse-variance weight.
+ * out_w/out_h are set to 0 and must be filled. */
 void hdr_params_default(hdr_params *p);
 
 /* Create a context on CUDA device `device` (allocates its status word). */

@@ -57,12 +57,16 @@ def all_samples(sensors: Sequence) -> Dict[str, np.ndarray]:
 
 
 def fit_point(samples: Dict[str, np.ndarray], P, color: int, sigma_c: float, order: int,
-              trunc_k: float = 3.0, weight_mode: int = 0):
-    """C_0, Var C_0 and count for one channel at one (colour-adjusted) scale; C_0 is NaN if rank deficient."""
+              trunc_k: float = 3.0, weight_mode: int = 0, h_c: float = None):
+    """C_0, Var C_0 and count for one channel at one (colour-adjusted) scale; C_0 is NaN if rank deficient.
+
+    With `h_c` the window is the printed form of Eq. 8, exp(-|d|^2 / h_c), on |d|^2 < k^2 h_c / 2
+    (the same k-sigma support), and sigma_c is not used."""
     dx = samples["X"] - P[0]
     dy = samples["Y"] - P[1]
     r2 = dx * dx + dy * dy
-    sel = (samples["col"] == color) & (r2 < (trunc_k * sigma_c) ** 2)
+    support = (trunc_k * sigma_c) ** 2 if h_c is None else trunc_k ** 2 * h_c / 2.0
+    sel = (samples["col"] == color) & (r2 < support)
     dx, dy, r2 = dx[sel], dy[sel], r2[sel]
     f, s2 = samples["f"][sel], samples["s2"][sel]
     n = int(sel.sum())
@@ -72,7 +76,7 @@ def fit_point(samples: Dict[str, np.ndarray], P, color: int, sigma_c: float, ord
     if order >= 2:
         cols += [dx * dx, dx * dy, dy * dy]
     Phi = np.stack(cols, axis=1)
-    K = np.exp(-r2 / (2 * sigma_c ** 2)) - math.exp(-0.5 * trunc_k ** 2)
+    K = (np.exp(-r2 / (2 * sigma_c ** 2)) if h_c is None else np.exp(-r2 / h_c)) - math.exp(-0.5 * trunc_k ** 2)
     w = K / np.sqrt(s2) if weight_mode == 1 else K / s2
     p = Phi.shape[1]
     if n < p:

@@ -221,6 +221,7 @@ hdr_status check_params(const hdr_params *p) {
   if (p->out_dtype != 0 && p->out_dtype != 1) return fail(HDR_E_INVALID, "out_dtype must be 0 or 1");
   if (p->accum != 0 && p->accum != 1) return fail(HDR_E_INVALID, "accum must be 0 or 1");
   if (p->tab_weights != 0 && p->tab_weights != 1) return fail(HDR_E_INVALID, "tab_weights must be 0 or 1");
+  if (p->weight_mode != 0 && p->weight_mode != 1) return fail(HDR_E_INVALID, "weight_mode must be 0 or 1");
   return HDR_OK;
 }
 
@@ -430,6 +431,10 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
   CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, env.device));
   if ((int)off > max_smem - 1024)
     return fail(HDR_E_UNSUPPORTED, "staging needs %u bytes of shared memory (limit %d)", off, max_smem - 1024);
+  if (p->weight_mode == 1) {  // the printed noise weight K / s: searched window, its own kernel
+    L.mode = LPA_LITERAL;
+    return HDR_OK;
+  }
   return build_tables(env, rig, p, L);
 }
 
@@ -466,6 +471,8 @@ hdr_status reconstruct_impl(hdr_ctx *ctx, int32_t rig_id, const hdr_params *para
                             void *out_dev, uint8_t *choice_dev, float *levels_dev, void *stream) {
   hdr_status st = common_checks(ctx, rig_id, params, raw_dev, out_dev);
   if (st) return st;
+  if (levels_dev && params->weight_mode != 0)
+    return fail(HDR_E_UNSUPPORTED, "the level maps are computed with the inverse-variance weight (weight_mode 0)");
   LpaLaunch L;
   st = plan(ctx, ctx->rigs[rig_id], params, raw_dev, L);
   if (st) return st;
@@ -498,6 +505,7 @@ void hdr_params_default(hdr_params *p) {
   p->out_dtype = 0;
   p->accum = 0;
   p->tab_weights = 1;
+  p->weight_mode = 0;
 }
 
 hdr_status hdr_create(int device, hdr_ctx **out) {
@@ -792,6 +800,8 @@ hdr_status check_batch(hdr_ctx *ctx, int32_t n, const hdr_frame *frames) {
       return fail(HDR_E_INVALID, "frame %d: rig %d is not defined", f, F.rig_id);
     hdr_status st = check_params(F.params);
     if (st) return st;
+    if (F.params->weight_mode != 0)
+      return fail(HDR_E_UNSUPPORTED, "frame %d: batches use the inverse-variance weight (weight_mode 0)", f);
     if (F.params->accum != frames[0].params->accum)
       return fail(HDR_E_INVALID, "frame %d: all frames of a batch must use the same accum", f);
     if (!F.out_dev && (long long)F.params->out_w * F.params->out_h > 0)
@@ -1120,6 +1130,8 @@ hdr_status lpa_launch_mode(hdr_ctx *ctx, int32_t rig_id, const hdr_params *param
                            int mode, float *aux, double reach, void *out_dev, uint8_t *choice_dev, cudaStream_t st) {
   hdr_status s = common_checks(ctx, rig_id, params, raw_dev, mode == LPA_GRADIENTS ? aux : out_dev);
   if (s) return s;
+  if (params->weight_mode != 0)
+    return fail(HDR_E_UNSUPPORTED, "the adaptive passes use the inverse-variance weight (weight_mode 0)");
   hdr_params p = *params;
   p.tab_weights = 0;  // the window is searched: offsets or weights differ per pixel
   LpaLaunch L;

@@ -410,9 +410,13 @@ struct Anchor {
 
 // One window cell: offset D from the pixel's point, disc test, Eq. 8 weight times inverse
 // variance, moment update.
-template <int ORDER, bool STEER, class MOM>
+template <int ORDER, int MODE, class MOM>
 __device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R2, float cexp, float taper,
                                             float4 Q) {
+  constexpr bool STEER = MODE == LPA_STEERED;
+  // the variance sums take w^2 s2 = K w for the inverse-variance weight; with the printed weight
+  // K / s (fv.y = 1 / s) it is K^2
+  constexpr bool LIT = MODE == LPA_LITERAL;
   const float2 D2 = __fmul2_rn(D, D);
   // |d|^2, or d^T C d for the steered window (Section 5.4)
   const float r2 = STEER ? fmaf(Q.x, D2.x, fmaf(Q.z, D2.y, 2.f * Q.y * (D.x * D.y))) : D2.x + D2.y;
@@ -421,17 +425,17 @@ __device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R
     // four sums: cheaper to add exact zeros for cells outside the window than to branch
     const float K = ex2_approx(r2 * cexp) - taper;  // Eq. 8, truncated and tapered
     const float w = in ? K * fv.y : 0.f;            // window x inverse variance
-    m.add0(w, w * fv.x, w * K, in ? 1.f : 0.f);
+    m.add0(w, w * fv.x, (LIT ? (in ? K : 0.f) : w) * K, in ? 1.f : 0.f);
   } else if (in) {
     const float K = ex2_approx(r2 * cexp) - taper;
     const float w = K * fv.y;
-    m.add2(D, D2, w, w * fv.x, w * K);
+    m.add2(D, D2, w, w * fv.x, (LIT ? K : w) * K);
   }
 }
 
 // The n cells of one row: cell q is at D = DR + q S2. (Fully unrolled rows dispatched on n were
 // measured slower.)
-template <int ORDER, bool STEER, class MOM>
+template <int ORDER, int MODE, class MOM>
 __device__ __forceinline__ void row_cells(MOM &m, const float2 *rowp, int n, float2 DR, float2 S2, float R2,
                                           float cexp, float taper, float4 Q) {
   float qf = 0.f;
@@ -439,10 +443,10 @@ __device__ __forceinline__ void row_cells(MOM &m, const float2 *rowp, int n, flo
   constexpr int kUnroll = ORDER == 2 ? 2 : 1;
 #pragma unroll kUnroll
   for (int q = 0; q < n; q++, qf += 1.f)
-    window_cell<ORDER, STEER>(m, __ffma2_rn(make_float2(qf, qf), S2, DR), rowp[q], R2, cexp, taper, Q);
+    window_cell<ORDER, MODE>(m, __ffma2_rn(make_float2(qf, qf), S2, DR), rowp[q], R2, cexp, taper, Q);
 }
 
-template <int ORDER, bool COMP, bool STEER = false>
+template <int ORDER, bool COMP, int MODE = LPA_SEARCHED>
 __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COMP>::type &m, const LpaSensorK &S,
                                                   const Anchor &an, int du, int dv, int c, float R, float R2,
                                                   float cexp, float taper, int x0, int y0,
@@ -457,6 +461,7 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
   const int PW = S.box_w >> 1, PH = S.box_h >> 1;
   const float2 *planes = reinterpret_cast<const float2 *>(smem + S.off_planes);
   const float a00 = S.A[0], a01 = S.A[1], a10 = S.A[2], a11 = S.A[3];
+  constexpr bool STEER = MODE == LPA_STEERED;
   float hx, hy;
   if constexpr (STEER) {
     // sensor-space bounding box of the support D^T B D < R^2, B = A^T C A (d = A D)
@@ -511,7 +516,7 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
       const float2 DR = make_float2(dxr, dyr);
       const float2 *rowp = pl + pr * PW + pc0;
       const float2 S2 = make_float2(sx, sy);
-      row_cells<ORDER, STEER>(m, rowp, nw, DR, S2, R2, cexp, taper, Q);
+      row_cells<ORDER, MODE>(m, rowp, nw, DR, S2, R2, cexp, taper, Q);
     }
   }
 }
@@ -639,7 +644,9 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
     return false;
   }
 
-  // convert the staged raw values once per sample: Eq. 18 and the inverse of Eq. 20
+  // convert the staged raw values once per sample: Eq. 18 and the inverse of Eq. 20 (its square
+  // root for the printed weight K / s)
+  constexpr bool LIT = MODE == LPA_LITERAL;
   for (int s = 0; s < S; s++) {
     const LpaSensorK &Sk = L.s[s];
     const uint16_t *raw = reinterpret_cast<const uint16_t *>(smem + Sk.off_raw);
@@ -662,6 +669,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
             const float e0 = y - b0;
             f = e0 * inv_gtn;
             iv = __fdividef(gtn2, fmaf(gain, fmaxf(e0, 0.f), rv0));
+            if (LIT) iv = sqrtf(iv);
           }
         } else {
           const long px = (long)Y * W + X;
@@ -673,6 +681,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
             const float e0 = y - b;
             f = __fdividef(e0 * inv_gtn, a);
             iv = __fdividef(gtn2 * a * a, fmaf(gain, fmaxf(e0, 0.f), rv));
+            if (LIT) iv = sqrtf(iv);
           }
         }
       }
@@ -726,7 +735,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
         if constexpr (TAB)
           accumulate_table<ORDER>(m, L, s, c, j, u, v, fp_x0[s], fp_y0[s], smem, act, L.status);
         else
-          accumulate_sensor<ORDER, COMP, STEER>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, RD(L.taper),
+          accumulate_sensor<ORDER, COMP, MODE>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, RD(L.taper),
                                                 fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q);
       }
       FitOut f = solve_with_fallback<P, decltype(m), GRAD>(m, RD(L.min_pivot), RD(L.cond_fallback));

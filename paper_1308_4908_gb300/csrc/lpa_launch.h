@@ -67,14 +67,15 @@ struct LpaLaunch {
   // the pixel's even lattice cell.
   const int4 *tab_hdr;           // {first, count, (qx_min & 0xffff) | (qx_max << 16), same for qy}
   const float4 *tab_cells;
-  // Adaptive reconstruction (Sections 5.4-5.5): LPA_STEERED reads the steering matrix of each
-  // output pixel from aux ([out_h][out_w][3]: C11, C12, C22); LPA_GRADIENTS writes the gradient of
-  // the green fit to aux ([out_h][out_w][2]).
+  // Kernel mode (LPA_SEARCHED .. LPA_LITERAL below). Adaptive reconstruction (Sections 5.4-5.5):
+  // LPA_STEERED reads the steering matrix of each output pixel from aux ([out_h][out_w][3]: C11,
+  // C12, C22); LPA_GRADIENTS writes the gradient of the green fit to aux ([out_h][out_w][2]).
+  // LPA_LITERAL: the searched window with the noise weight printed in Eq. 6 (K / s, not K / s2).
   int mode;
   float *aux;
 };
 
-enum { LPA_SEARCHED = 0, LPA_TABULATED = 1, LPA_STEERED = 2, LPA_GRADIENTS = 3 };
+enum { LPA_SEARCHED = 0, LPA_TABULATED = 1, LPA_STEERED = 2, LPA_GRADIENTS = 3, LPA_LITERAL = 4 };
 
 // Several frames in one graph launch: the tile list is grouped by polynomial order and each
 // order's persistent kernel takes tiles from its own segment. The tile list, the segment bounds

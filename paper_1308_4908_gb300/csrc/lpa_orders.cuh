@@ -2,8 +2,8 @@
 // lpa_m0.cu, lpa_m1.cu and lpa_m2.cu, which compile in parallel).
 //
 // Instantiated per order: the searched window (Eq. 8) with and without the level maps, the
-// tabulated window (Section 8), tile heights 8 and 16; the steered window (Section 5.4) at tile
-// height 16; the gradient pass (Section 5.4) for order 1 only.
+// tabulated window (Section 8), tile heights 8 and 16; the steered window (Section 5.4) and the
+// printed noise weight K / s at tile height 16; the gradient pass (Section 5.4) for order 1 only.
 #pragma once
 #include "lpa_dispatch.h"
 #include "lpa_kernel.cuh"
@@ -13,7 +13,7 @@ namespace lpa_orders {
 template <int ORDER, int MODE, int TH>
 constexpr bool instantiated() {
   if (MODE == LPA_GRADIENTS) return ORDER == 1 && TH == 16;
-  if (MODE == LPA_STEERED) return TH == 16;
+  if (MODE == LPA_STEERED || MODE == LPA_LITERAL) return TH == 16;
   return true;
 }
 
@@ -30,6 +30,7 @@ const void *kernel_mode(int mode) {
     case LPA_TABULATED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_TABULATED>();
     case LPA_STEERED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED>();
     case LPA_GRADIENTS: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_GRADIENTS>();
+    case LPA_LITERAL: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_LITERAL>();
     default: return nullptr;
   }
 }

@@ -388,6 +388,8 @@ hdr_status hdr_submit(hdr_server *srv, const hdr_request *req, uint64_t *ticket)
   if (ns == 0) return lpa_fail(HDR_E_INVALID, "rig is not defined");
   hdr_status st = lpa_check_params(&req->params);
   if (st) return st;
+  if (req->params.weight_mode != 0)
+    return lpa_fail(HDR_E_UNSUPPORTED, "the serving loop uses the inverse-variance weight (weight_mode 0)");
   if (!req->out_host && (long long)req->params.out_w * req->params.out_h > 0)
     return lpa_fail(HDR_E_INVALID, "out_host is NULL");
   for (int s = 0; s < ns; s++)

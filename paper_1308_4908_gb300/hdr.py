@@ -39,7 +39,7 @@ class hdr_params(ctypes.Structure):
                 ("trunc_k", ctypes.c_double), ("ici_gamma", ctypes.c_double), ("min_pivot", ctypes.c_double),
                 ("cond_fallback", ctypes.c_double), ("out_w", ctypes.c_int32), ("out_h", ctypes.c_int32),
                 ("out_affine", ctypes.c_double * 6), ("out_dtype", ctypes.c_int32), ("accum", ctypes.c_int32),
-                ("tab_weights", ctypes.c_int32)]
+                ("tab_weights", ctypes.c_int32), ("weight_mode", ctypes.c_int32)]
 
 
 class hdr_calpa_params(ctypes.Structure):
@@ -386,6 +386,7 @@ def params_struct(p) -> hdr_params:
     h.out_dtype = int(getattr(p, "out_dtype", 0))
     h.accum = int(getattr(p, "accum", 0))
     h.tab_weights = int(getattr(p, "tab_weights", 1))
+    h.weight_mode = int(getattr(p, "weight_mode", 0))
     return h
 
 

@@ -204,6 +204,7 @@ class Params:
     out_dtype: int = 0        # 0 float32, 1 float16
     accum: int = 0            # 0 plain, 1 compensated
     tab_weights: int = 1      # 1 tabulated window weights where the rig allows, 0 never
+    weight_mode: int = 0      # 0 noise weight K / s2, 1 the printed K / s (Eq. 6)
 
     def __post_init__(self):
         if self.out_affine is None:

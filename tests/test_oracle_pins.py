@@ -402,15 +402,17 @@ def test_per_pixel_calibration_frames_match_scalars():
 
 # ------------------------------------------------------------------ independent route
 
+@pytest.mark.parametrize("weight_mode", [0, 1])
 @pytest.mark.parametrize("order", [0, 1, 2])
-def test_against_bruteforce_qr(order):
+def test_against_bruteforce_qr(order, weight_mode):
     """The C route (search box, normal equations, LDL^T) against brute-force enumeration + Householder
-    QR on a 16x16 rotated three-sensor rig, at every level, in raw mode (Eqs. 6, 18, 20)."""
+    QR on a 16x16 rotated three-sensor rig, at every level, in raw mode (Eqs. 6, 18, 20), with the
+    inverse-variance weight and with the printed weight K / s."""
     fr = synth.paper_scale(size=16, seed=77)
     for s, rot in zip(fr.sensors, (0.0, 6.0, -4.0)):
         s.affine = synth.affine_about_center(16, 16, 0.3, -0.2, rot, 1.01)
         s.raw = synth.simulate_raw(fr.scene, s, 77, rot != 0)
-    p = dataclasses.replace(fr.params, order=order, min_pivot=1e-9)
+    p = dataclasses.replace(fr.params, order=order, min_pivot=1e-9, weight_mode=weight_mode)
     pix = np.array([[u, v] for u in range(0, 16, 3) for v in range(1, 16, 3)])
     res = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True)
     smp = bruteforce.all_samples(fr.sensors)
@@ -419,7 +421,7 @@ def test_against_bruteforce_qr(order):
         for c in range(3):
             for l, sg in enumerate(p.sigmas):
                 sc = sg * (p.green_ratio if c == 1 else 1.0)
-                c0, var, n = bruteforce.fit_point(smp, (float(u), float(v)), c, sc, order)
+                c0, var, n = bruteforce.fit_point(smp, (float(u), float(v)), c, sc, order, weight_mode=weight_mode)
                 assert res["count"][i, c, l] == n
                 if res["valid"][i, c, l]:
                     # both routes carry rounding of order (double epsilon) x (condition number)
@@ -428,3 +430,28 @@ def test_against_bruteforce_qr(order):
                     assert res["var"][i, c, l] == pytest.approx(var, rel=10 * tol)
                     checked += 1
     assert checked > 100
+
+
+def test_printed_window_form_is_sigma_sqrt_h_over_2():
+    """The printed window exp(-|d|^2 / h) with h_G = h_RB / sqrt 2 (Section 5.3.1) is the kernel's
+    exp(-|d|^2 / (2 sigma^2)) at sigma = sqrt(h / 2) with green_ratio = 2^(-1/4): the oracle run with
+    those parameters against the brute-force route evaluating the printed form directly."""
+    fr = synth.paper_scale(size=16, seed=78)
+    hs = (0.6, 1.4, 3.0)
+    p = dataclasses.replace(fr.params, order=1, sigmas=tuple(math.sqrt(h / 2) for h in hs),
+                            green_ratio=2 ** -0.25, min_pivot=1e-9)
+    pix = np.array([[u, v] for u in range(1, 16, 4) for v in range(0, 16, 4)])
+    res = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True)
+    smp = bruteforce.all_samples(fr.sensors)
+    checked = 0
+    for i, (u, v) in enumerate(pix):
+        for c in range(3):
+            for l, h in enumerate(hs):
+                hc = h / math.sqrt(2.0) if c == 1 else h
+                c0, var, n = bruteforce.fit_point(smp, (float(u), float(v)), c, 0.0, 1, h_c=hc)
+                assert res["count"][i, c, l] == n
+                if res["valid"][i, c, l]:
+                    tol = 1e-12 + 50 * np.finfo(float).eps * res["kappa"][i, c, l]
+                    assert res["c0"][i, c, l] == pytest.approx(c0, rel=tol, abs=tol)
+                    checked += 1
+    assert checked > 60

@@ -338,3 +338,49 @@ def test_invalid_arguments_are_rejected(ctx):
     with pytest.raises(hdr.HdrError):
         ctx.set_rig(2, [bad_sensor])
     ctx.check()
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_printed_noise_weight(ctx, order):
+    """weight_mode 1, the noise weight K / s as printed in Section 5.2 (Var C_0 with w^2 s2 = K^2),
+    against the oracle in the same mode on every pixel of the 96x96 paper rig; the default weight
+    gives a different result, and the host-buffer entry point the same bits."""
+    fr = synth.paper_scale(size=96, seed=1070 + order)
+    p = dataclasses.replace(fr.params, order=order, weight_mode=1)
+    _, g, _ = check_frame(ctx, fr, p)
+    h = run(ctx, fr, dataclasses.replace(p, weight_mode=0))
+    assert not np.array_equal(g["out"], h["out"])
+    out = np.empty((3, p.out_h, p.out_w), np.float32)
+    ctx.reconstruct_host(0, p, [np.ascontiguousarray(s.raw) for s in fr.sensors], out)
+    np.testing.assert_array_equal(out, g["out"])
+
+
+def test_printed_noise_weight_rejected_where_unsupported(ctx):
+    """The level maps, batches, the serving loop and the adaptive passes use the inverse-variance
+    weight only: weight_mode 1 is refused there with HDR_E_UNSUPPORTED, before any work."""
+    from paper_1308_4908_gb300 import hdr
+    fr = synth.paper_scale(size=64, seed=1075)
+    p = dataclasses.replace(fr.params, weight_mode=1)
+    ctx.set_rig(0, fr.sensors)
+    raws = upload(fr)
+    out = torch.empty((3, p.out_h, p.out_w), dtype=torch.float32, device="cuda")
+    lv = torch.empty((3, len(p.sigmas) + p.order, p.out_h, p.out_w, 2), dtype=torch.float32, device="cuda")
+    calls = [
+        lambda: ctx.reconstruct(0, p, raws, out=out, levels=lv),
+        lambda: ctx.reconstruct_batch([ctx.frame(0, p, raws, out, keep=keep)]),
+        lambda: ctx.calpa_gradients(0, p, hdr.hdr_calpa_params_default(), raws),
+        lambda: ctx.reconstruct_adaptive(0, p, hdr.hdr_calpa_params_default(), raws, out=out),
+    ]
+    keep = []
+    for call in calls:
+        with pytest.raises(hdr.HdrError) as e:
+            call()
+        assert e.value.status == hdr.HDR_E_UNSUPPORTED
+    srv = hdr.Server(ctx, pool_bytes=64 << 20)
+    try:
+        with pytest.raises(hdr.HdrError) as e:
+            srv.submit(0, p, [np.ascontiguousarray(s.raw) for s in fr.sensors], np.empty((3, 64, 64), np.float32))
+        assert e.value.status == hdr.HDR_E_UNSUPPORTED
+    finally:
+        srv.close()
+    ctx.check()
