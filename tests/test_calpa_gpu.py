@@ -232,3 +232,19 @@ def test_full_size_sampled(ctx):
     o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True, metric=q.astype(np.float64))
     parity.compare(out[:, pix[:, 1], pix[:, 0]], ch[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
                    p.ici_gamma, p.min_pivot)
+
+
+@pytest.mark.parametrize("accum,out_dtype", [(1, 0), (0, 1)])
+def test_steered_compensated_sums_and_fp16_output(ctx, small, accum, out_dtype):
+    """The steered kernel with compensated moment sums (its own instantiation) and with FP16
+    output, against the oracle with the same matrices (FP16 adds its 2^-11 rounding)."""
+    import dataclasses
+    p = dataclasses.replace(small.params, accum=accum, out_dtype=out_dtype, out_w=48, out_h=40)
+    c = _calpa()
+    g, q, out, ch = _passes(ctx, small, c, params=p)
+    check_gradients(small, p, c, g)
+    vv, uu = np.mgrid[0:p.out_h, 0:p.out_w]
+    pix = np.stack([uu.ravel(), vv.ravel()], axis=1)
+    o = oracle.reconstruct(small.sensors, p, pix, levels=True, kappa=True, metric=q.astype(np.float64))
+    parity.compare(out[:, pix[:, 1], pix[:, 0]], ch[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
+                   p.ici_gamma, p.min_pivot, extra_rel=parity.HALF_TOL if out_dtype == 1 else 0.0)
