@@ -384,3 +384,33 @@ def test_printed_noise_weight_rejected_where_unsupported(ctx):
     finally:
         srv.close()
     ctx.check()
+
+
+def test_largest_output(ctx):
+    """The largest output the library accepts, 2^29 pixels (23168 x 23168, the paper rig upsampled
+    about 11.3x: 2.1M tiles, planar offsets beyond 2^30), against the oracle on sampled pixels
+    including the far corner; five rows more exceed 2^29 and are refused with HDR_E_UNSUPPORTED
+    before any work."""
+    from paper_1308_4908_gb300 import hdr
+    fr = synth.paper_scale(size=2048)
+    n = 23168
+    assert n * (n + 4) <= 2 ** 29 < n * (n + 5)
+    p = dataclasses.replace(fr.params, out_w=n, out_h=n, out_affine=synth.output_affine(2048, 2048, n, n))
+    ctx.set_rig(0, fr.sensors)
+    raws = upload(fr)
+    out = torch.empty((3, n, n), dtype=torch.float32, device="cuda")
+    ch = torch.empty((3, n, n), dtype=torch.uint8, device="cuda")
+    ctx.reconstruct(0, p, raws, out=out, choice=ch)
+    ctx.check()
+    r = np.random.default_rng(11)
+    pix = np.concatenate([r.integers(0, n, (150, 2)), [[n - 1, n - 1], [0, n - 1], [n - 1, 0], [0, 0]]])
+    iy, ix = torch.from_numpy(pix[:, 1]).cuda(), torch.from_numpy(pix[:, 0]).cuda()
+    gu = out[:, iy, ix].cpu().numpy()
+    gc = ch[:, iy, ix].cpu().numpy()
+    del out, ch
+    o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True)
+    parity.compare(gu, gc, o, pix, len(p.sigmas), p.order, p.ici_gamma, p.min_pivot)
+    with pytest.raises(hdr.HdrError) as e:
+        ctx.reconstruct(0, dataclasses.replace(p, out_h=n + 5), raws, out=torch.empty(1, device="cuda"))
+    assert e.value.status == hdr.HDR_E_UNSUPPORTED
+    torch.cuda.empty_cache()
