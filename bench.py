@@ -637,7 +637,8 @@ def run_calpa_study(args):
     oracle.build()
     fr = synth.paper_scale(size=args.size)
     p = fr.params
-    c = hdr.hdr_calpa_params_default()
+    over = dict(kv.split("=") for kv in args.calpa.split(",")) if args.calpa else {}
+    c = hdr.hdr_calpa_params_default(**{k: float(v) for k, v in over.items()})
     ctx = hdr.Context(0)
     ctx.set_rig(0, fr.sensors)
     raws = [torch.from_numpy(s.raw).cuda() for s in fr.sensors]
@@ -855,6 +856,7 @@ def main():
     ap.add_argument("--study", choices=["precision", "tiny", "tabweights", "calib", "calpa"], default=None,
                     help="print a study instead of the bench line")
     ap.add_argument("--study-pixels", type=int, default=20000)
+    ap.add_argument("--calpa", default="", help="--study calpa: parameter overrides, e.g. min_eig=0.5,alpha=0.3")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson arrival schedule")
     ap.add_argument("--step-tiles", type=int, default=8192, help="tile budget of one serving step (0 = all pending)")
     args = ap.parse_args()

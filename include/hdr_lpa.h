@@ -333,10 +333,14 @@ typedef struct {
   double lambda2;      /* scaling regulariser in [1e-12, 1e12]                                */
   double min_eig;      /* clamp of C's eigenvalues, 1e-6 <= min_eig <= max_eig <= 1e6; the   */
   double max_eig;      /*   staged window footprint grows by 1 / sqrt(min_eig)                */
+  double grad_scale;   /* pass 2 uses grad_scale times the gradients, in (0, 1e6]: the paper
+                          fixes lambda1 and lambda2 without stating the unit of the radiant
+                          power, so this sets that unit (1 = the unit of the rig's calibration) */
 } hdr_calpa_params;
 
-/* Defaults: grad_sigma 1.2, window_sigma 1, alpha 0.5, lambda1 1, lambda2 1e-3, eigenvalues
- * clamped to [0.25, 16]. */
+/* Defaults: grad_sigma 1.2, window_sigma 1, alpha 0.3, lambda1 1, lambda2 1e-3 (as the paper
+ * fixes them), eigenvalues clamped to [0.25, 16], grad_scale 0.1 (chosen on synthetic HDR scenes
+ * whose radiance spans 1e-2 to 1e4 in the calibration's unit). */
 void hdr_calpa_params_default(hdr_calpa_params *c);
 
 /* Pass 1. grad_dev: device [out_h][out_w][2] float32, the (x, y) gradient in radiance per output

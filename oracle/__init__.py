@@ -233,7 +233,8 @@ def gradients(sensors: Sequence, params, grad_sigma: float, pixels: Optional[np.
 
 
 def steering_metric(grad: np.ndarray, window_sigma: float, alpha: float, lambda1: float = 1.0,
-                    lambda2: float = 0.001, min_eig: float = 0.25, max_eig: float = 16.0) -> np.ndarray:
+                    lambda2: float = 0.001, min_eig: float = 0.25, max_eig: float = 16.0,
+                    grad_scale: float = 1.0) -> np.ndarray:
     """Second pass (Section 5.4): per output pixel the steering matrix C_j (as {C11, C12, C22}) from
     the gradients `grad` [H, W, 2] of the output pixels within 3 window_sigma (Gaussian weights
     w_i, pixels inside the image only; M = their number). The singular values s1 >= s2 and right
@@ -241,8 +242,10 @@ def steering_metric(grad: np.ndarray, window_sigma: float, alpha: float, lambda1
     T = sum_i w_i g_i g_i^T; elongation sigma_j = (s1 + lambda1) / (s2 + lambda1), scaling
     gamma_j = ((s1 s2 + lambda2) / M)^alpha, and C_j = gamma_j (sigma_j u1 u1^T + u2 u2^T / sigma_j)
     (reading: the window exp(-d^T C_j d / (2 sigma^2)) is narrow across the dominant gradient and
-    long along it), its two eigenvalues clamped to [min_eig, max_eig] (reading: bounds the window)."""
-    g = np.asarray(grad, dtype=np.float64)
+    long along it), its two eigenvalues clamped to [min_eig, max_eig] (reading: bounds the window).
+    `grad_scale` multiplies the gradients first (the unit of the radiant power, which the paper's
+    fixed lambda1 and lambda2 presuppose but do not state)."""
+    g = np.asarray(grad, dtype=np.float64) * grad_scale
     H, W = g.shape[:2]
     r = int(np.floor(3.0 * window_sigma))
     T = np.zeros((H, W, 3))
@@ -324,12 +327,13 @@ def equivalent_kernel(sensors, params, u: int, v: int, c: int, sigma: float, ord
 
 def adaptive(sensors: Sequence, params, grad_sigma: float, window_sigma: float, alpha: float,
              lambda1: float = 1.0, lambda2: float = 0.001, min_eig: float = 0.25, max_eig: float = 16.0,
-             pixels: Optional[np.ndarray] = None, levels: bool = False, kappa: bool = False):
+             pixels: Optional[np.ndarray] = None, levels: bool = False, kappa: bool = False,
+             grad_scale: float = 1.0):
     """The adaptive reconstruction of Sections 5.4-5.5 (CALPA): gradients of the green channel,
     the steering matrix per output pixel, then the fit of every channel with the steered window.
     Returns reconstruct()'s dict plus `grad` and `metric` (whole output grid)."""
     g = gradients(sensors, params, grad_sigma)
-    q = steering_metric(g, window_sigma, alpha, lambda1, lambda2, min_eig, max_eig)
+    q = steering_metric(g, window_sigma, alpha, lambda1, lambda2, min_eig, max_eig, grad_scale)
     res = reconstruct(sensors, params, pixels, levels=levels, kappa=kappa, metric=q)
     res["grad"] = g
     res["metric"] = q

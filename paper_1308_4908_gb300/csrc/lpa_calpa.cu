@@ -21,6 +21,7 @@ struct MetricArgs {
   int W, H, r;
   int rw[2 * kRmax + 1];           // half width of the disc in row offset dj (|di| <= rw)
   double w[2 * kRmax * kRmax + 1];  // Gaussian weight by di^2 + dj^2
+  double scale2;                    // grad_scale^2: T of the scaled gradients
   float alpha, lambda1, lambda2, min_eig, max_eig;
 };
 
@@ -64,6 +65,9 @@ __global__ void __launch_bounds__(kBX *kBY) calpa_metric(const __grid_constant__
       c = fma(wt, syy[row + di], c);
     }
   }
+  a *= A.scale2;
+  b *= A.scale2;
+  c *= A.scale2;
   const double h = 0.5 * (a + c), d = sqrt(0.25 * (a - c) * (a - c) + b * b);
   const double l1 = h + d, l2 = fmax(h - d, 0.0);
   double vx = b, vy = l1 - a;
@@ -109,6 +113,7 @@ hdr_status check_calpa(const hdr_calpa_params *c) {
     return lpa_fail(HDR_E_INVALID, "lambda1 in [1e-6, 1e6] and lambda2 in [1e-12, 1e12] required");
   if (!(c->min_eig >= 1e-6) || !(c->max_eig >= c->min_eig) || !(c->max_eig <= 1e6))
     return lpa_fail(HDR_E_INVALID, "1e-6 <= min_eig <= max_eig <= 1e6 required");
+  if (!(c->grad_scale > 0.0) || !(c->grad_scale <= 1e6)) return lpa_fail(HDR_E_INVALID, "grad_scale must be in (0, 1e6]");
   return HDR_OK;
 }
 
@@ -120,11 +125,12 @@ void hdr_calpa_params_default(hdr_calpa_params *c) {
   if (!c) return;
   c->grad_sigma = 1.2;
   c->window_sigma = 1.0;
-  c->alpha = 0.5;
+  c->alpha = 0.3;
   c->lambda1 = 1.0;
   c->lambda2 = 1e-3;
   c->min_eig = 0.25;
   c->max_eig = 16.0;
+  c->grad_scale = 0.1;
 }
 
 hdr_status hdr_calpa_gradients(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const hdr_calpa_params *calpa,
@@ -164,6 +170,7 @@ hdr_status hdr_calpa_metric(hdr_ctx *ctx, int32_t out_w, int32_t out_h, const hd
     A.rw[dj + A.r] = rw;
   }
   for (int k = 0; k <= 2 * A.r * A.r; k++) A.w[k] = std::exp(-(double)k / (2.0 * ws * ws));
+  A.scale2 = calpa->grad_scale * calpa->grad_scale;
   A.alpha = (float)calpa->alpha;
   A.lambda1 = (float)calpa->lambda1;
   A.lambda2 = (float)calpa->lambda2;

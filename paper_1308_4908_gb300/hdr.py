@@ -45,7 +45,7 @@ class hdr_params(ctypes.Structure):
 class hdr_calpa_params(ctypes.Structure):
     _fields_ = [("grad_sigma", ctypes.c_double), ("window_sigma", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("lambda1", ctypes.c_double), ("lambda2", ctypes.c_double), ("min_eig", ctypes.c_double),
-                ("max_eig", ctypes.c_double)]
+                ("max_eig", ctypes.c_double), ("grad_scale", ctypes.c_double)]
 
 
 class hdr_frame(ctypes.Structure):

@@ -83,8 +83,8 @@ def test_defaults_without_a_gpu(lib):
     assert abs(p.green_ratio - 2 ** -0.5) < 1e-15 and p.trunc_k == 3.0 and p.ici_gamma == 2.0
     assert p.min_pivot == 1e-3 and p.cond_fallback == 1e6
     c = hdr.hdr_calpa_params_default()
-    assert (c.grad_sigma, c.window_sigma, c.alpha, c.lambda1, c.lambda2, c.min_eig, c.max_eig) == \
-        (1.2, 1.0, 0.5, 1.0, 1e-3, 0.25, 16.0)
+    assert (c.grad_sigma, c.window_sigma, c.alpha, c.lambda1, c.lambda2, c.min_eig, c.max_eig, c.grad_scale) == \
+        (1.2, 1.0, 0.3, 1.0, 1e-3, 0.25, 16.0, 0.1)
 
 
 def test_create_fails_loudly_without_a_device(lib):

@@ -113,7 +113,7 @@ def test_pass1_gradients(small, small_run):
 def test_pass2_metric(small_run):
     c, (g, q, _, _) = small_run
     q_orc = oracle.steering_metric(g.astype(np.float64), c.window_sigma, c.alpha, c.lambda1, c.lambda2, c.min_eig,
-                                   c.max_eig)
+                                   c.max_eig, c.grad_scale)
     check_metric(q, q_orc)
     # eigenvalues inside the clamp, up to FP32 rounding: the entries' own rounding and the unit
     # direction's squared norm (1 within a few ulp) scale the clamped eigenvalues
@@ -200,7 +200,7 @@ def test_empty_tiny_and_rejected(ctx, small):
                         c.max_eig, pixels=np.array([[0, 0]]), levels=True, kappa=True)
     check_gradients(small, p1, c, g)
     check_metric(q, oracle.steering_metric(g.astype(np.float64), c.window_sigma, c.alpha, c.lambda1, c.lambda2,
-                                           c.min_eig, c.max_eig))
+                                           c.min_eig, c.max_eig, c.grad_scale))
     assert np.isfinite(out).all() and o["out"].shape == (1, 3)
     with pytest.raises(hdr.HdrError) as e:
         ctx.reconstruct_adaptive(0, small.params, _calpa(window_sigma=4.0), raws)
@@ -227,7 +227,7 @@ def test_full_size_sampled(ctx):
     for u, v in pix[:60]:
         v0, v1, u0, u1 = max(0, v - rad), min(p.out_h, v + rad + 1), max(0, u - rad), min(p.out_w, u + rad + 1)
         qo = oracle.steering_metric(g[v0:v1, u0:u1].astype(np.float64), c.window_sigma, c.alpha, c.lambda1,
-                                    c.lambda2, c.min_eig, c.max_eig)[v - v0, u - u0]
+                                    c.lambda2, c.min_eig, c.max_eig, c.grad_scale)[v - v0, u - u0]
         check_metric(q[v, u][None], qo[None])
     o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True, metric=q.astype(np.float64))
     parity.compare(out[:, pix[:, 1], pix[:, 0]], ch[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
@@ -248,3 +248,13 @@ def test_steered_compensated_sums_and_fp16_output(ctx, small, accum, out_dtype):
     o = oracle.reconstruct(small.sensors, p, pix, levels=True, kappa=True, metric=q.astype(np.float64))
     parity.compare(out[:, pix[:, 1], pix[:, 0]], ch[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
                    p.ici_gamma, p.min_pivot, extra_rel=parity.HALF_TOL if out_dtype == 1 else 0.0)
+
+
+def test_metric_with_a_gradient_unit(ctx, small_run):
+    """grad_scale (the unit of the radiant power for the fixed regularisers) against the oracle."""
+    c0, (g, _, _, _) = small_run
+    c = _calpa(grad_scale=1e-3, alpha=0.3)
+    q = ctx.calpa_metric(c, torch.from_numpy(g).cuda()).cpu().numpy()
+    ctx.check()
+    check_metric(q, oracle.steering_metric(g.astype(np.float64), c.window_sigma, c.alpha, c.lambda1, c.lambda2,
+                                           c.min_eig, c.max_eig, c.grad_scale))

@@ -118,3 +118,16 @@ def test_steered_window_area_follows_the_determinant():
     assert np.all(np.abs(aniso / iso - 1.0) < 0.12)
     with pytest.raises(ValueError):
         oracle.reconstruct(sensors, p, pix, metric=-q4)
+
+
+def test_gradient_unit_scaling():
+    """Gradients in a unit s times larger: the elongation is unchanged when lambda1 is scaled by s,
+    and the scaling parameter grows by s^(2 alpha) when lambda2 is scaled by s^2, so the matrix
+    computed with grad_scale = s equals s^(2 alpha) times the one with the regularisers rescaled."""
+    r = np.random.default_rng(4)
+    g = r.normal(0.0, 3.0, (17, 19, 2))
+    g[:, 8:11, 0] += 40.0
+    s, alpha = 1e-3, 0.4
+    a = oracle.steering_metric(g, 1.3, alpha, 1.0, 1e-3, 1e-12, 1e12, grad_scale=s)
+    b = oracle.steering_metric(g, 1.3, alpha, 1.0 / s, 1e-3 / s ** 2, 1e-12, 1e12)
+    np.testing.assert_allclose(a, s ** (2 * alpha) * b, rtol=1e-10, atol=0)
