@@ -258,15 +258,17 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
     pos = pos && (a[tri(i, i)] > T(0));
     rdiag[i] = a[tri(i, i)] > T(0) ? rcp_t(a[tri(i, i)]) : T(0);
   }
-  // triangular loops are written with fixed trip counts and guards so that they unroll fully
-  T dinv[P];
+  // triangular loops are written with fixed trip counts and guards so that they unroll fully;
+  // u holds L_iq d_q (the column before its division by the pivot), so that each update term
+  // is one FMA
+  T dinv[P], u[P * (P + 1) / 2];
   T dmin = T(1e30), dmax = T(0);
 #pragma unroll
   for (int j = 0; j < P; j++) {
     T dj = a[tri(j, j)];
 #pragma unroll
     for (int q = 0; q < P; q++)
-      if (q < j) dj -= a[tri(j, q)] * a[tri(j, q)] * a[tri(q, q)];
+      if (q < j) dj -= a[tri(j, q)] * u[tri(j, q)];
     a[tri(j, j)] = dj;
     const T de = dj * rdiag[j];  // pivot of the equilibrated matrix
     dmin = de < dmin ? de : dmin;
@@ -278,7 +280,8 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
         T t = a[tri(i, j)];
 #pragma unroll
         for (int q = 0; q < P; q++)
-          if (q < j) t -= a[tri(i, q)] * a[tri(j, q)] * a[tri(q, q)];
+          if (q < j) t -= a[tri(i, q)] * u[tri(j, q)];
+        u[tri(i, j)] = t;
         a[tri(i, j)] = t * dinv[j];
       }
     }
@@ -307,13 +310,16 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
       if (q > i) t -= a[tri(q, i)] * x[q];
     x[i] = t;
   }
+  // the quadratic form over the symmetric K: diagonal terms once, the others doubled
   T c0 = T(0), var = T(0);
 #pragma unroll
   for (int i = 0; i < P; i++) {
     c0 += x[i] * m.template B<T>(i);
     T row = T(0);
 #pragma unroll
-    for (int j = 0; j < P; j++) row += x[j] * m.template Kv<T>(mono_index(ex(i) + ex(j), ey(i) + ey(j)));
+    for (int j = 0; j < P; j++)
+      if (j > i) row += x[j] * m.template Kv<T>(mono_index(ex(i) + ex(j), ey(i) + ey(j)));
+    row = T(2) * row + x[i] * m.template Kv<T>(mono_index(2 * ex(i), 2 * ey(i)));
     var += x[i] * row;
   }
   r.c0 = (float)c0;
@@ -503,18 +509,17 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
     const bool colok = pc0 >= 0 && pc0 + nw <= PW;
     const float2 *pl = planes + (ox + 2 * oy) * (PH * PW);
     const float Dx0 = 2.f * (float)ilo - rx;
+    // a row of the lane's own window outside the staged box is an error (the footprint is planned
+    // to hold every window); only the rows inside the box are walked
+    if (active && nj > 0 && !(colok && pr0 >= 0 && pr0 + nj <= PH)) atomicOr(status, LPA_ERR_BOUNDS);
+    const int rbeg = colok ? max(0, -pr0) : NJ;
+    const int rend = min(STEER ? nj : NJ, PH - pr0);
+    const float2 *rowp = pl + (pr0 + rbeg) * PW + pc0;
 #pragma unroll 1
-    for (int r = 0; r < NJ; r++) {
-      if (STEER && r >= nj) break;
-      const int pr = pr0 + r;
-      if (!(colok && pr >= 0 && pr < PH)) {
-        if (active && r < nj) atomicOr(status, LPA_ERR_BOUNDS);
-        continue;
-      }
+    for (int r = rbeg; r < rend; r++, rowp += PW) {
       const float Dy = 2.f * (float)(jlo + r) - ry;
       const float dxr = fmaf(a00, Dx0, a01 * Dy), dyr = fmaf(a10, Dx0, a11 * Dy);
       const float2 DR = make_float2(dxr, dyr);
-      const float2 *rowp = pl + pr * PW + pc0;
       const float2 S2 = make_float2(sx, sy);
       row_cells<ORDER, MODE>(m, rowp, nw, DR, S2, R2, cexp, taper, Q);
     }
