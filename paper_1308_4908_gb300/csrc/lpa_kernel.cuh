@@ -515,14 +515,14 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
     const int rbeg = colok ? max(0, -pr0) : NJ;
     const int rend = min(STEER ? nj : NJ, PH - pr0);
     const float2 *rowp = pl + (pr0 + rbeg) * PW + pc0;
+    // offset of the first cell of the first row; each row adds A (0, 2)
+    const float Dy0 = 2.f * (float)(jlo + rbeg) - ry;
+    const float2 DR0 = make_float2(fmaf(a00, Dx0, a01 * Dy0), fmaf(a10, Dx0, a11 * Dy0));
+    const float2 T2 = make_float2(2.f * a01, 2.f * a11), S2 = make_float2(sx, sy);
+    float rf = 0.f;
 #pragma unroll 1
-    for (int r = rbeg; r < rend; r++, rowp += PW) {
-      const float Dy = 2.f * (float)(jlo + r) - ry;
-      const float dxr = fmaf(a00, Dx0, a01 * Dy), dyr = fmaf(a10, Dx0, a11 * Dy);
-      const float2 DR = make_float2(dxr, dyr);
-      const float2 S2 = make_float2(sx, sy);
-      row_cells<ORDER, MODE>(m, rowp, nw, DR, S2, R2, cexp, taper, Q);
-    }
+    for (int r = rbeg; r < rend; r++, rowp += PW, rf += 1.f)
+      row_cells<ORDER, MODE>(m, rowp, nw, __ffma2_rn(make_float2(rf, rf), T2, DR0), S2, R2, cexp, taper, Q);
   }
 }
 
