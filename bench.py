@@ -857,7 +857,7 @@ def main():
                     help="print a study instead of the bench line")
     ap.add_argument("--study-pixels", type=int, default=20000)
     ap.add_argument("--calpa", default="", help="--study calpa: parameter overrides, e.g. min_eig=0.5,alpha=0.3")
-    ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson arrival schedule")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="length of the Poisson arrival schedule")
     ap.add_argument("--step-tiles", type=int, default=8192, help="tile budget of one serving step (0 = all pending)")
     args = ap.parse_args()
     if args.study == "precision":

@@ -956,7 +956,8 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
     const void *fn = lpa_kernel(L.order, comp, false, L.mode, cfg.tile_h);
     if (!fn) return fail(HDR_E_INTERNAL, "no kernel for order %d, mode %d, tile height %d", L.order, L.mode, cfg.tile_h);
     CUDA_TRY(lpa_opt_in(fn));
-    key.push_back({L.order * 4 + L.mode, comp ? 1 : 0, cfg.tile_h, grid[order[k]], (int64_t)L.smem_bytes});
+    // grid size and shared memory are set on each replay: graphs are kept per sequence of kernels
+    key.push_back({L.order * 4 + L.mode, comp ? 1 : 0, cfg.tile_h, 0, 0});
     args[k] = &plans[order[k]];
     kp[k] = cudaKernelNodeParams{};
     kp[k].func = const_cast<void *>(fn);
@@ -967,10 +968,19 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
   }
   auto it = B.frame_graphs.find(key);
   if (it != B.frame_graphs.end()) {
-    for (size_t k = 0; k < order.size(); k++)
-      CUDA_TRY(cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.nodes[k], &kp[k]));
-  } else {
-    if (B.frame_graphs.size() >= 256) {  // shapes that never repeat (serving steps): start over
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < order.size() && e == cudaSuccess; k++)
+      e = cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.nodes[k], &kp[k]);
+    if (e != cudaSuccess) {  // an update the driver refuses: record the graph again
+      cudaGetLastError();
+      cudaGraphExecDestroy(it->second.exec);
+      cudaGraphDestroy(it->second.graph);
+      B.frame_graphs.erase(it);
+      it = B.frame_graphs.end();
+    }
+  }
+  if (it == B.frame_graphs.end()) {
+    if (B.frame_graphs.size() >= 256) {  // kernel sequences that never repeat: start over
       for (auto &g : B.frame_graphs) {
         cudaGraphExecDestroy(g.second.exec);
         cudaGraphDestroy(g.second.graph);
