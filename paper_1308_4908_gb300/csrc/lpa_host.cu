@@ -425,6 +425,9 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled failed for sensor %d (code %d)", s, (int)cr);
   }
+  off = (off + 15) / 16 * 16;
+  L.off_pos = off;
+  off += (uint32_t)(rig.n * 16 * LPA_TILE * tile_h);
   L.tx_bytes = tx;
   L.smem_bytes = off;
   int max_smem = 0;

@@ -454,16 +454,13 @@ __device__ __forceinline__ void row_cells(MOM &m, const float2 *rowp, int n, flo
 
 template <int ORDER, bool COMP, int MODE = LPA_SEARCHED>
 __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COMP>::type &m, const LpaSensorK &S,
-                                                  const Anchor &an, int du, int dv, int c, float R, float R2,
+                                                  int4 pos, int c, float R, float R2,
                                                   float cexp, float taper, int x0, int y0,
                                                   const unsigned char *smem, bool active, unsigned *status,
                                                   float4 Q = make_float4(1.f, 0.f, 1.f, 0.f)) {
-  // the pixel's point in sensor s: anchor (FP64 at the 8x8 block corner) + small FP32 step
-  float px = an.fx + (float)du * S.Gf[0] + (float)dv * S.Gf[1];
-  float py = an.fy + (float)du * S.Gf[2] + (float)dv * S.Gf[3];
-  float flx = floorf(px), fly = floorf(py);
-  const int ix = an.ix + (int)flx, iy = an.iy + (int)fly;
-  const float fx = px - flx, fy = py - fly;
+  // the pixel's point in sensor s: sample cell (ix, iy) and fraction (fx, fy) in [0, 1)
+  const int ix = pos.x, iy = pos.y;
+  const float fx = __int_as_float(pos.z), fy = __int_as_float(pos.w);
   const int PW = S.box_w >> 1, PH = S.box_h >> 1;
   const float2 *planes = reinterpret_cast<const float2 *>(smem + S.off_planes);
   const float a00 = S.A[0], a01 = S.A[1], a10 = S.A[2], a11 = S.A[3];
@@ -717,6 +714,20 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   const float log2e = 1.4426950408889634f;
 
   constexpr bool TAB = MODE == LPA_TABULATED, STEER = MODE == LPA_STEERED, GRAD = MODE == LPA_GRADIENTS;
+  // the pixel's point in each sensor, once: anchor (FP64 at the 8x8 block corner) + small FP32
+  // step, split into sample cell and fraction; every channel and scale reads it back
+  int4 *pos = reinterpret_cast<int4 *>(smem + RD(L.off_pos)) + tid;
+  if constexpr (!TAB) {
+#pragma unroll 1
+    for (int s = 0; s < S; s++) {
+      const Anchor &an = anchors[ab][s];
+      const LpaSensorK &Sk = L.s[s];
+      const float px = an.fx + (float)du * Sk.Gf[0] + (float)dv * Sk.Gf[1];
+      const float py = an.fy + (float)du * Sk.Gf[2] + (float)dv * Sk.Gf[3];
+      const float flx = floorf(px), fly = floorf(py);
+      pos[s * NT] = make_int4(an.ix + (int)flx, an.iy + (int)fly, __float_as_int(px - flx), __float_as_int(py - fly));
+    }
+  }
   float4 Q = make_float4(1.f, 0.f, 1.f, 0.f);  // steering matrix of this pixel (Section 5.4)
   if constexpr (STEER)
     if (pix) Q = make_float4(L.aux[opix * 3], L.aux[opix * 3 + 1], L.aux[opix * 3 + 2], 0.f);
@@ -740,7 +751,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
         if constexpr (TAB)
           accumulate_table<ORDER>(m, L, s, c, j, u, v, fp_x0[s], fp_y0[s], smem, act, L.status);
         else
-          accumulate_sensor<ORDER, COMP, MODE>(m, L.s[s], anchors[ab][s], du, dv, c, R, R2, cexp, RD(L.taper),
+          accumulate_sensor<ORDER, COMP, MODE>(m, L.s[s], pos[s * NT], c, R, R2, cexp, RD(L.taper),
                                                 fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q);
       }
       FitOut f = solve_with_fallback<P, decltype(m), GRAD>(m, RD(L.min_pivot), RD(L.cond_fallback));

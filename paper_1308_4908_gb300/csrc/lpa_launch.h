@@ -56,6 +56,8 @@ struct LpaLaunch {
   unsigned int *status;
   uint32_t tx_bytes;             // bytes landed by the bulk tensor copies of one tile
   uint32_t smem_bytes;
+  uint32_t off_pos;              // byte offset of each thread's pixel position in each sensor
+                                 // (int4 {ix, iy, fx bits, fy bits}, [n_sensors][threads])
   int tile_h;                    // tile height the plan was made for
   int tile0;                     // single-frame grid: CTA b reconstructs tile tile0 + b
   int tile_count;                // single-frame grid size; 0 = every tile from tile0 on
