@@ -425,20 +425,24 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled failed for sensor %d (code %d)", s, (int)cr);
   }
-  off = (off + 15) / 16 * 16;
-  L.off_pos = off;
-  off += (uint32_t)(rig.n * 16 * LPA_TILE * tile_h);
   L.tx_bytes = tx;
+  if (p->weight_mode == 1) {  // the printed noise weight K / s: searched window, its own kernel
+    L.mode = LPA_LITERAL;
+  } else {
+    hdr_status st = build_tables(env, rig, p, L);
+    if (st) return st;
+  }
+  if (L.mode != LPA_TABULATED) {  // each thread's sample cell in each sensor (tables need none)
+    off = (off + 15) / 16 * 16;
+    L.off_pos = off;
+    off += (uint32_t)(rig.n * 16 * LPA_TILE * tile_h);
+  }
   L.smem_bytes = off;
   int max_smem = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, env.device));
   if ((int)off > max_smem - 1024)
     return fail(HDR_E_UNSUPPORTED, "staging needs %u bytes of shared memory (limit %d)", off, max_smem - 1024);
-  if (p->weight_mode == 1) {  // the printed noise weight K / s: searched window, its own kernel
-    L.mode = LPA_LITERAL;
-    return HDR_OK;
-  }
-  return build_tables(env, rig, p, L);
+  return HDR_OK;
 }
 
 hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
@@ -873,9 +877,11 @@ hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *
   for (int o = 0; o < 3; o++) smem[o] = 0, n_tiles[o] = 0;
   for (int f = 0; f < n; f++) {
     const hdr_frame &F = frames[f];
-    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
-                             plans[f], cfg.tile_h);
+    // no tables: the persistent kernels search every window
+    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, nullptr}, ctx->rigs[F.rig_id], F.params,
+                             F.raw_dev, plans[f], cfg.tile_h);
     if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
+    if (plans[f].mode != LPA_SEARCHED) return fail(HDR_E_INTERNAL, "frame %d: the persistent form searches windows", f);
     plans[f].out = F.out_dev;
     plans[f].choice = F.choice_dev;
     plans[f].levels = nullptr;

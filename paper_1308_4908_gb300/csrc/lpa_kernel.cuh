@@ -718,6 +718,10 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   // step, split into sample cell and fraction; every channel and scale reads it back
   int4 *pos = reinterpret_cast<int4 *>(smem + RD(L.off_pos)) + tid;
   if constexpr (!TAB) {
+    if (RD(L.off_pos) == 0u) {  // a plan without the position table (offset 0 holds a raw box)
+      if (tid == 0) atomicOr(L.status, LPA_ERR_BOUNDS);
+      return false;
+    }
 #pragma unroll 1
     for (int s = 0; s < S; s++) {
       const Anchor &an = anchors[ab][s];
