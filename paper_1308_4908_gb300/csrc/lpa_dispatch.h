@@ -2,6 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "lpa_launch.h"
 
 // Largest dynamic shared memory a block of the current device may opt in to.
@@ -19,12 +23,25 @@ inline int lpa_smem_optin() {
 // Opt a kernel in to the largest dynamic shared memory its static shared memory leaves, never to
 // one launch's size: a graph recorded with a larger launch stays valid whatever smaller launches
 // of the same kernel run in between.
+// Done once per kernel and device (the attribute persists).
 inline cudaError_t lpa_opt_in(const void *fn) {
-  cudaFuncAttributes a;
-  cudaError_t e = cudaFuncGetAttributes(&a, fn);
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              lpa_smem_optin() - (int)a.sharedSizeBytes);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({fn, dev})) return cudaSuccess;
+  }
+  cudaFuncAttributes a;
+  e = cudaFuncGetAttributes(&a, fn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lpa_smem_optin() - (int)a.sharedSizeBytes);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  done.insert({fn, dev});
+  return cudaSuccess;
 }
 
 // One CTA per tile of L with the kernel of L.mode (cudaErrorInvalidConfiguration where that mode

@@ -106,13 +106,20 @@ struct BatchState {
 // Device copies of tabulated-weight tables, keyed by a hash of their contents. Tables are small
 // (tens of KB) and kept until the context is destroyed (at most kMaxTables; then the context waits
 // for its work and starts over).
-struct TabCache {
+// Host-side caches of a context's launch planning.
+struct PlanCache {
+  // encoded tensor maps by (raw pointer, width, height, pitch, box): encoding is a driver call
+  std::map<std::array<uint64_t, 4>, CUtensorMap> tmaps;
+  // tabulated-weight tables on the device, by a hash of their contents
   std::map<uint64_t, void *> dev;
+  // the inputs a table is built from (sensor count, scales, window constants, each sensor's
+  // translation) -> the device table, so that a repeated configuration skips the host build
+  std::map<std::vector<double>, void *> by_inputs;
 };
 
 struct hdr_ctx {
   int device = 0;
-  TabCache tabs;
+  PlanCache tabs;
   unsigned int *status = nullptr;
   BatchState batch;
   Rig rigs[kMaxRigs];
@@ -231,7 +238,8 @@ struct PlanEnv {
   EncodeTiledFn encode;
   unsigned int *status;
   int device;
-  TabCache *tabs;  // NULL: never tabulate (the entry point may not allocate)
+  PlanCache *tabs;  // NULL: no caches (the entry point may not allocate): nothing tabulated
+  bool tabulate;    // tabulated weights allowed (the persistent batch kernels search every window)
 };
 
 constexpr size_t kMaxTables = 4096;
@@ -251,19 +259,33 @@ int floor_div2_parity(long long v) { return (int)(((v % 2) + 2) % 2); }
 hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p, LpaLaunch &L) {
   L.tab_hdr = nullptr;
   L.tab_cells = nullptr;
-  if (!env.tabs || p->tab_weights != 1 || !is_identity_linear(p->out_affine)) return HDR_OK;
+  if (!env.tabs || !env.tabulate || p->tab_weights != 1 || !is_identity_linear(p->out_affine)) return HDR_OK;
   for (int s = 0; s < rig.n; s++)
     if (!is_identity_linear(rig.s[s].d.affine)) return HDR_OK;
   const int J = p->n_scales;
+  std::vector<double> inputs = {(double)rig.n, (double)J, p->trunc_k, p->green_ratio};
+  for (int j = 0; j < J; j++) inputs.push_back(p->sigma[j]);
+  for (int s = 0; s < rig.n; s++) {
+    inputs.push_back(L.s[s].G[2]);
+    inputs.push_back(L.s[s].G[5]);
+    L.s[s].ix_shift = (int)std::floor(L.s[s].G[2]);
+    L.s[s].iy_shift = (int)std::floor(L.s[s].G[5]);
+  }
+  const size_t n_hdr = (size_t)rig.n * 16 * J;
+  auto known = env.tabs->by_inputs.find(inputs);
+  if (known != env.tabs->by_inputs.end()) {
+    L.tab_hdr = static_cast<const int4 *>(known->second);
+    L.tab_cells = reinterpret_cast<const float4 *>(static_cast<const int4 *>(known->second) + n_hdr);
+    L.mode = LPA_TABULATED;
+    return HDR_OK;
+  }
   const double taper = std::exp(-0.5 * p->trunc_k * p->trunc_k);
-  std::vector<int4> hdr((size_t)rig.n * 16 * J);
+  std::vector<int4> hdr(n_hdr);
   std::vector<float4> cells;
   auto pack = [](int lo, int hi) { return (lo & 0xffff) | (hi << 16); };
   for (int s = 0; s < rig.n; s++) {
     const double gx = L.s[s].G[2], gy = L.s[s].G[5];
     const double flx = std::floor(gx), fly = std::floor(gy);
-    L.s[s].ix_shift = (int)flx;
-    L.s[s].iy_shift = (int)fly;
     for (int pu = 0; pu < 2; pu++)
       for (int pv = 0; pv < 2; pv++)
         for (int ph = 0; ph < 4; ph++) {
@@ -318,6 +340,7 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
       CUDA_TRY(cudaDeviceSynchronize());
       for (auto &t : env.tabs->dev) cudaFree(t.second);
       env.tabs->dev.clear();
+      env.tabs->by_inputs.clear();
     }
     void *d = nullptr;
     CUDA_TRY(cudaMalloc(&d, std::max<size_t>(nb, 16)));
@@ -331,6 +354,8 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
     }
     it = env.tabs->dev.emplace(hsh, d).first;
   }
+  if (env.tabs->by_inputs.size() >= 4 * kMaxTables) env.tabs->by_inputs.clear();
+  env.tabs->by_inputs.emplace(std::move(inputs), it->second);
   L.tab_hdr = static_cast<const int4 *>(it->second);
   L.tab_cells = reinterpret_cast<const float4 *>(static_cast<const int4 *>(it->second) + hdr.size());
   L.mode = LPA_TABULATED;
@@ -420,10 +445,22 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
     cuuint64_t gstride[1] = {(cuuint64_t)d.pitch_elems * 2};
     cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
     cuuint32_t estr[2] = {1, 1};
-    CUresult cr = env.encode(&K.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t *>(raw[s]), gdim, gstride,
-                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled failed for sensor %d (code %d)", s, (int)cr);
+    const std::array<uint64_t, 4> mkey = {reinterpret_cast<uint64_t>(raw[s]),
+                                          ((uint64_t)d.width << 32) | (uint32_t)d.height, (uint64_t)d.pitch_elems,
+                                          ((uint64_t)bw << 32) | (uint32_t)bh};
+    auto known = env.tabs ? env.tabs->tmaps.find(mkey) : std::map<std::array<uint64_t, 4>, CUtensorMap>::iterator();
+    if (env.tabs && known != env.tabs->tmaps.end()) {
+      K.tmap = known->second;
+    } else {
+      CUresult cr = env.encode(&K.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t *>(raw[s]), gdim, gstride,
+                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (cr != CUDA_SUCCESS) return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled failed for sensor %d (code %d)", s, (int)cr);
+      if (env.tabs) {
+        if (env.tabs->tmaps.size() >= 4096) env.tabs->tmaps.clear();
+        env.tabs->tmaps.emplace(mkey, K.tmap);
+      }
+    }
   }
   L.tx_bytes = tx;
   if (p->weight_mode == 1) {  // the printed noise weight K / s: searched window, its own kernel
@@ -447,7 +484,7 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
 
 hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
                 double reach = 1.0) {
-  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs}, rig, p, raw, L, 16, reach);
+  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, true}, rig, p, raw, L, 16, reach);
 }
 
 hdr_status launch(const LpaLaunch &L, int accum, bool diag, cudaStream_t st) {
@@ -878,8 +915,8 @@ hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *
   for (int f = 0; f < n; f++) {
     const hdr_frame &F = frames[f];
     // no tables: the persistent kernels search every window
-    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, nullptr}, ctx->rigs[F.rig_id], F.params,
-                             F.raw_dev, plans[f], cfg.tile_h);
+    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, false}, ctx->rigs[F.rig_id],
+                             F.params, F.raw_dev, plans[f], cfg.tile_h);
     if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
     if (plans[f].mode != LPA_SEARCHED) return fail(HDR_E_INTERNAL, "frame %d: the persistent form searches windows", f);
     plans[f].out = F.out_dev;
@@ -935,7 +972,7 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
   std::vector<int> grid(n, 0);
   for (int f = 0; f < n; f++) {
     const hdr_frame &F = frames[f];
-    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
+    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, true}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
                              plans[f], cfg.tile_h);
     if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
     plans[f].out = F.out_dev;
@@ -1318,7 +1355,7 @@ extern "C" hdr_status hdr_reconstruct_noalloc(int device, int32_t n_sensors, con
     CUDA_TRY(place(rs.d.sat_frame, npx * 2, (void **)&rs.satf));
   }
   LpaLaunch L;
-  st = plan_env(PlanEnv{encode, status, device, nullptr}, rig, params, raw_dev, L);
+  st = plan_env(PlanEnv{encode, status, device, nullptr, false}, rig, params, raw_dev, L);
   for (int s = 0; s < n_sensors; s++) rig.s[s] = RigSensor();  // the frames belong to the scratch array
   rig.n = 0;
   if (st) return st;
