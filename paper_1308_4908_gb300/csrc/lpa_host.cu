@@ -483,8 +483,8 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
 }
 
 hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
-                double reach = 1.0) {
-  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, true}, rig, p, raw, L, 16, reach);
+                double reach = 1.0, bool tabulate = true) {
+  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, tabulate}, rig, p, raw, L, 16, reach);
 }
 
 hdr_status launch(const LpaLaunch &L, int accum, bool diag, cudaStream_t st) {
@@ -518,7 +518,8 @@ hdr_status reconstruct_impl(hdr_ctx *ctx, int32_t rig_id, const hdr_params *para
   if (levels_dev && params->weight_mode != 0)
     return fail(HDR_E_UNSUPPORTED, "the level maps are computed with the inverse-variance weight (weight_mode 0)");
   LpaLaunch L;
-  st = plan(ctx, ctx->rigs[rig_id], params, raw_dev, L);
+  // the diagnostic (level maps) kernel searches every window
+  st = plan(ctx, ctx->rigs[rig_id], params, raw_dev, L, 1.0, levels_dev == nullptr);
   if (st) return st;
   L.out = out_dev;
   L.choice = choice_dev;

@@ -49,8 +49,8 @@ const void *kernel(bool comp, bool diag, int mode, int tile_h) {
 // One CTA per tile of L (tiles L.tile0 .. L.tile0 + grid - 1) with the kernel L.mode selects.
 template <int ORDER>
 cudaError_t launch(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st) {
-  // the diagnostic (level maps) pass always searches the window, also for a tabulated plan
-  const void *fn = kernel<ORDER>(comp, diag, diag && L.mode == LPA_TABULATED ? LPA_SEARCHED : L.mode, L.tile_h);
+  // the diagnostic (level maps) kernel is instantiated for the searched window only
+  const void *fn = kernel<ORDER>(comp, diag, L.mode, L.tile_h);
   if (!fn) return cudaErrorInvalidConfiguration;
   cudaError_t e = lpa_opt_in(fn);
   if (e != cudaSuccess) return e;

@@ -92,10 +92,8 @@ def test_paper_scale_full_size_sampled(ctx):
     assert np.isfinite(g["out"]).mean() > 0.999
 
 
-def test_levels_match_oracle(ctx):
-    """Every level (each scale at order M, then the lower orders at the largest scale):
-    C_0 and Var C_0 from the diagnostic entry point against the oracle's."""
-    fr = synth.paper_scale(size=64, seed=1010)
+def check_levels(ctx, fr):
+    """C_0 and Var C_0 of every level from the diagnostic entry point against the oracle's."""
     p = fr.params
     g = run(ctx, fr, p, levels=True)
     vv, uu = np.mgrid[0:64, 0:64]
@@ -121,6 +119,18 @@ def test_levels_match_oracle(ctx):
             assert np.all(ev <= 10 * tol / np.maximum(np.abs(oc0[both]), parity.TAU) + 1e-4), (c, l, float(ev.max()))
             n_cmp += both.sum()
     assert n_cmp > 3 * 64 * 64 * 3
+
+
+def test_levels_match_oracle(ctx):
+    """Every level (each scale at order M, then the lower orders at the largest scale):
+    C_0 and Var C_0 from the diagnostic entry point against the oracle's."""
+    check_levels(ctx, synth.paper_scale(size=64, seed=1010))
+
+
+def test_levels_on_a_translational_rig(ctx):
+    """A rig whose plain reconstruction reads tabulated weights: the diagnostic entry point plans
+    the searched window instead, and every level matches the oracle."""
+    check_levels(ctx, translational(64, 1011, [(0.0, 0.0), (0.4, 0.45), (-1.3, 0.7)]))
 
 
 # ------------------------------------------------------------------ rigs and mappings
