@@ -183,8 +183,10 @@ typedef struct {
  * owned by the context (double-buffered: the call waits only if the launch before the previous
  * one is still reading) and clears the tile counters. `cfg` NULL = the configuration
  * hdr_tune_batch found for batches of this kind, else the default {16, 0, 1, 0}. All frames must
- * use the same `accum`. Asynchronous like hdr_reconstruct. Results are identical to reconstructing
- * each frame with hdr_reconstruct. */
+ * use the same `accum` and weight_mode 0 (HDR_E_UNSUPPORTED otherwise). Asynchronous like
+ * hdr_reconstruct. Results are identical to reconstructing each frame with hdr_reconstruct, except
+ * that form 1 searches every window: for a frame that hdr_reconstruct reads from tabulated weights
+ * (tab_weights), form 1 gives the same fit with different rounding. */
 hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames,
                                  const hdr_batch_config *cfg, void *cuda_stream);
 
