@@ -207,7 +207,9 @@ def run_reference(args, world, rank, pg):
     oracle.build()
     frame = synth.paper_scale()
     rate, dt, thr = oracle_rate(frame, 4096, seed=1)
-    n = int(min(max(3.0 * rate * 1e6, 4096), 1_000_000))   # about 3 s per step
+    # about 3 s per step, and about two minutes for all timed steps together
+    per_step_s = min(3.0, 120.0 / max(args.steps, 1))
+    n = int(min(max(per_step_s * rate * 1e6, 4096), 1_000_000))
     for w in range(args.warmup if args.warmup < 1 else 1):
         oracle_rate(frame, min(n, 4096), seed=100 + w)
     times = []
