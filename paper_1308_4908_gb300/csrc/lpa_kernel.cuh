@@ -758,7 +758,17 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
           accumulate_sensor<ORDER, COMP, MODE>(m, L.s[s], pos[s * NT], c, R, R2, cexp, RD(L.taper),
                                                 fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q);
       }
-      FitOut f = solve_with_fallback<P, decltype(m), GRAD>(m, RD(L.min_pivot), RD(L.cond_fallback));
+      // a fit with fewer samples than unknowns is not usable whatever its pivots: when that holds
+      // for the whole warp (its lanes share one sample layout on near-translational rigs), the
+      // factorisation is skipped
+      FitOut f;
+      if (__all_sync(LPA_FULL, m.cnt < (float)P)) {
+        f.valid = false;
+        f.c0 = f.var = f.c1 = f.c2 = 0.f;
+        f.dmin = f.dmax = 0.f;
+      } else {
+        f = solve_with_fallback<P, decltype(m), GRAD>(m, RD(L.min_pivot), RD(L.cond_fallback));
+      }
       if constexpr (GRAD) {  // Section 5.4: the order-1 fit's linear coefficients; 0 if not usable
         if (pix) {
           L.aux[opix * 2] = f.valid ? f.c1 : 0.f;
