@@ -131,3 +131,30 @@ def test_gradient_unit_scaling():
     a = oracle.steering_metric(g, 1.3, alpha, 1.0, 1e-3, 1e-12, 1e12, grad_scale=s)
     b = oracle.steering_metric(g, 1.3, alpha, 1.0 / s, 1e-3 / s ** 2, 1e-12, 1e12)
     np.testing.assert_allclose(a, s ** (2 * alpha) * b, rtol=1e-10, atol=0)
+
+
+def test_gradient_rounding_scale_bounds_a_perturbation():
+    """The rounding scale the oracle reports for each gradient component bounds how far it moves
+    when every sample value is perturbed by a relative eps (first order): with f_k -> f_k (1 + eps
+    s_k), |s_k| <= 1, the coefficient moves by sum_k w_k (A^-1 phi_k)_1 f_k eps s_k, at most
+    eps efit. Random signs come close to it; the scale must never be exceeded."""
+    import copy
+    rng = np.random.default_rng(12)
+
+    def fn(c, X, Y):
+        return 200.0 + 30.0 * np.sin(0.4 * X) + 10.0 * np.cos(0.3 * Y) + 5.0 * c
+    sensors = value_rig(fn, seed=9)
+    p = synth.Params(order=2, sigmas=(1.0,), out_w=24, out_h=24)
+    pix = np.array([[u, v] for u in range(6, 18, 3) for v in range(6, 18, 3)])
+    base = oracle.gradients(sensors, p, 1.2, pixels=pix, diagnostics=True)
+    eps = 1e-6
+    worst = 0.0
+    for trial in range(4):
+        pert = copy.deepcopy(sensors)
+        for s in pert:
+            s.value_f = s.value_f * (1.0 + eps * rng.choice([-1.0, 1.0], s.value_f.shape))
+        g = oracle.gradients(pert, p, 1.2, pixels=pix)
+        ratio = np.abs(g - base["grad"]) / (eps * base["efit"])
+        worst = max(worst, float(ratio.max()))
+    assert worst <= 1.0 + 1e-6, worst
+    assert worst > 0.05, worst    # the scale is not loose by orders of magnitude
