@@ -672,6 +672,18 @@ def run_calpa_study(args):
           "pass2_metric": timed(lambda: ctx.calpa_metric(c, g, metric=q)),
           "pass3_steered": timed(lambda: ctx.reconstruct_steered(0, p, c, raws, q, out=ada)),
           "adaptive_one_call": timed(lambda: ctx.reconstruct_adaptive(0, p, c, raws, out=ada))}
+    # end to end from pinned host buffers (copies in, three passes, copies out, inside the timing)
+    raws_h = [pinned(s.raw) for s in fr.sensors]
+    out_h = pinned(np.zeros((3, p.out_h, p.out_w), np.float32))
+    ctx.reconstruct_adaptive_host(0, p, c, raws_h, out_h)
+    e2e_ms = []
+    for _ in range(5):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.reconstruct_adaptive_host(0, p, c, raws_h, out_h)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    ms["adaptive_host_buffers_e2e"] = float(np.median(e2e_ms))
     qn = q.cpu().numpy().astype(np.float64)
     area = 1.0 / np.sqrt(np.maximum(qn[..., 0] * qn[..., 2] - qn[..., 1] ** 2, 1e-12))
     flops = algorithmic_flops(p, fr.sensors, ch_ada.cpu().numpy(), area=area, per_pair=FLOPS_PER_PAIR[p.order] + 5)
@@ -715,7 +727,9 @@ def run_calpa_study(args):
                       "calpa": {k: getattr(c, k) for k, _ in c._fields_},
                       "ms": {k: round(v, 3) for k, v in ms.items()},
                       "mpx_s": {"isotropic": round(p.out_w * p.out_h / ms["isotropic"] / 1e3, 1),
-                                "adaptive_one_call": round(p.out_w * p.out_h / ms["adaptive_one_call"] / 1e3, 1)},
+                                "adaptive_one_call": round(p.out_w * p.out_h / ms["adaptive_one_call"] / 1e3, 1),
+                                "adaptive_host_buffers_e2e": round(p.out_w * p.out_h / ms["adaptive_host_buffers_e2e"]
+                                                                   / 1e3, 1)},
                       "mean_window_area_factor": round(float(area.mean()), 3),
                       "roofline_pass3": {"bound": "alu", "achieved": round(tf, 2), "peak": round(peak, 1),
                                          "unit": "TFLOP/s", "frac": round(tf / peak, 3)},

@@ -375,6 +375,14 @@ hdr_status hdr_reconstruct_adaptive(hdr_ctx *ctx, int32_t rig_id, const hdr_para
                                     const hdr_calpa_params *calpa, const uint16_t *const *raw_dev, void *out_dev,
                                     uint8_t *choice_dev, void *cuda_stream);
 
+/* hdr_reconstruct_adaptive from HOST buffers: copies raw_host[s] ([height][pitch_elems]) into the
+ * context's staging, runs the three passes, copies the output (and choice when non-NULL) back to
+ * out_host and waits. Copies and passes run in order on `cuda_stream` (pinned host buffers make the
+ * copies asynchronous to the host). */
+hdr_status hdr_reconstruct_adaptive_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                                         const hdr_calpa_params *calpa, const uint16_t *const *raw_host,
+                                         void *out_host, uint8_t *choice_host, void *cuda_stream);
+
 /* Size of the fixed device array that hdr_reconstruct_noalloc uses as scratch. */
 #define HDR_NOALLOC_SCRATCH_BYTES (4u << 20)
 

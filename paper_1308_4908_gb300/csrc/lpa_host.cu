@@ -670,13 +670,14 @@ hdr_status hdr_reconstruct_levels(hdr_ctx *ctx, int32_t rig_id, const hdr_params
   return reconstruct_impl(ctx, rig_id, params, raw_dev, out_dev, choice_dev, levels_dev, cuda_stream);
 }
 
-hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_host,
-                                void *out_host, uint8_t *choice_host, void *cuda_stream) {
-  hdr_status st = common_checks(ctx, rig_id, params, raw_host, out_host);
-  if (st) return st;
-  cudaStream_t stream = (cudaStream_t)cuda_stream;
-  const Rig &rig = ctx->rigs[rig_id];
-  const uint16_t *raw_dev[HDR_MAX_SENSORS];
+}  // extern "C"
+
+namespace {
+
+// Device staging of the host-buffer entry points, grown on demand (growing waits for `stream`):
+// one raw frame per sensor, the output planes and, when asked for, the level map.
+hdr_status ensure_host_staging(hdr_ctx *ctx, const Rig &rig, const hdr_params *params, const uint16_t *const *raw_host,
+                               bool want_choice, cudaStream_t stream, const uint16_t **raw_dev) {
   for (int s = 0; s < rig.n; s++) {
     if (!raw_host[s]) return fail(HDR_E_INVALID, "raw_host[%d] is NULL", s);
     const size_t bytes = (size_t)rig.s[s].d.pitch_elems * rig.s[s].d.height * 2;
@@ -690,10 +691,8 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
     }
     raw_dev[s] = ctx->raw_stage[s];
   }
-  const size_t plane = (size_t)params->out_w * params->out_h;
-  const size_t npx = plane * 3;
-  const size_t esize = params->out_dtype ? 2 : 4;
-  const size_t obytes = npx * esize;
+  const size_t npx = (size_t)params->out_w * params->out_h * 3;
+  const size_t obytes = npx * (params->out_dtype ? 2 : 4);
   if (ctx->out_cap < obytes) {
     CUDA_TRY(cudaStreamSynchronize(stream));
     cudaFree(ctx->out_stage);
@@ -702,7 +701,7 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
     CUDA_TRY(cudaMalloc(&ctx->out_stage, obytes));
     ctx->out_cap = obytes;
   }
-  if (choice_host && ctx->choice_cap < npx) {
+  if (want_choice && ctx->choice_cap < npx) {
     CUDA_TRY(cudaStreamSynchronize(stream));
     cudaFree(ctx->choice_stage);
     ctx->choice_stage = nullptr;
@@ -710,6 +709,50 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
     CUDA_TRY(cudaMalloc(&ctx->choice_stage, npx));
     ctx->choice_cap = npx;
   }
+  return HDR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hdr_status hdr_reconstruct_adaptive_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
+                                         const hdr_calpa_params *calpa, const uint16_t *const *raw_host,
+                                         void *out_host, uint8_t *choice_host, void *cuda_stream) {
+  hdr_status st = common_checks(ctx, rig_id, params, raw_host, out_host);
+  if (st) return st;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const Rig &rig = ctx->rigs[rig_id];
+  const uint16_t *raw_dev[HDR_MAX_SENSORS];
+  st = ensure_host_staging(ctx, rig, params, raw_host, choice_host != nullptr, stream, raw_dev);
+  if (st) return st;
+  for (int s = 0; s < rig.n; s++)
+    CUDA_TRY(cudaMemcpyAsync(ctx->raw_stage[s], raw_host[s], (size_t)rig.s[s].d.pitch_elems * rig.s[s].d.height * 2,
+                             cudaMemcpyHostToDevice, stream));
+  st = hdr_reconstruct_adaptive(ctx, rig_id, params, calpa, raw_dev, ctx->out_stage,
+                                choice_host ? ctx->choice_stage : nullptr, cuda_stream);
+  if (st) return st;
+  const size_t npx = (size_t)params->out_w * params->out_h * 3;
+  if (npx) {
+    CUDA_TRY(cudaMemcpyAsync(out_host, ctx->out_stage, npx * (params->out_dtype ? 2 : 4), cudaMemcpyDeviceToHost,
+                             stream));
+    if (choice_host) CUDA_TRY(cudaMemcpyAsync(choice_host, ctx->choice_stage, npx, cudaMemcpyDeviceToHost, stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  return HDR_OK;
+}
+
+hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_host,
+                                void *out_host, uint8_t *choice_host, void *cuda_stream) {
+  hdr_status st = common_checks(ctx, rig_id, params, raw_host, out_host);
+  if (st) return st;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const Rig &rig = ctx->rigs[rig_id];
+  const uint16_t *raw_dev[HDR_MAX_SENSORS];
+  st = ensure_host_staging(ctx, rig, params, raw_host, choice_host != nullptr, stream, raw_dev);
+  if (st) return st;
+  const size_t plane = (size_t)params->out_w * params->out_h;
+  const size_t esize = params->out_dtype ? 2 : 4;
   LpaLaunch L;
   st = plan(ctx, rig, params, raw_dev, L);
   if (st) return st;

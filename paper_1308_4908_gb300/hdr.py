@@ -139,13 +139,15 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.hdr_calpa_metric.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]
     lib.hdr_reconstruct_steered.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P]
     lib.hdr_reconstruct_adaptive.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
+    lib.hdr_reconstruct_adaptive_host.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P]
     lib.hdr_last_error.argtypes = []
     lib.hdr_last_error.restype = ctypes.c_char_p
     for name in ("hdr_create", "hdr_set_rig", "hdr_reconstruct", "hdr_reconstruct_levels", "hdr_reconstruct_host",
                  "hdr_check", "hdr_reconstruct_noalloc", "hdr_reconstruct_batch", "hdr_tune_batch",
                  "hdr_server_create", "hdr_submit", "hdr_poll", "hdr_server_stats_get", "hdr_selftest_timeout",
                  "hdr_calib_stack_stats", "hdr_calib_gain", "hdr_calib_exposure", "hdr_calpa_gradients",
-                 "hdr_calpa_metric", "hdr_reconstruct_steered", "hdr_reconstruct_adaptive"):
+                 "hdr_calpa_metric", "hdr_reconstruct_steered", "hdr_reconstruct_adaptive",
+                 "hdr_reconstruct_adaptive_host"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -280,6 +282,14 @@ def hdr_reconstruct_adaptive(ctx: int, rig_id: int, params: hdr_params, calpa: h
     _check(load().hdr_reconstruct_adaptive(ctypes.c_void_p(ctx), int(rig_id), ctypes.byref(params),
                                            ctypes.byref(calpa), _ptr_array(raw_dev), ctypes.c_void_p(out_dev),
                                            ctypes.c_void_p(choice_dev), ctypes.c_void_p(stream)))
+
+
+def hdr_reconstruct_adaptive_host(ctx: int, rig_id: int, params: hdr_params, calpa: hdr_calpa_params,
+                                  raw_host: Sequence[int], out_host: int, choice_host: Optional[int] = None,
+                                  stream: Optional[int] = None) -> None:
+    _check(load().hdr_reconstruct_adaptive_host(ctypes.c_void_p(ctx), int(rig_id), ctypes.byref(params),
+                                                ctypes.byref(calpa), _ptr_array(raw_host), ctypes.c_void_p(out_host),
+                                                ctypes.c_void_p(choice_host), ctypes.c_void_p(stream)))
 
 
 def hdr_last_error() -> str:
@@ -517,6 +527,16 @@ class Context:
         hdr_reconstruct_adaptive(self.handle, rig_id, hp, calpa, [int(r.data_ptr()) for r in raws], out.data_ptr(),
                                  choice.data_ptr() if choice is not None else None, self._stream(stream))
         return out
+
+    def reconstruct_adaptive_host(self, rig_id: int, params, calpa: hdr_calpa_params,
+                                  raws_host: Sequence[np.ndarray], out_host: np.ndarray,
+                                  choice_host: Optional[np.ndarray] = None, stream=None):
+        """The three passes from host buffers (numpy arrays; pinned ones copy asynchronously)."""
+        hp = params if isinstance(params, hdr_params) else params_struct(params)
+        hdr_reconstruct_adaptive_host(self.handle, rig_id, hp, calpa, [int(r.ctypes.data) for r in raws_host],
+                                      out_host.ctypes.data, choice_host.ctypes.data if choice_host is not None else None,
+                                      self._stream(stream))
+        return out_host
 
     # ---------------------------------------------------------------- calibration (Section 6.2)
     def calib_stack_stats(self, frames, width: int, stream=None):

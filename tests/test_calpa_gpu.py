@@ -143,6 +143,13 @@ def test_adaptive_entry_point_is_the_three_passes(ctx, small, small_run):
     ctx.check()
     np.testing.assert_array_equal(out2.cpu().numpy(), out)
     np.testing.assert_array_equal(ch2.cpu().numpy(), ch)
+    # the host-buffer entry point: same bits
+    out3 = np.full((3, p.out_h, p.out_w), -7.0, np.float32)
+    ch3 = np.zeros((3, p.out_h, p.out_w), np.uint8)
+    ctx.reconstruct_adaptive_host(0, p, c, [np.ascontiguousarray(s.raw) for s in small.sensors], out3, ch3)
+    ctx.check()
+    np.testing.assert_array_equal(out3, out)
+    np.testing.assert_array_equal(ch3, ch)
 
 
 @pytest.mark.parametrize("order", [0, 1])
