@@ -298,6 +298,7 @@ def run_batching(ctx, frames, dev, reps: int = 10):
             hdr.hdr_reconstruct(ctx.handle, rig, hp, ptrs, out.data_ptr(), None, stream.cuda_stream)
 
     t_batch = timed(lambda: ctx.reconstruct_batch(hf, None, stream))
+    t_forms = [timed(lambda f=f: ctx.reconstruct_batch(hf, hdr.hdr_batch_config(16, 0, 1, f), stream)) for f in (0, 1)]
     t_plain = timed(plain)
     return {"workload": "batching: 16 frames, raw sizes from {512^2, 1280x720, 1920x1080, 2048^2}, 2-4 sensors "
                         "(ND 1, 1/8, 1/64, 1/512), order 0-2, output 1x or 1.5x, 4 scales with ICI",
@@ -306,6 +307,8 @@ def run_batching(ctx, frames, dev, reps: int = 10):
                         "config": {"form": ("graph of per-frame grids", "persistent per-order kernels")[best.form],
                                    "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm,
                                    "cost_order": best.cost_order}},
+            "forms_ms": {"graph of per-frame grids (16-row tiles)": round(t_forms[0], 3),
+                         "persistent per-order kernels (16-row tiles, as many CTAs as fit)": round(t_forms[1], 3)},
             "per_frame": {"ms": round(t_plain, 3), "mpx_s": round(px / t_plain / 1e3, 1), "gpu_launches": len(frames)},
             "speedup": round(t_plain / t_batch, 3), "l2": "flushed between timed repetitions"}
 
