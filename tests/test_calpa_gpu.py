@@ -265,3 +265,20 @@ def test_metric_with_a_gradient_unit(ctx, small_run):
     ctx.check()
     check_metric(q, oracle.steering_metric(g.astype(np.float64), c.window_sigma, c.alpha, c.lambda1, c.lambda2,
                                            c.min_eig, c.max_eig, c.grad_scale))
+
+
+def test_four_sensors_and_an_upsampled_output(ctx):
+    """A 4-sensor rig (ND 1 .. 1/512) reconstructed 1.5x upsampled with steered windows, order 2,
+    against the oracle on every pixel."""
+    fr = synth.batching_frame((1004, 99, 4, 64, 48, 2, 1.5))
+    p = fr.params
+    c = _calpa()
+    g, q, out, ch = _passes(ctx, fr, c)
+    check_gradients(fr, p, c, g)
+    check_metric(q, oracle.steering_metric(g.astype(np.float64), c.window_sigma, c.alpha, c.lambda1, c.lambda2,
+                                           c.min_eig, c.max_eig, c.grad_scale))
+    vv, uu = np.mgrid[0:p.out_h, 0:p.out_w]
+    pix = np.stack([uu.ravel(), vv.ravel()], axis=1)
+    o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True, metric=q.astype(np.float64))
+    parity.compare(out[:, pix[:, 1], pix[:, 0]], ch[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
+                   p.ici_gamma, p.min_pivot)

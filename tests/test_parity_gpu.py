@@ -350,6 +350,12 @@ def test_invalid_arguments_are_rejected(ctx):
     ctx.check()
 
 
+def test_printed_noise_weight_with_compensated_sums(ctx):
+    """weight_mode 1 with compensated moment sums (its own instantiation), order 2, every pixel."""
+    fr = synth.paper_scale(size=64, seed=1074)
+    check_frame(ctx, fr, dataclasses.replace(fr.params, weight_mode=1, accum=1))
+
+
 @pytest.mark.parametrize("order", [0, 1, 2])
 def test_printed_noise_weight(ctx, order):
     """weight_mode 1, the noise weight K / s as printed in Section 5.2 (Var C_0 with w^2 s2 = K^2),
