@@ -189,3 +189,19 @@ def test_empty_and_tiny_outputs(ctx, streams):
         srv.close()
     ref = _plain(ctx, 0, dataclasses.replace(fr, params=p1))
     np.testing.assert_array_equal(one, ref[0])
+
+
+def test_translational_frames_use_their_tables_in_the_mix(ctx, streams):
+    """Frames whose rigs are pure translations at 1x output read tabulated weights (Section 8) in
+    the serving steps as in a plain launch: served alone, in a mix with other streams, and by
+    hdr_reconstruct, the same bits."""
+    from tests.test_parity_gpu import translational
+    tr = [translational(80, 1090 + k, [(0.0, 0.0), (0.4 * k, -0.3), (-1.2, 0.7 * k)]) for k in range(2)]
+    for k, fr in enumerate(tr):
+        ctx.set_rig(40 + k, fr.sensors)
+    items = [(40 + k, fr) for k, fr in enumerate(tr)] + [(m, streams[m][0]) for m in (0, 3)]
+    mixed, _ = _serve(ctx, items, step_tiles=64)
+    for (rig, fr), (out, ch, r) in zip(items, mixed):
+        ref = _plain(ctx, rig, fr)
+        np.testing.assert_array_equal(out, ref[0])
+        np.testing.assert_array_equal(ch, ref[1])

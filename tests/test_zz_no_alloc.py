@@ -66,11 +66,16 @@ def _within_tolerance(ref, ref_choice, out, choice):
     assert np.all(np.abs(out[fin] - ref[fin]) <= tol)
 
 
+def _printed_weight_rig():
+    fr = _scalar_rig()
+    return synth.Frame(fr.sensors, dataclasses.replace(fr.params, weight_mode=1), fr.scene)
+
+
 def test_noalloc_matches_context_entry_point_twice():
     from paper_1308_4908_gb300 import hdr
     ctx = hdr.Context(0)
     try:
-        for fr in (_frames_rig(), _scalar_rig()):
+        for fr in (_frames_rig(), _scalar_rig(), _printed_weight_rig()):
             _within_tolerance(*_run_both(hdr, ctx, fr))
     finally:
         ctx.close()
