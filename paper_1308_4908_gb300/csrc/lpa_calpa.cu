@@ -37,7 +37,9 @@ __global__ void __launch_bounds__(kBX *kBY) calpa_metric(const __grid_constant__
   constexpr int kTile = (kBY + 2 * kRmax) * (kBX + 2 * kRmax);
   __shared__ double sxx[kTile], sxy[kTile], syy[kTile];
   const int r = A.r, TW = kBX + 2 * r, TH = kBY + 2 * r;
-  const int bx0 = blockIdx.x * kBX, by0 = blockIdx.y * kBY;
+  // one-dimensional grid over the 32 x 8 blocks (any output height)
+  const int nbx = (A.W + kBX - 1) / kBX;
+  const int bx0 = (int)(blockIdx.x % nbx) * kBX, by0 = (int)(blockIdx.x / nbx) * kBY;
   const int tid = threadIdx.y * kBX + threadIdx.x;
   for (int e = tid; e < TW * TH; e += kBX * kBY) {
     const int X = bx0 - r + e % TW, Y = by0 - r + e / TW;
@@ -176,7 +178,8 @@ hdr_status hdr_calpa_metric(hdr_ctx *ctx, int32_t out_w, int32_t out_h, const hd
   A.lambda2 = (float)calpa->lambda2;
   A.min_eig = (float)calpa->min_eig;
   A.max_eig = (float)calpa->max_eig;
-  calpa_metric<<<dim3((out_w + kBX - 1) / kBX, (out_h + kBY - 1) / kBY), dim3(kBX, kBY), 0,
+  const unsigned blocks = (unsigned)(((long long)out_w + kBX - 1) / kBX * (((long long)out_h + kBY - 1) / kBY));
+  calpa_metric<<<blocks, dim3(kBX, kBY), 0,
                  (cudaStream_t)cuda_stream>>>(A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return lpa_fail(HDR_E_CUDA, cudaGetErrorString(e));

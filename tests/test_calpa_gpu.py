@@ -282,3 +282,16 @@ def test_four_sensors_and_an_upsampled_output(ctx):
     o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True, metric=q.astype(np.float64))
     parity.compare(out[:, pix[:, 1], pix[:, 0]], ch[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
                    p.ici_gamma, p.min_pivot)
+
+
+def test_metric_of_a_tall_thin_output(ctx):
+    """An output of one column and 600000 rows (more block rows than a grid's second dimension
+    allows): the matrix pass against the oracle."""
+    r = np.random.default_rng(21)
+    g = r.normal(0.0, 20.0, (600000, 1, 2)).astype(np.float32)
+    g[::97, 0, 0] += 300.0
+    c = _calpa()
+    q = ctx.calpa_metric(c, torch.from_numpy(g).cuda()).cpu().numpy()
+    ctx.check()
+    check_metric(q, oracle.steering_metric(g.astype(np.float64), c.window_sigma, c.alpha, c.lambda1, c.lambda2,
+                                           c.min_eig, c.max_eig, c.grad_scale))
