@@ -115,6 +115,7 @@ struct PlanCache {
   // the inputs a table is built from (sensor count, scales, window constants, each sensor's
   // translation) -> the device table, so that a repeated configuration skips the host build
   std::map<std::vector<double>, void *> by_inputs;
+  uint64_t epoch = 0;  // bumped when the device tables are freed (plans holding them are stale)
 };
 
 struct hdr_ctx {
@@ -137,6 +138,10 @@ struct hdr_ctx {
   // gradient and steering-matrix planes of the adaptive reconstruction
   void *calpa = nullptr;
   size_t calpa_cap = 0;
+  // launch plans of single-frame calls by (rig, rig generation, parameters, raw pointers): a
+  // repeated call skips the planning; hdr_set_rig bumps the rig's generation
+  uint64_t rig_gen[kMaxRigs] = {};
+  std::map<std::vector<uint8_t>, LpaLaunch> plans;
 };
 
 namespace {
@@ -341,6 +346,7 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
       for (auto &t : env.tabs->dev) cudaFree(t.second);
       env.tabs->dev.clear();
       env.tabs->by_inputs.clear();
+      env.tabs->epoch++;
     }
     void *d = nullptr;
     CUDA_TRY(cudaMalloc(&d, std::max<size_t>(nb, 16)));
@@ -487,6 +493,34 @@ hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_
   return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, tabulate}, rig, p, raw, L, 16, reach);
 }
 
+// plan() of a single-frame call through the context's plan cache.
+hdr_status cached_plan(hdr_ctx *ctx, int32_t rig_id, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
+                       bool tabulate) {
+  const Rig &rig = ctx->rigs[rig_id];
+  std::vector<uint8_t> key(sizeof(int32_t) + 2 * sizeof(uint64_t) + sizeof(hdr_params) + 1 + rig.n * sizeof(void *));
+  uint8_t *k = key.data();
+  memcpy(k, &rig_id, sizeof(int32_t));
+  k += sizeof(int32_t);
+  memcpy(k, &ctx->rig_gen[rig_id], sizeof(uint64_t));
+  k += sizeof(uint64_t);
+  memcpy(k, &ctx->tabs.epoch, sizeof(uint64_t));  // tables the plan points at are still allocated
+  k += sizeof(uint64_t);
+  memcpy(k, p, sizeof(hdr_params));
+  k += sizeof(hdr_params);
+  *k++ = tabulate ? 1 : 0;
+  memcpy(k, raw, rig.n * sizeof(void *));
+  auto it = ctx->plans.find(key);
+  if (it != ctx->plans.end()) {
+    L = it->second;
+    return HDR_OK;
+  }
+  hdr_status st = plan(ctx, rig, p, raw, L, 1.0, tabulate);
+  if (st) return st;
+  if (ctx->plans.size() >= 256) ctx->plans.clear();
+  ctx->plans.emplace(std::move(key), L);
+  return HDR_OK;
+}
+
 hdr_status launch(const LpaLaunch &L, int accum, bool diag, cudaStream_t st) {
   if (L.tiles_x == 0 || L.tiles_y == 0) return HDR_OK;
   cudaError_t e;
@@ -519,7 +553,7 @@ hdr_status reconstruct_impl(hdr_ctx *ctx, int32_t rig_id, const hdr_params *para
     return fail(HDR_E_UNSUPPORTED, "the level maps are computed with the inverse-variance weight (weight_mode 0)");
   LpaLaunch L;
   // the diagnostic (level maps) kernel searches every window
-  st = plan(ctx, ctx->rigs[rig_id], params, raw_dev, L, 1.0, levels_dev == nullptr);
+  st = cached_plan(ctx, rig_id, params, raw_dev, L, levels_dev == nullptr);
   if (st) return st;
   L.out = out_dev;
   L.choice = choice_dev;
@@ -655,6 +689,7 @@ hdr_status hdr_set_rig(hdr_ctx *ctx, int32_t rig_id, int32_t n_sensors, const hd
   rig = fresh;
   for (int s = 0; s < n_sensors; s++) fresh.s[s] = RigSensor();   // ownership moved
   fresh.n = 0;
+  ctx->rig_gen[rig_id]++;  // plans made for the previous rig no longer match
   return HDR_OK;
 }
 
@@ -754,7 +789,7 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
   const size_t plane = (size_t)params->out_w * params->out_h;
   const size_t esize = params->out_dtype ? 2 : 4;
   LpaLaunch L;
-  st = plan(ctx, rig, params, raw_dev, L);
+  st = cached_plan(ctx, rig_id, params, raw_dev, L, true);
   if (st) return st;
   L.out = ctx->out_stage;
   L.choice = choice_host ? ctx->choice_stage : nullptr;
