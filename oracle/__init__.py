@@ -81,6 +81,8 @@ def _load():
         lib.orc_equivalent_kernel.argtypes = [P, ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_int32, ctypes.c_int32] + [P] * 7
         lib.orc_equivalent_kernel.restype = ctypes.c_int
+        lib.orc_condition.argtypes = [P, ctypes.c_int32]
+        lib.orc_condition.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -285,6 +287,15 @@ def steering_metric(grad: np.ndarray, window_sigma: float, alpha: float, lambda1
     C12 = (ea - eb) * ux * uy
     C22 = ea * uy * uy + eb * ux * ux
     return np.stack([C11, C12, C22], axis=2)
+
+
+def condition(A: np.ndarray) -> float:
+    """2-norm condition number max|lambda| / min|lambda| of a symmetric matrix (at most 6 x 6) by the
+    oracle's cyclic Jacobi eigen-iteration (the routine behind the `kappa` diagnostics)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("square matrix expected")
+    return float(_load().orc_condition(_ptr(A), A.shape[0]))
 
 
 def radiometry(y, b, g, t, a, n, read_var, sat):

@@ -220,6 +220,13 @@ static double jacobi_condition(const double *Ain, int P) {
   return lo > 0.0 ? hi / lo : INFINITY;
 }
 
+/* The same condition number for a caller-supplied symmetric P x P matrix (row-major, P <= 6), so
+ * that the tests can check the eigen-iteration on matrices whose spectrum is known. */
+double orc_condition(const double *A, int32_t P) {
+  if (!A || P < 1 || P > ORC_MAX_P) return NAN;
+  return jacobi_condition(A, P);
+}
+
 /* Result of one weighted fit (one channel, one scale, one order). */
 typedef struct {
   int count;         /* samples inside the window */
