@@ -404,6 +404,8 @@ def run_serving(ctx, frames, dev, seconds: float, step_tiles: int):
         "served": {"mpx_s": round(st.output_pixels / wall / 1e6, 1), "p50_ms": round(st.p50_ms, 2),
                    "p99_ms": round(st.p99_ms, 2), "max_ms": round(st.max_ms, 2),
                    "mean_queue_ms": round(st.mean_queue_ms, 3), "steps": int(st.steps), "completed": int(st.completed),
+                   "gpu_step_ms_total": round(st.gpu_step_ms, 1), "gpu_gap_ms_total": round(st.gpu_gap_ms, 1),
+                   "host_step_ms": {"mean": round(st.host_step_ms_mean, 3), "max": round(st.host_step_ms_max, 3)},
                    "config": cfg},
         "plain_per_frame": {"mpx_s": round(sum(px[m] for _, m in sched) / pwall / 1e6, 1),
                             "p50_ms": round(_pct(lat, 50), 2), "p99_ms": round(_pct(lat, 99), 2),
@@ -487,6 +489,174 @@ def run_precision_study(args):
                       f"{2 * args.size}^2 output, sigma 0.7, orders 0 and 2",
                       "error": "|gpu - oracle| / max(|oracle|, 1e-2) on pixels whose level choice matches",
                       "sample_pixels": n_pix, "rows": rows}), flush=True)
+
+
+def _error_terms(g, gc, o, tau: float = 1e-2):
+    """Per pixel-channel: relative error of GPU values g [n, 3] with level choices gc [n, 3] (255:
+    none) against the oracle o (levels and kappa) - where the GPU took another (admissible) level,
+    against the oracle's estimate at that level - with the condition number at the level used,
+    the error in units of FP32 rounding of the terms (|g - o| / (2^-24 (efit + ew)), the oracle's
+    rounding scales of that fit), and flags for finite values and level mismatches."""
+    gc = gc.astype(np.int64)
+    gc[gc == 255] = -1
+    och = o["choice"]
+    used = np.where(gc >= 0, gc, np.maximum(och, 0))
+    at = np.take_along_axis(o["c0"], used[..., None], axis=2)[..., 0]
+    ref = np.where((gc != och) & (gc >= 0), at, o["out"])
+    kap = np.take_along_axis(o["kappa"], used[..., None], axis=2)[..., 0]
+    efit = np.take_along_axis(o["efit"], used[..., None], axis=2)[..., 0]
+    ew = np.take_along_axis(o["ew"], used[..., None], axis=2)[..., 0]
+    return {"rel": np.abs(g - ref) / np.maximum(np.abs(ref), tau),
+            "u": np.abs(g - ref) / (2.0 ** -24 * (efit + ew) + 1e-300), "kappa": kap,
+            "fin": np.isfinite(ref) & np.isfinite(g), "nan_mismatch": np.isfinite(ref) != np.isfinite(g),
+            "mismatch": gc != och}
+
+
+def error_stats(parts):
+    """Summary of one or more (g, gc, oracle) triples (see _error_terms): max, median, p99 relative
+    error, the fraction above 1e-5, the error in units of FP32 rounding of the terms, level
+    mismatches, all bucketed by the condition number of the equilibrated normal matrix."""
+    t = [_error_terms(*pt) for pt in parts]
+    cat = {k: np.concatenate([x[k].ravel() for x in t]) for k in t[0]}
+    fin = cat["fin"]
+
+    def summary(m):
+        rel, u = cat["rel"][m], cat["u"][m]
+        if rel.size == 0:
+            return {"n": 0}
+        return {"n": int(rel.size), "max": float(rel.max()), "median": float(np.median(rel)),
+                "p99": float(np.percentile(rel, 99)), "frac_above_1e-5": float((rel > 1e-5).mean()),
+                "u_of_terms_max": float(u.max()), "u_of_terms_median": float(np.median(u))}
+    out = summary(fin)
+    out["level_mismatch_frac"] = float(cat["mismatch"].mean())
+    out["nan_mismatch"] = int(cat["nan_mismatch"].sum())
+    kap = cat["kappa"]
+    out["by_kappa"] = {f"{lo:.0e}-{hi:.0e}": summary(fin & (kap >= lo) & (kap < hi))
+                       for lo, hi in ((1, 1e2), (1e2, 1e4), (1e4, 1e6), (1e6, np.inf))}
+    return out
+
+
+def _sample(p, n, seed, border=True):
+    r = np.random.default_rng(seed)
+    pix = [np.stack([r.integers(0, p.out_w, n), r.integers(0, p.out_h, n)], axis=1)]
+    if border and p.out_w > 2 and p.out_h > 2:
+        k = max(n // 16, 1)
+        xs, ys = r.integers(0, p.out_w, k), r.integers(0, p.out_h, k)
+        pix += [np.stack([xs, np.zeros(k, int)], 1), np.stack([xs, np.full(k, p.out_h - 1)], 1),
+                np.stack([np.zeros(k, int), ys], 1), np.stack([np.full(k, p.out_w - 1), ys], 1)]
+    return np.concatenate(pix)
+
+
+def run_error_study(args):
+    """The error of every configuration against the FP64 oracle on sampled pixels (random pixels
+    plus the four borders): the paper-scale frame in the benchmark's launch, the precision frame
+    (FP32 and FP16 output), the 16-frame batch in one batched launch, one frame of each of the 8
+    serving streams submitted together to the request loop, and the adaptive reconstruction (its
+    steered pass against the oracle with the GPU's steering matrices). Beside them, the oracle
+    itself on inputs rounded to FP32 (Eq. 18's f and Eq. 20's s2) against the oracle on FP64
+    inputs: what exact arithmetic starting from FP32 inputs would reach. One JSON line."""
+    import dataclasses
+    import torch
+    import oracle
+    from paper_1308_4908_gb300 import hdr, synth
+    oracle.build()
+    n = args.study_pixels
+    res = {}
+    ctx = hdr.Context(0)
+
+    def gpu_frame(fr, p, rig=0):
+        ctx.set_rig(rig, fr.sensors)
+        raws = [torch.from_numpy(s.raw).cuda() for s in fr.sensors]
+        ch = torch.empty((3, p.out_h, p.out_w), dtype=torch.uint8, device="cuda")
+        out = ctx.reconstruct(rig, p, raws, choice=ch)
+        ctx.check()
+        return out.float().cpu().numpy(), ch.cpu().numpy()
+
+    def at(img, pix):
+        return img[:, pix[:, 1], pix[:, 0]].T
+
+    # configuration 2: the paper-scale frame, and the oracle on FP32-rounded inputs
+    fr = synth.paper_scale(size=args.size)
+    p = fr.params
+    pix = _sample(p, n, 1002)
+    o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True)
+    g, gc = gpu_frame(fr, p)
+    res["paper_scale"] = error_stats([(at(g, pix), at(gc, pix), o)])
+    o32 = oracle.reconstruct(oracle.value_sensors(fr.sensors, round_to=np.float32), p, pix)
+    res["paper_scale_oracle_on_fp32_inputs"] = error_stats([(o32["out"], np.where(o32["choice"] < 0, 255,
+                                                                                o32["choice"]), o)])
+    print(json.dumps({"paper_scale": res["paper_scale"]}), file=sys.stderr, flush=True)
+    # configuration 3: the precision frame (2x upsampled), orders 0 and 2, FP32 and FP16 output
+    for order in (0, 2):
+        fr = synth.precision(size=args.size, order=order)
+        pix = _sample(fr.params, n, 1003 + order)
+        o = oracle.reconstruct(fr.sensors, fr.params, pix, levels=True, kappa=True)
+        for dt in (0, 1):
+            p = dataclasses.replace(fr.params, out_dtype=dt)
+            g, gc = gpu_frame(fr, p)
+            res[f"precision_m{order}_{'fp16' if dt else 'fp32'}"] = error_stats([(at(g, pix), at(gc, pix), o)])
+        o32 = oracle.reconstruct(oracle.value_sensors(fr.sensors, round_to=np.float32), fr.params, pix)
+        res[f"precision_m{order}_oracle_on_fp32_inputs"] = error_stats(
+            [(o32["out"], np.where(o32["choice"] < 0, 255, o32["choice"]), o)])
+    # configuration 4: the 16-frame batch in one batched launch (the tuned form)
+    frames = make_frames([("batch", sp) for sp in synth.batching_specs()])
+    keep, hf, outs = [], [], []
+    for k, f in enumerate(frames):
+        ctx.set_rig(16 + k, f.sensors)
+        raws = [torch.from_numpy(s.raw).cuda() for s in f.sensors]
+        keep.append(raws)
+        out = torch.empty((3, f.params.out_h, f.params.out_w), device="cuda")
+        ch = torch.empty((3, f.params.out_h, f.params.out_w), dtype=torch.uint8, device="cuda")
+        outs.append((out, ch))
+        hf.append(ctx.frame(16 + k, f.params, raws, out, ch, keep))
+    cfg = ctx.tune_batch(hf)
+    ctx.reconstruct_batch(hf, cfg)
+    ctx.check()
+    parts = []
+    for k, (f, (out, ch)) in enumerate(zip(frames, outs)):
+        pix = _sample(f.params, max(n // 16, 64), 1004 + k)
+        parts.append((at(out.cpu().numpy(), pix), at(ch.cpu().numpy(), pix),
+                      oracle.reconstruct(f.sensors, f.params, pix, levels=True, kappa=True)))
+    res["batching"] = error_stats(parts)
+    res["batching"]["config"] = {"form": int(cfg.form), "tile_h": int(cfg.tile_h)}
+    del keep, outs
+    # configuration 5: one frame of each serving stream, submitted together to the request loop
+    sframes = make_frames([("serve", m) for m in range(8)])
+    srv = hdr.Server(ctx, max_frames=48, pool_bytes=6 << 30, step_tiles=args.step_tiles)
+    tickets, held = [], []
+    for m, f in enumerate(sframes):
+        ctx.set_rig(8 + m, f.sensors)
+        raws = [pinned(s.raw) for s in f.sensors]
+        out = pinned(np.zeros((3, f.params.out_h, f.params.out_w), np.float32))
+        ch = pinned(np.zeros((3, f.params.out_h, f.params.out_w), np.uint8))
+        held.append((raws, out, ch))
+        tickets.append(srv.submit(8 + m, f.params, raws, out, ch, stream_id=m))
+    for t in tickets:
+        srv.poll(t, -1)
+    srv.close()
+    parts = []
+    for m, (f, (_, out, ch)) in enumerate(zip(sframes, held)):
+        pix = _sample(f.params, max(n // 8, 64), 1005 + m)
+        parts.append((at(out, pix), at(ch, pix), oracle.reconstruct(f.sensors, f.params, pix, levels=True,
+                                                                     kappa=True)))
+    res["serving_mix"] = error_stats(parts)
+    # adaptive windows: the steered pass against the oracle with the GPU's steering matrices
+    fr = synth.paper_scale(size=args.size)
+    p = fr.params
+    c = hdr.hdr_calpa_params_default()
+    ctx.set_rig(0, fr.sensors)
+    raws = [torch.from_numpy(s.raw).cuda() for s in fr.sensors]
+    q = ctx.calpa_metric(c, ctx.calpa_gradients(0, p, c, raws))
+    ch = torch.empty((3, p.out_h, p.out_w), dtype=torch.uint8, device="cuda")
+    ada = ctx.reconstruct_steered(0, p, c, raws, q, choice=ch)
+    ctx.check()
+    pix = _sample(p, max(n // 4, 64), 1008)
+    o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True, metric=q.cpu().numpy().astype(np.float64))
+    res["adaptive_steered_pass"] = error_stats([(at(ada.cpu().numpy(), pix), at(ch.cpu().numpy(), pix), o)])
+    ctx.close()
+    print(json.dumps({"study": "error against the FP64 oracle", "workload": "every configuration (see keys)",
+                      "error": "|gpu - oracle| / max(|oracle|, 1e-2); sampled random and border pixels",
+                      "sample_pixels_per_config": n, "results": res}), flush=True)
 
 
 def run_tiny_study(args):
@@ -872,7 +1042,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--size", type=int, default=2048, help="raw and output edge (2048 = the paper-scale workload)")
     ap.add_argument("--headline-only", action="store_true", help="skip the batching and serving measurements")
-    ap.add_argument("--study", choices=["precision", "tiny", "tabweights", "calib", "calpa"], default=None,
+    ap.add_argument("--study", choices=["precision", "tiny", "tabweights", "calib", "calpa", "errors"], default=None,
                     help="print a study instead of the bench line")
     ap.add_argument("--study-pixels", type=int, default=20000)
     ap.add_argument("--calpa", default="", help="--study calpa: parameter overrides, e.g. min_eig=0.5,alpha=0.3")
@@ -881,6 +1051,9 @@ def main():
     args = ap.parse_args()
     if args.study == "precision":
         run_precision_study(args)
+        return
+    if args.study == "errors":
+        run_error_study(args)
         return
     if args.study == "tiny":
         run_tiny_study(args)

@@ -242,6 +242,13 @@ typedef struct {
   double mean_queue_ms;
   uint64_t steps, output_pixels;
   double busy_s;                    /* wall time between the first admission and the last completion */
+  double gpu_step_ms;               /* device time of the batched steps, summed (each from the start of
+                                       its first kernel to the end of its last)                   */
+  double gpu_gap_ms;                /* device time between the end of one step and the start of the
+                                       next, summed: the compute stream idles there               */
+  double host_step_ms_mean;         /* host time to build and launch one step (planning, graph
+                                       update, launch), mean and maximum                          */
+  double host_step_ms_max;
 } hdr_server_stats;
 
 /* Start a server on `ctx` (allocates the pool, streams and the scheduler thread). */

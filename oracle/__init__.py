@@ -81,6 +81,8 @@ def _load():
         lib.orc_equivalent_kernel.argtypes = [P, ctypes.c_int, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_int32, ctypes.c_int32] + [P] * 7
         lib.orc_equivalent_kernel.restype = ctypes.c_int
+        lib.orc_radiometry_frame.argtypes = [P, P, P]
+        lib.orc_radiometry_frame.restype = ctypes.c_int
         lib.orc_condition.argtypes = [P, ctypes.c_int32]
         lib.orc_condition.restype = ctypes.c_double
         _lib = lib
@@ -296,6 +298,46 @@ def condition(A: np.ndarray) -> float:
     if A.ndim != 2 or A.shape[0] != A.shape[1]:
         raise ValueError("square matrix expected")
     return float(_load().orc_condition(_ptr(A), A.shape[0]))
+
+
+class ValueSensor:
+    """A sensor in value mode: the radiant power estimate and its variance per pixel (excluded
+    pixels: variance +inf) with the sensor's transform."""
+
+    def __init__(self, width, height, affine, value_f, value_var):
+        self.width, self.height = int(width), int(height)
+        self.affine = np.asarray(affine, dtype=np.float64).reshape(2, 3)
+        self.value_f, self.value_var = value_f, value_var
+        self.gain = self.exposure = self.nd = self.read_var = 1.0
+        self.black, self.sat = 0.0, 1e300
+        self.bias_frame = self.prnu_frame = self.read_var_frame = self.sat_frame = None
+
+
+def value_sensors(sensors: Sequence, round_to=None) -> List[ValueSensor]:
+    """The value-mode sensors of raw sensors: Eq. 18's f and Eq. 20's s2 of every pixel (Section 6,
+    saturated pixels excluded). With `round_to` (e.g. np.float32) f and the inverse variance 1/s2
+    (the factor the weight uses) are rounded to that type: the inputs a lower-precision path
+    starts from."""
+    lib = _load()
+    out = []
+    for s in sensors:
+        m = _Marshal([s], _DefaultParams())
+        f = np.empty((s.height, s.width))
+        s2 = np.empty((s.height, s.width))
+        if lib.orc_radiometry_frame(ctypes.byref(m.arr), _ptr(f), _ptr(s2)) != 0:
+            raise ValueError("value_sensors needs raw sensors")
+        if round_to is not None:
+            f = f.astype(round_to).astype(np.float64)
+            with np.errstate(divide="ignore"):
+                iv = (1.0 / s2).astype(round_to).astype(np.float64)
+                s2 = np.where(iv > 0, 1.0 / iv, np.inf)
+        out.append(ValueSensor(s.width, s.height, s.affine, f, s2))
+    return out
+
+
+class _DefaultParams:
+    order, sigmas, green_ratio, trunc_k, ici_gamma, min_pivot = 0, (1.0,), 1.0, 3.0, 2.0, 1e-3
+    out_affine = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
 
 
 def radiometry(y, b, g, t, a, n, read_var, sat):

@@ -110,6 +110,28 @@ int orc_radiometry(double y, double b, double g, double t, double a, double n,
   return 0;
 }
 
+/* Eqs. 18 and 20 for every pixel of one sensor's raw frame (the sensor's scalar calibration or
+ * its per-pixel frames): f and s2 [height][width]; excluded (saturated) pixels get s2 = +inf. The
+ * value-mode inputs that reproduce the raw-mode fit exactly, or, rounded, the fit of rounded
+ * inputs. Returns 0, or -1 for a missing raw frame. */
+int orc_radiometry_frame(const orc_sensor *S, double *f, double *s2) {
+  if (!S || !S->raw || !f || !s2) return -1;
+  for (int y = 0; y < S->height; y++)
+    for (int x = 0; x < S->width; x++) {
+      long idx = (long)y * S->width + x;
+      double b = S->bias_px ? S->bias_px[idx] : S->black;
+      double a = S->prnu_px ? S->prnu_px[idx] : 1.0;
+      double rv = S->read_var_px ? S->read_var_px[idx] : S->read_var;
+      double sat = S->sat_px ? S->sat_px[idx] : S->sat;
+      double yv = (double)S->raw[(long)y * S->pitch + x];
+      if (orc_radiometry(yv, b, S->gain, S->exposure, a, S->nd, rv, sat, &f[idx], &s2[idx])) {
+        f[idx] = 0.0;
+        s2[idx] = INFINITY;
+      }
+    }
+  return 0;
+}
+
 /* One sample as the fit sees it. */
 typedef struct {
   int color;

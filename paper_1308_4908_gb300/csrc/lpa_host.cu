@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <algorithm>
 #include <array>
 #include <cstring>
@@ -103,19 +104,35 @@ struct BatchState {
   std::map<std::vector<std::array<int64_t, 5>>, FrameGraph> frame_graphs;
 };
 
-// Device copies of tabulated-weight tables, keyed by a hash of their contents. Tables are small
-// (tens of KB) and kept until the context is destroyed (at most kMaxTables; then the context waits
-// for its work and starts over).
 // Host-side caches of a context's launch planning.
 struct PlanCache {
   // encoded tensor maps by (raw pointer, width, height, pitch, box): encoding is a driver call
   std::map<std::array<uint64_t, 4>, CUtensorMap> tmaps;
-  // tabulated-weight tables on the device, by a hash of their contents
+  // Tabulated-weight tables on the device, by a hash of their contents. Tables are small (tens of
+  // KB) and kept until the context is destroyed, at most max_tables of them: the next one evicts
+  // them all (after the device has finished the work that may use them).
   std::map<uint64_t, void *> dev;
   // the inputs a table is built from (sensor count, scales, window constants, each sensor's
   // translation) -> the device table, so that a repeated configuration skips the host build
   std::map<std::vector<double>, void *> by_inputs;
-  uint64_t epoch = 0;  // bumped when the device tables are freed (plans holding them are stale)
+  uint64_t epoch = 0;  // bumped at each eviction (plans holding evicted tables are stale)
+  size_t max_tables = 4096;
+  // Plans made but not yet launched (a batch plans every frame before its one launch) may hold
+  // tables an eviction removes: inside a hold scope evicted tables are retired, not freed; a later
+  // eviction frees those retired in earlier scopes (whose launches it has waited for).
+  int hold = 0;
+  uint64_t scope = 0;
+  std::vector<std::pair<void *, uint64_t>> retired;  // (table, scope that retired it)
+};
+
+// Keeps the tables that plans made in its scope point at allocated until it ends.
+struct TableHold {
+  PlanCache &c;
+  explicit TableHold(PlanCache &cache) : c(cache) {
+    c.hold++;
+    c.scope++;
+  }
+  ~TableHold() { c.hold--; }
 };
 
 struct hdr_ctx {
@@ -247,8 +264,6 @@ struct PlanEnv {
   bool tabulate;    // tabulated weights allowed (the persistent batch kernels search every window)
 };
 
-constexpr size_t kMaxTables = 4096;
-
 bool is_identity_linear(const double *a) {
   return std::fabs(a[0] - 1.0) <= 1e-12 && std::fabs(a[1]) <= 1e-12 && std::fabs(a[3]) <= 1e-12 &&
          std::fabs(a[4] - 1.0) <= 1e-12;
@@ -341,9 +356,21 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
   hsh ^= (uint64_t)hdr.size() << 40;
   auto it = env.tabs->dev.find(hsh);
   if (it == env.tabs->dev.end()) {
-    if (env.tabs->dev.size() >= kMaxTables) {
+    if (env.tabs->dev.size() >= env.tabs->max_tables) {
+      // every launch made so far may use the tables: wait for the device, then free them, unless
+      // plans that are not launched yet may hold them (then they wait in `retired`)
       CUDA_TRY(cudaDeviceSynchronize());
-      for (auto &t : env.tabs->dev) cudaFree(t.second);
+      PlanCache &tc = *env.tabs;
+      size_t keep = 0;
+      for (auto &t : tc.retired) {
+        if (tc.hold > 0 && t.second == tc.scope) tc.retired[keep++] = t;
+        else cudaFree(t.first);
+      }
+      tc.retired.resize(keep);
+      for (auto &t : tc.dev) {
+        if (tc.hold == 0) cudaFree(t.second);
+        else tc.retired.push_back({t.second, tc.scope});
+      }
       env.tabs->dev.clear();
       env.tabs->by_inputs.clear();
       env.tabs->epoch++;
@@ -360,13 +387,17 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
     }
     it = env.tabs->dev.emplace(hsh, d).first;
   }
-  if (env.tabs->by_inputs.size() >= 4 * kMaxTables) env.tabs->by_inputs.clear();
+  if (env.tabs->by_inputs.size() >= 4 * env.tabs->max_tables) env.tabs->by_inputs.clear();
   env.tabs->by_inputs.emplace(std::move(inputs), it->second);
   L.tab_hdr = static_cast<const int4 *>(it->second);
   L.tab_cells = reinterpret_cast<const float4 *>(static_cast<const int4 *>(it->second) + hdr.size());
   L.mode = LPA_TABULATED;
   return HDR_OK;
 }
+
+#ifndef LPA_FRAME_TILE_H
+#define LPA_FRAME_TILE_H 16  // tile height of single-frame launches
+#endif
 
 // Fill the launch descriptor for one frame. raw: device pointers per sensor.
 // reach: the largest window grows by this factor (the steered window of Section 5.4 reaches
@@ -475,6 +506,10 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
     hdr_status st = build_tables(env, rig, p, L);
     if (st) return st;
   }
+  // a usable fit's equilibrated pivots lie in (min_pivot, 1]: when min_pivot * cond_fallback >= 2
+  // their spread never exceeds cond_fallback and the FP64 re-solve cannot trigger
+  const bool f64_possible = p->cond_fallback > 0.0 && (p->min_pivot - 1e-4) * p->cond_fallback < 2.0;
+  if (L.mode == LPA_SEARCHED && !f64_possible) L.mode = LPA_SEARCHED_F32;
   if (L.mode != LPA_TABULATED) {  // each thread's sample cell in each sensor (tables need none)
     off = (off + 15) / 16 * 16;
     L.off_pos = off;
@@ -490,7 +525,8 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
 
 hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
                 double reach = 1.0, bool tabulate = true) {
-  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, tabulate}, rig, p, raw, L, 16, reach);
+  return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, tabulate}, rig, p, raw, L,
+                  LPA_FRAME_TILE_H, reach);
 }
 
 // plan() of a single-frame call through the context's plan cache.
@@ -605,6 +641,11 @@ hdr_status hdr_create(int device, hdr_ctx **out) {
     return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
   }
   c->encode = reinterpret_cast<EncodeTiledFn>(fn);
+  // HDR_LPA_MAX_TABLES (optional): fewer cached weight tables, so that tests can force evictions
+  if (const char *mt = getenv("HDR_LPA_MAX_TABLES")) {
+    const long v = strtol(mt, nullptr, 10);
+    if (v >= 1 && v <= 4096) c->tabs.max_tables = (size_t)v;
+  }
   e = cudaMalloc(&c->status, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(unsigned int));
   if (e != cudaSuccess) {
@@ -626,6 +667,7 @@ void hdr_destroy(hdr_ctx *ctx) {
   cudaFree(ctx->choice_stage);
   cudaFree(ctx->calpa);
   for (auto &t : ctx->tabs.dev) cudaFree(t.second);
+  for (auto &t : ctx->tabs.retired) cudaFree(t.first);
   if (ctx->h2d) cudaStreamDestroy(ctx->h2d);
   if (ctx->d2h) cudaStreamDestroy(ctx->d2h);
   for (int b = 0; b < 8; b++) {
@@ -997,7 +1039,8 @@ hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *
     hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, false}, ctx->rigs[F.rig_id],
                              F.params, F.raw_dev, plans[f], cfg.tile_h);
     if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
-    if (plans[f].mode != LPA_SEARCHED) return fail(HDR_E_INTERNAL, "frame %d: the persistent form searches windows", f);
+    if (plans[f].mode != LPA_SEARCHED && plans[f].mode != LPA_SEARCHED_F32)
+      return fail(HDR_E_INTERNAL, "frame %d: the persistent form searches windows", f);
     plans[f].out = F.out_dev;
     plans[f].choice = F.choice_dev;
     plans[f].levels = nullptr;
@@ -1047,6 +1090,7 @@ hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *
 hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *ranges,
                             const hdr_batch_config &cfg, cudaStream_t stream) {
   BatchState &B = ctx->batch;
+  TableHold hold(ctx->tabs);  // the plans of every frame stay valid until the launch
   std::vector<LpaLaunch> plans(n);
   std::vector<int> grid(n, 0);
   for (int f = 0; f < n; f++) {
@@ -1082,7 +1126,7 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
     if (!fn) return fail(HDR_E_INTERNAL, "no kernel for order %d, mode %d, tile height %d", L.order, L.mode, cfg.tile_h);
     CUDA_TRY(lpa_opt_in(fn));
     // grid size and shared memory are set on each replay: graphs are kept per sequence of kernels
-    key.push_back({L.order * 4 + L.mode, comp ? 1 : 0, cfg.tile_h, 0, 0});
+    key.push_back({L.order * 8 + L.mode, comp ? 1 : 0, cfg.tile_h, 0, 0});
     args[k] = &plans[order[k]];
     kp[k] = cudaKernelNodeParams{};
     kp[k].func = const_cast<void *>(fn);

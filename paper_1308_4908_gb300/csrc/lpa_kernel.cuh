@@ -135,6 +135,7 @@ struct Moments {
     cnt += 1.f;
   }
 
+  __device__ __forceinline__ float count() const { return cnt; }
   template <typename T>
   __device__ __forceinline__ T A(int i) const { return COMP ? (T)a[i] + (T)al[i] : (T)a[i]; }
   template <typename T>
@@ -148,6 +149,7 @@ struct Moments {
 #endif
 
 
+
 // The same plain FP32 moments with the Gram and variance sums of each monomial held as one pair
 // (sum w m, sum w K m): one paired FMA (fma.rn.f32x2, weights (w, w K), the monomial in both
 // halves) advances both, rounding each half as the scalar FMA would. The monomials of degree 3
@@ -159,22 +161,22 @@ struct MomentsPacked {
   static constexpr int NA = n_monos(ORDER);
   static constexpr int NB = n_unknowns(ORDER);
   float2 ak[NA];  // (sum w m_i, sum w K m_i)
-  float b[NB];
-  float cnt;
+  // the right-hand side sum w f m_i in pairs of monomials held in register pairs:
+  // (sum w f, count), (m_1, m_2) = D, (m_3, m_5) = D2; m_4 alone
+  float2 b0n, b12, b35;
+  float b4;
 
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < NA; i++) ak[i] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < NB; i++) b[i] = 0.f;
-    cnt = 0.f;
+    b0n = b12 = b35 = make_float2(0.f, 0.f);
+    b4 = 0.f;
   }
+  __device__ __forceinline__ float count() const { return b0n.y; }
 
-  // one sample at offset D = (dx, dy) with squares D2 = (dx^2, dy^2): the monomials of degree 3
+  // the monomials of one sample at offset D = (dx, dy) with squares D2 = (dx^2, dy^2): degree 3
   // and 4 come two at a time from paired products
-  __device__ __forceinline__ void add2(float2 D, float2 D2, float w, float wf, float wk) {
-    const float2 W = make_float2(w, wk);
-    float s[15];
+  static __device__ __forceinline__ void monomials(float2 D, float2 D2, float (&s)[15]) {
     s[1] = D.x;
     s[2] = D.y;
     s[3] = D2.x;
@@ -196,19 +198,33 @@ struct MomentsPacked {
       s[13] = P31.y;
       s[14] = P4.y;
     }
+  }
+  // one sample with its monomials s, weight w = K / s2, w f and w K
+  __device__ __forceinline__ void adds(const float (&s)[15], float2 D, float2 D2, float w, float wf, float wk) {
+    const float2 W = make_float2(w, wk);
     ak[0] = __fadd2_rn(ak[0], W);
 #pragma unroll
     for (int i = 1; i < NA; i++) ak[i] = __ffma2_rn(W, make_float2(s[i], s[i]), ak[i]);
-    b[0] += wf;
-    cnt += 1.f;
-#pragma unroll
-    for (int i = 1; i < NB; i++) b[i] = fmaf(wf, s[i], b[i]);
+    const float2 F = make_float2(wf, wf);
+    b0n = __fadd2_rn(b0n, make_float2(wf, 1.f));
+    b12 = __ffma2_rn(F, D, b12);
+    if (NB > 3) {
+      b35 = __ffma2_rn(F, D2, b35);
+      b4 = fmaf(wf, s[4], b4);
+    }
+  }
+  __device__ __forceinline__ void add2(float2 D, float2 D2, float w, float wf, float wk) {
+    float s[15];
+    monomials(D, D2, s);
+    adds(s, D, D2, w, wf, wk);
   }
 
   template <typename T>
   __device__ __forceinline__ T A(int i) const { return (T)ak[i].x; }
   template <typename T>
-  __device__ __forceinline__ T B(int i) const { return (T)b[i]; }
+  __device__ __forceinline__ T B(int i) const {
+    return (T)(i == 0 ? b0n.x : i == 1 ? b12.x : i == 2 ? b12.y : i == 3 ? b35.x : i == 4 ? b4 : b35.y);
+  }
   template <typename T>
   __device__ __forceinline__ T Kv(int i) const { return (T)ak[i].y; }
 };
@@ -288,7 +304,7 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
   }
   r.dmin = (float)dmin;
   r.dmax = (float)dmax;
-  r.valid = pos && (m.cnt >= (float)P) && (dmin > (T)min_pivot);
+  r.valid = pos && (m.count() >= (float)P) && (dmin > (T)min_pivot);
   // l = A^{-1} e_0: forward (unit L), diagonal, backward (L^T)
   T x[P];
 #pragma unroll
@@ -359,20 +375,21 @@ __device__ __forceinline__ FitOut solve(const MOM &m, float min_pivot) {
 
 // FP32 solve; the same solve in FP64 when the FP32 pivots span more than
 // cond_fallback and the fit could still pass min_pivot in exact arithmetic.
-template <int P, class MOM, bool COEF = false>
+template <int P, class MOM, bool COEF = false, bool F64 = true>
 __device__ __forceinline__ FitOut solve_with_fallback(const MOM &m, float min_pivot, float cond_fallback) {
   FitOut r = solve<float, P, MOM, COEF>(m, min_pivot);
-  bool redo = cond_fallback > 0.f && m.cnt >= (float)P && !(r.dmin * cond_fallback >= r.dmax) &&
+  if constexpr (!F64) return r;
+  bool redo = cond_fallback > 0.f && m.count() >= (float)P && !(r.dmin * cond_fallback >= r.dmax) &&
               r.dmin > min_pivot - LPA_PIVOT_FP32_ERR;
   if (redo) r = solve<double, P, MOM, COEF>(m, min_pivot);
   return r;
 }
 
 // Lower-order fits at the largest scale reuse the leading block of the moments.
-template <int ORDER, int I, class MOM>
+template <int ORDER, int I, bool F64, class MOM>
 __device__ __forceinline__ FitOut fallback_fit(const MOM &m, float min_pivot, float cond_fallback) {
-  if constexpr (ORDER - 1 - I == 1) return solve_with_fallback<3>(m, min_pivot, cond_fallback);
-  else return solve_with_fallback<1>(m, min_pivot, cond_fallback);
+  if constexpr (ORDER - 1 - I == 1) return solve_with_fallback<3, MOM, false, F64>(m, min_pivot, cond_fallback);
+  else return solve_with_fallback<1, MOM, false, F64>(m, min_pivot, cond_fallback);
 }
 
 // ---------------------------------------------------------------- scale choice
@@ -406,6 +423,23 @@ struct Ici {
 
 // ---------------------------------------------------------------- kernel
 
+// Scales per walk of the window cells: the searched window of order 0 to 2 with plain FP32 sums
+// feeds up to four nested scales from one walk (their sums stay in registers); the other variants
+// walk once per scale.
+#ifndef LPA_MULTI_SCALE
+#define LPA_MULTI_SCALE 2      // order 2
+#endif
+#ifndef LPA_MULTI_SCALE_LOW
+#define LPA_MULTI_SCALE_LOW 4  // orders 0 and 1
+#endif
+template <int ORDER, bool COMP, int MODE>
+struct MultiScale {
+  static constexpr int value = COMP ? 1
+                               : MODE == LPA_SEARCHED_F32 ? (ORDER == 2 ? LPA_MULTI_SCALE : LPA_MULTI_SCALE_LOW)
+                               : MODE == LPA_SEARCHED    ? (ORDER == 2 ? 1 : LPA_MULTI_SCALE_LOW)
+                                                         : 1;
+};
+
 // sensor-space positions are clamped to +-LPA_FAR px (far outside any sensor) before integer conversion
 #define LPA_FAR 1.0e7
 
@@ -413,6 +447,15 @@ struct Anchor {
   int ix, iy;
   float fx, fy;
 };
+
+// Staged sample layout: (f, 1/s2) (1/s for the printed weight); 1/s2 = 0 excludes the sample.
+__device__ __forceinline__ float2 stage_pair(float f, float iv) { return make_float2(f, iv); }
+__device__ __forceinline__ bool sample_ok(float2 fv) { return fv.y > 0.f; }
+// (w, w f) of a staged sample for window value K: w = K / s2
+__device__ __forceinline__ float2 weights(float K, float2 fv) {
+  const float w = K * fv.y;
+  return make_float2(w, w * fv.x);
+}
 
 // One window cell: offset D from the pixel's point, disc test, Eq. 8 weight times inverse
 // variance, moment update.
@@ -426,38 +469,54 @@ __device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R
   const float2 D2 = __fmul2_rn(D, D);
   // |d|^2, or d^T C d for the steered window (Section 5.4)
   const float r2 = STEER ? fmaf(Q.x, D2.x, fmaf(Q.z, D2.y, 2.f * Q.y * (D.x * D.y))) : D2.x + D2.y;
-  const bool in = r2 < R2 && fv.y > 0.f;
+  const bool in = r2 < R2 && sample_ok(fv);
   if constexpr (ORDER == 0) {
     // four sums: cheaper to add exact zeros for cells outside the window than to branch
     const float K = ex2_approx(r2 * cexp) - taper;  // Eq. 8, truncated and tapered
-    const float w = in ? K * fv.y : 0.f;            // window x inverse variance
-    m.add0(w, w * fv.x, (LIT ? (in ? K : 0.f) : w) * K, in ? 1.f : 0.f);
+    const float2 W = weights(in ? K : 0.f, fv);     // window x inverse variance, times f
+    m.add0(W.x, W.y, (LIT ? (in ? K : 0.f) : W.x) * K, in ? 1.f : 0.f);
   } else if (in) {
     const float K = ex2_approx(r2 * cexp) - taper;
-    const float w = K * fv.y;
-    m.add2(D, D2, w, w * fv.x, (LIT ? K : w) * K);
+    const float2 W = weights(K, fv);
+    m.add2(D, D2, W.x, W.y, (LIT ? K : W.x) * K);
   }
 }
 
-// The n cells of one row: cell q is at D = DR + q S2. (Fully unrolled rows dispatched on n were
-// measured slower.)
-template <int ORDER, int MODE, class MOM>
-__device__ __forceinline__ void row_cells(MOM &m, const float2 *rowp, int n, float2 DR, float2 S2, float R2,
-                                          float cexp, float taper, float4 Q) {
-  float qf = 0.f;
-  // two samples in flight pay off only for the long order-2 bodies
-  constexpr int kUnroll = ORDER == 2 ? 2 : 1;
-#pragma unroll kUnroll
-  for (int q = 0; q < n; q++, qf += 1.f)
-    window_cell<ORDER, MODE>(m, __ffma2_rn(make_float2(qf, qf), S2, DR), rowp[q], R2, cexp, taper, Q);
+// Several window scales in one walk (the windows of one channel are nested discs): the cell's
+// offset, its disc test against the largest scale and its monomials are computed once, then each
+// scale whose disc holds the sample adds it with its own Eq. 8 weight. Slot q of the scale arrays
+// belongs to the q-th scale of the pass; R2[q] < 0 marks an unused slot.
+
+template <int ORDER, int NSP, int MODE, class MOM>
+__device__ __forceinline__ void window_cell_ms(MOM (&m)[NSP], float2 D, float2 fv, const float (&R2)[NSP],
+                                               const float (&cexp)[NSP], float taper, float4 Q) {
+  constexpr bool STEER = MODE == LPA_STEERED;
+  constexpr bool LIT = MODE == LPA_LITERAL;
+  const float2 D2 = __fmul2_rn(D, D);
+  const float r2 = STEER ? fmaf(Q.x, D2.x, fmaf(Q.z, D2.y, 2.f * Q.y * (D.x * D.y))) : D2.x + D2.y;
+  if (!(r2 < R2[NSP - 1] && sample_ok(fv))) return;
+  float sm[15];
+  if constexpr (ORDER > 0) MOM::monomials(D, D2, sm);
+  // largest scale first; the windows are nested, so the first one that misses ends the loop
+  // (a loop with an exit, not a chain of tests: no reconvergence point per scale)
+#pragma unroll
+  for (int q = NSP - 1; q >= 0; q--) {
+    if (!(r2 < R2[q])) break;
+    const float K = ex2_approx(r2 * cexp[q]) - taper;
+    const float2 W = weights(K, fv);
+    if constexpr (ORDER == 0) m[q].add0(W.x, W.y, (LIT ? K : W.x) * K, 1.f);
+    else m[q].adds(sm, D, D2, W.x, W.y, (LIT ? K : W.x) * K);
+  }
 }
 
-template <int ORDER, bool COMP, int MODE = LPA_SEARCHED>
-__device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COMP>::type &m, const LpaSensorK &S,
-                                                  int4 pos, int c, float R, float R2,
-                                                  float cexp, float taper, int x0, int y0,
-                                                  const unsigned char *smem, bool active, unsigned *status,
-                                                  float4 Q = make_float4(1.f, 0.f, 1.f, 0.f)) {
+// Walk the window cells of channel c in sensor S for one pixel (sample cell and fraction `pos`):
+// the cells of the bounding box of the pre-image of the window of radius R (or of the steered
+// window d^T Q d < R^2), row by row inside the staged box. body(D, fv) receives each cell's offset
+// D = X - P_j in reference px and its staged (f, 1/s2). The rows run UNROLL cells at a time.
+template <int MODE, int UNROLL, class Body>
+__device__ __forceinline__ void walk_sensor(const LpaSensorK &S, int4 pos, int c, float R, int x0, int y0,
+                                            const unsigned char *smem, bool active, unsigned *status, float4 Q,
+                                            Body &&body) {
   // the pixel's point in sensor s: sample cell (ix, iy) and fraction (fx, fy) in [0, 1)
   const int ix = pos.x, iy = pos.y;
   const float fx = __int_as_float(pos.z), fy = __int_as_float(pos.w);
@@ -512,15 +571,35 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
     const int rbeg = colok ? max(0, -pr0) : NJ;
     const int rend = min(STEER ? nj : NJ, PH - pr0);
     const float2 *rowp = pl + (pr0 + rbeg) * PW + pc0;
-    // offset of the first cell of the first row; each row adds A (0, 2)
+    // offset of the first cell of the first row; each row adds A (0, 2), each cell A (2, 0)
     const float Dy0 = 2.f * (float)(jlo + rbeg) - ry;
     const float2 DR0 = make_float2(fmaf(a00, Dx0, a01 * Dy0), fmaf(a10, Dx0, a11 * Dy0));
     const float2 T2 = make_float2(2.f * a01, 2.f * a11), S2 = make_float2(sx, sy);
     float rf = 0.f;
 #pragma unroll 1
-    for (int r = rbeg; r < rend; r++, rowp += PW, rf += 1.f)
-      row_cells<ORDER, MODE>(m, rowp, nw, __ffma2_rn(make_float2(rf, rf), T2, DR0), S2, R2, cexp, taper, Q);
+    for (int r = rbeg; r < rend; r++, rowp += PW, rf += 1.f) {
+      const float2 DR = __ffma2_rn(make_float2(rf, rf), T2, DR0);
+      // cell q is at DR + q A (2, 0), by repeated addition (a few roundings of the offset, well
+      // within the window-position term of the parity tolerance)
+      float2 Dq = DR;
+#pragma unroll UNROLL
+      for (int q = 0; q < nw; q++, Dq = __fadd2_rn(Dq, S2)) body(Dq, rowp[q]);
+    }
   }
+}
+
+template <int ORDER, bool COMP, int MODE = LPA_SEARCHED>
+__device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COMP>::type &m, const LpaSensorK &S,
+                                                  int4 pos, int c, float R, float R2,
+                                                  float cexp, float taper, int x0, int y0,
+                                                  const unsigned char *smem, bool active, unsigned *status,
+                                                  float4 Q = make_float4(1.f, 0.f, 1.f, 0.f)) {
+  // two samples in flight pay off only for the long order-2 bodies (fully unrolled rows
+  // dispatched on their length were measured slower)
+  constexpr int kUnroll = ORDER == 2 ? 2 : 1;
+  walk_sensor<MODE, kUnroll>(S, pos, c, R, x0, y0, smem, active, status, Q, [&](float2 D, float2 fv) {
+    window_cell<ORDER, MODE>(m, D, fv, R2, cexp, taper, Q);
+  });
 }
 
 // The window of one pixel read from the tabulated cells (Section 8; see LpaLaunch::tab_hdr): the
@@ -554,13 +633,13 @@ __device__ __forceinline__ void accumulate_table(MOM &m, const LpaLaunch &L, int
       const float4 t = __ldg(cell + k);
       const int q = __float_as_int(t.w);
       const float2 fv = pl[(q >> 16) * PW + (int)(short)(q & 0xffff)];
-      if (active && fv.y > 0.f) {
-        const float w = t.z * fv.y;  // tabulated window weight x inverse variance
+      if (active && sample_ok(fv)) {
+        const float2 W = weights(t.z, fv);  // tabulated window weight x inverse variance, times f
         if constexpr (ORDER == 0) {
-          m.add0(w, w * fv.x, w * t.z, 1.f);
+          m.add0(W.x, W.y, W.x * t.z, 1.f);
         } else {
           const float2 D = make_float2(t.x, t.y);
-          m.add2(D, __fmul2_rn(D, D), w, w * fv.x, w * t.z);
+          m.add2(D, __fmul2_rn(D, D), W.x, W.y, W.x * t.z);
         }
       }
     }
@@ -687,7 +766,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
           }
         }
       }
-      planes[((lx & 1) + 2 * (ly & 1)) * PP + (ly >> 1) * PW + (lx >> 1)] = make_float2(f, iv);
+      planes[((lx & 1) + 2 * (ly & 1)) * PP + (ly >> 1) * PW + (lx >> 1)] = stage_pair(f, iv);
       lx += step_x;
       ly += step_y;
       if (lx >= bw) {
@@ -714,6 +793,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   const float log2e = 1.4426950408889634f;
 
   constexpr bool TAB = MODE == LPA_TABULATED, STEER = MODE == LPA_STEERED, GRAD = MODE == LPA_GRADIENTS;
+  constexpr bool F64 = MODE != LPA_SEARCHED_F32;  // the FP64 re-solve is compiled in
   // the pixel's point in each sensor, once: anchor (FP64 at the 8x8 block corner) + small FP32
   // step, split into sample cell and fraction; every channel and scale reads it back
   int4 *pos = reinterpret_cast<int4 *>(smem + RD(L.off_pos)) + tid;
@@ -736,11 +816,111 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   if constexpr (STEER)
     if (pix) Q = make_float4(L.aux[opix * 3], L.aux[opix * 3 + 1], L.aux[opix * 3 + 2], 0.f);
 
+  using MOM = typename MomentsSel<ORDER, COMP>::type;
+  // the fit of one (channel, scale) from its moments: factorised unless no lane of the warp has as
+  // many samples as unknowns (such a fit is not usable whatever its pivots; on near-translational
+  // rigs the lanes share one sample layout, so whole warps qualify)
+  auto fit_of = [&](const MOM &m) {
+    FitOut f;
+    if (__all_sync(LPA_FULL, m.count() < (float)P)) {
+      f.valid = false;
+      f.c0 = f.var = f.c1 = f.c2 = 0.f;
+      f.dmin = f.dmax = 0.f;
+    } else {
+      f = solve_with_fallback<P, MOM, GRAD, F64>(m, RD(L.min_pivot), RD(L.cond_fallback));
+    }
+    return f;
+  };
+  auto put_level = [&](int c, int level, const FitOut &f) {
+    if (DIAG && pix) {
+      float *o = L.levels + (((size_t)c * NL + level) * plane_px + opix) * 2;
+      o[0] = f.valid ? f.c0 : __int_as_float(0x7fffffff);
+      o[1] = f.valid ? f.var : __int_as_float(0x7fffffff);
+    }
+  };
+  // order fallback at the largest scale (m holds its moments when any lane needs it), then the store
+  auto finish = [&](int c, Ici &ici, const MOM &m) {
+    const bool need = ici.choice == 255 && pix;
+    if (DIAG || __any_sync(LPA_FULL, need)) {
+      auto take = [&](const FitOut &f, int i) {
+        put_level(c, J + i, f);
+        if (ici.choice == 255 && f.valid) {
+          ici.choice = J + i;
+          ici.val = f.c0;
+        }
+      };
+      if constexpr (ORDER >= 1) take(fallback_fit<ORDER, 0, F64>(m, RD(L.min_pivot), RD(L.cond_fallback)), 0);
+      if constexpr (ORDER >= 2) take(fallback_fit<ORDER, 1, F64>(m, RD(L.min_pivot), RD(L.cond_fallback)), 1);
+    }
+    if (pix) {
+      if (RD(L.out_half))
+        reinterpret_cast<__half *>(RD(L.out))[c * plane_px + opix] = __float2half_rn(ici.val);
+      else
+        reinterpret_cast<float *>(RD(L.out))[c * plane_px + opix] = ici.val;
+      if (RD(L.choice)) RD(L.choice)[c * plane_px + opix] = (uint8_t)ici.choice;
+    }
+  };
+
+  // the persistent many-frame kernel walks once per scale (its register budget, shared by every
+  // frame it serves, has no room for the sums of several scales)
+  constexpr int NSP = GLOBAL_MAPS ? 1 : MultiScale<ORDER, COMP, MODE>::value;
+  if constexpr (NSP > 1) {
+    if (J >= 2) {
+      // all scales of a channel from one walk per sensor (up to NSP scales per pass): slot q of
+      // a pass holds scale j0 + q - lead, so that the pass's largest scale is always the last slot
+#pragma unroll 1
+      for (int c = 0; c < 3; c++) {
+        Ici ici;
+        ici.reset(pix);
+        MOM m[NSP];
+        const float gsc = (c == 1) ? RD(L.green_ratio) : 1.f;
+        // the first pass takes what the later full passes leave (the small scales), so that the
+        // largest scales share the longest walk
+        const int npass = (J + NSP - 1) / NSP;
+#pragma unroll 1
+        for (int pass = 0, j0 = 0, nj = J - NSP * (npass - 1); pass < npass; pass++, j0 += nj, nj = NSP) {
+          if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
+          const int lead = NSP - nj;
+          float R2s[NSP], cxs[NSP];
+#pragma unroll
+          for (int q = 0; q < NSP; q++) {
+            const float sg = RD(L.sigma[q >= lead ? j0 + q - lead : j0]) * gsc;
+            const float Rq = RD(L.trunc_k) * sg;
+            R2s[q] = q >= lead ? Rq * Rq : -1.f;
+            cxs[q] = -log2e / (2.f * sg * sg);
+            m[q].zero();
+          }
+          const float R = RD(L.trunc_k) * RD(L.sigma[j0 + nj - 1]) * gsc;
+          const float taper = RD(L.taper);
+          const bool act = DIAG ? pix : !ici.done;
+#pragma unroll 1
+          for (int s = 0; s < S; s++)
+            walk_sensor<MODE, 1>(L.s[s], pos[s * NT], c, R, fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q,
+                                 [&](float2 D, float2 fv) { window_cell_ms<ORDER, NSP, MODE>(m, D, fv, R2s, cxs, taper, Q); });
+          // the fits in ascending scale order, always from slot 0: the later slots move down one
+          // place after each fit, so that slot 0 ends with the pass's largest scale
+          // the fits in ascending scale order
+#pragma unroll
+          for (int q = 0; q < NSP; q++) {
+            if (q >= lead) {
+              if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
+              const FitOut f = fit_of(m[q]);
+              put_level(c, j0 + q - lead, f);
+              ici.step(f, j0 + q - lead, RD(L.ici_gamma));
+            }
+          }
+        }
+        finish(c, ici, m[NSP - 1]);
+      }
+      return true;
+    }
+  }
+
 #pragma unroll 1
   for (int c = GRAD ? 1 : 0; c < (GRAD ? 2 : 3); c++) {  // the gradient pass fits the green channel only
     Ici ici;
     ici.reset(pix);
-    typename MomentsSel<ORDER, COMP>::type m;
+    MOM m;
     const float gsc = (c == 1) ? RD(L.green_ratio) : 1.f;
 #pragma unroll 1
     for (int j = 0; j < J; j++) {
@@ -758,17 +938,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
           accumulate_sensor<ORDER, COMP, MODE>(m, L.s[s], pos[s * NT], c, R, R2, cexp, RD(L.taper),
                                                 fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q);
       }
-      // a fit with fewer samples than unknowns is not usable whatever its pivots: when that holds
-      // for the whole warp (its lanes share one sample layout on near-translational rigs), the
-      // factorisation is skipped
-      FitOut f;
-      if (__all_sync(LPA_FULL, m.cnt < (float)P)) {
-        f.valid = false;
-        f.c0 = f.var = f.c1 = f.c2 = 0.f;
-        f.dmin = f.dmax = 0.f;
-      } else {
-        f = solve_with_fallback<P, decltype(m), GRAD>(m, RD(L.min_pivot), RD(L.cond_fallback));
-      }
+      const FitOut f = fit_of(m);
       if constexpr (GRAD) {  // Section 5.4: the order-1 fit's linear coefficients; 0 if not usable
         if (pix) {
           L.aux[opix * 2] = f.valid ? f.c1 : 0.f;
@@ -776,46 +946,29 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
         }
         break;
       }
-      if (DIAG && pix) {
-        float *o = L.levels + (((size_t)c * NL + j) * plane_px + opix) * 2;
-        o[0] = f.valid ? f.c0 : __int_as_float(0x7fffffff);
-        o[1] = f.valid ? f.var : __int_as_float(0x7fffffff);
-      }
+      put_level(c, j, f);
       ici.step(f, j, RD(L.ici_gamma));
     }
-    if constexpr (GRAD) continue;
-    // order fallback at the largest scale (the moments still hold it when any lane needs it)
-    const bool need = ici.choice == 255 && pix;
-    if (DIAG || __any_sync(LPA_FULL, need)) {
-      auto take = [&](const FitOut &f, int i) {
-        if (DIAG && pix) {
-          float *o = L.levels + (((size_t)c * NL + J + i) * plane_px + opix) * 2;
-          o[0] = f.valid ? f.c0 : __int_as_float(0x7fffffff);
-          o[1] = f.valid ? f.var : __int_as_float(0x7fffffff);
-        }
-        if (ici.choice == 255 && f.valid) {
-          ici.choice = J + i;
-          ici.val = f.c0;
-        }
-      };
-      if constexpr (ORDER >= 1) take(fallback_fit<ORDER, 0>(m, RD(L.min_pivot), RD(L.cond_fallback)), 0);
-      if constexpr (ORDER >= 2) take(fallback_fit<ORDER, 1>(m, RD(L.min_pivot), RD(L.cond_fallback)), 1);
-    }
-    if (pix) {
-      if (RD(L.out_half))
-        reinterpret_cast<__half *>(RD(L.out))[c * plane_px + opix] = __float2half_rn(ici.val);
-      else
-        reinterpret_cast<float *>(RD(L.out))[c * plane_px + opix] = ici.val;
-      if (RD(L.choice)) RD(L.choice)[c * plane_px + opix] = (uint8_t)ici.choice;
-    }
+    if constexpr (!GRAD) finish(c, ici, m);
   }
   return true;
 #undef RD
 }
 
 // Single frame: one CTA per tile (tiles tile0 .. tile0 + gridDim.x - 1).
+// Resident CTAs per SM the single-frame kernel is compiled for: the order-2 sums of four scales
+// need about 200 registers a thread (one 16-row CTA or two 8-row CTAs per SM).
+#ifndef LPA_M2_CTAS_256
+#define LPA_M2_CTAS_256 2  // resident 256-thread CTAs per SM the multi-scale order-2 kernel is built for
+#endif
+template <int ORDER, bool COMP, int TH, int MODE>
+struct FrameOccupancy {
+  static constexpr int value =
+      (ORDER == 2 && MultiScale<ORDER, COMP, MODE>::value > 1) ? LPA_M2_CTAS_256 * 16 / TH : 16 / TH * 2;
+};
+
 template <int ORDER, bool COMP, bool DIAG, int TH, int MODE = LPA_SEARCHED>
-__global__ void __launch_bounds__(LPA_TILE *TH, 16 / TH * 2) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
+__global__ void __launch_bounds__(LPA_TILE *TH, (FrameOccupancy<ORDER, COMP, TH, MODE>::value)) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
   __shared__ Anchor anchors[4][LPA_MAX_SENSORS];

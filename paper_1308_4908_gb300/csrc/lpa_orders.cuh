@@ -19,7 +19,8 @@ constexpr bool instantiated() {
 
 template <int ORDER, bool COMP, bool DIAG, int TH, int MODE>
 const void *kernel_fn() {
-  if constexpr (!instantiated<ORDER, MODE, TH>() || (DIAG && MODE != LPA_SEARCHED)) return nullptr;
+  if constexpr (!instantiated<ORDER, MODE, TH>() || (DIAG && MODE != LPA_SEARCHED && MODE != LPA_SEARCHED_F32))
+    return nullptr;
   else return (const void *)lpa::lpa_reconstruct<ORDER, COMP, DIAG, TH, MODE>;
 }
 
@@ -31,6 +32,7 @@ const void *kernel_mode(int mode) {
     case LPA_STEERED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED>();
     case LPA_GRADIENTS: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_GRADIENTS>();
     case LPA_LITERAL: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_LITERAL>();
+    case LPA_SEARCHED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED_F32>();
     default: return nullptr;
   }
 }

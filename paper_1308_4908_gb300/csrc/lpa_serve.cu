@@ -92,7 +92,8 @@ struct Job {
 };
 
 struct Step {
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;        // recorded after the step's launch (its completion)
+  cudaEvent_t ev_begin = nullptr;  // recorded before it (timing: the step's start on the device)
   std::vector<uint64_t> members;
 };
 
@@ -118,6 +119,9 @@ struct hdr_server {
   std::vector<double> total_ms;
   double queue_ms_sum = 0.0;
   uint64_t submitted = 0, n_steps = 0, out_px = 0;
+  double gpu_step_ms = 0.0, gpu_gap_ms = 0.0, host_step_ms = 0.0, host_step_ms_max = 0.0;
+  cudaEvent_t last_end = nullptr;    // completion of the last step observed (timing event)
+  std::vector<cudaEvent_t> spare_timing;
   bool have_first = false;
   Clock::time_point t_first, t_last;
   std::thread worker;
@@ -134,6 +138,21 @@ struct hdr_server {
   }
   void recycle(cudaEvent_t &e) {
     if (e) spare_events.push_back(e);
+    e = nullptr;
+  }
+  // events with timing, for the step start and end stamps
+  cudaEvent_t timing_event() {
+    if (!spare_timing.empty()) {
+      cudaEvent_t e = spare_timing.back();
+      spare_timing.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  void recycle_timing(cudaEvent_t &e) {
+    if (e) spare_timing.push_back(e);
     e = nullptr;
   }
 
@@ -228,9 +247,12 @@ struct hdr_server {
   }
 
   // Launch one batched step over pending tiles of ready frames (admission order, within budget).
-  // Two steps may be queued: the next one is prepared while the device runs the current one.
-  bool launch_step() {
-    if (steps.size() >= 2) return false;
+  // Up to kMaxInflight steps may be queued, so that the device never waits for the host to build
+  // the next one. The lock is released while the step is planned and launched (submit and poll
+  // stay responsive); only this thread changes the jobs a step holds.
+  static constexpr size_t kMaxInflight = 3;
+  bool launch_step(std::unique_lock<std::mutex> &lock) {
+    if (steps.size() >= kMaxInflight) return false;
     std::vector<hdr_frame> frames;
     std::vector<int2> ranges;
     Step st;
@@ -251,16 +273,25 @@ struct hdr_server {
       st.members.push_back(t);
     }
     if (frames.empty()) return false;
+    const Clock::time_point h0 = Clock::now();
+    st.ev_begin = timing_event();
+    st.ev = timing_event();
+    lock.unlock();
+    if (st.ev_begin) cudaEventRecord(st.ev_begin, compute);
     hdr_status s = lpa_batch_run(ctx, (int)frames.size(), frames.data(), ranges.data(), &cfg.batch, compute);
-    st.ev = event();
+    lock.lock();
     if (s == HDR_OK && !st.ev) s = lpa_fail(HDR_E_CUDA, "cudaEventCreate failed");
     if (s == HDR_OK) {
       cudaError_t e = cudaEventRecord(st.ev, compute);
       if (e != cudaSuccess) s = lpa_fail(HDR_E_CUDA, cudaGetErrorString(e));
     }
+    const double hms = ms_between(h0, Clock::now());
+    host_step_ms += hms;
+    host_step_ms_max = std::max(host_step_ms_max, hms);
     if (s != HDR_OK) {
       for (uint64_t t : st.members) fail_job(jobs[t], s);
-      recycle(st.ev);
+      recycle_timing(st.ev);
+      recycle_timing(st.ev_begin);
       return true;
     }
     for (size_t k = 0; k < st.members.size(); k++) {
@@ -281,6 +312,13 @@ struct hdr_server {
       Step st = steps.front();
       steps.pop_front();
       for (uint64_t t : st.members) jobs[t].inflight--;
+      float ms = 0.f;
+      if (st.ev_begin && cudaEventElapsedTime(&ms, st.ev_begin, st.ev) == cudaSuccess) gpu_step_ms += ms;
+      if (last_end && st.ev_begin && cudaEventElapsedTime(&ms, last_end, st.ev_begin) == cudaSuccess && ms > 0.f)
+        gpu_gap_ms += ms;
+      cudaGetLastError();  // an unrecorded stamp only costs the statistic
+      recycle_timing(last_end);
+      recycle_timing(st.ev_begin);
       hdr_status dev = lpa_take_status(ctx);
       if (dev != HDR_OK) {
         // the word may have been set by this step or the one queued behind it: fail both
@@ -309,7 +347,7 @@ struct hdr_server {
           j.state = State::CopyOut;
         }
       }
-      recycle(st.ev);
+      last_end = st.ev;
       did = true;
     }
     return did;
@@ -337,7 +375,7 @@ struct hdr_server {
       did |= poll_inputs();
       did |= poll_steps();
       did |= poll_outputs();
-      did |= launch_step();
+      did |= launch_step(lock);
       if (!did) cv_work.wait_for(lock, std::chrono::microseconds(50));
     }
   }
@@ -471,6 +509,10 @@ hdr_status hdr_server_stats_get(hdr_server *srv, hdr_server_stats *stats) {
     stats->mean_queue_ms = srv->queue_ms_sum / (double)v.size();
     stats->busy_s = std::chrono::duration<double>(srv->t_last - srv->t_first).count();
   }
+  stats->gpu_step_ms = srv->gpu_step_ms;
+  stats->gpu_gap_ms = srv->gpu_gap_ms;
+  stats->host_step_ms_mean = srv->n_steps ? srv->host_step_ms / (double)srv->n_steps : 0.0;
+  stats->host_step_ms_max = srv->host_step_ms_max;
   return HDR_OK;
 }
 
@@ -491,6 +533,12 @@ void hdr_server_destroy(hdr_server *srv) {
     if (kv.second.ev_out) cudaEventDestroy(kv.second.ev_out);
   }
   for (cudaEvent_t e : srv->spare_events) cudaEventDestroy(e);
+  for (cudaEvent_t e : srv->spare_timing) cudaEventDestroy(e);
+  if (srv->last_end) cudaEventDestroy(srv->last_end);
+  for (const Step &st : srv->steps) {
+    if (st.ev) cudaEventDestroy(st.ev);
+    if (st.ev_begin) cudaEventDestroy(st.ev_begin);
+  }
   cudaStreamDestroy(srv->compute);
   cudaStreamDestroy(srv->h2d);
   cudaStreamDestroy(srv->d2h);

@@ -78,7 +78,9 @@ class hdr_result(ctypes.Structure):
 class hdr_server_stats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("submitted", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_queue_ms", ctypes.c_double),
-                ("steps", ctypes.c_uint64), ("output_pixels", ctypes.c_uint64), ("busy_s", ctypes.c_double)]
+                ("steps", ctypes.c_uint64), ("output_pixels", ctypes.c_uint64), ("busy_s", ctypes.c_double),
+                ("gpu_step_ms", ctypes.c_double), ("gpu_gap_ms", ctypes.c_double),
+                ("host_step_ms_mean", ctypes.c_double), ("host_step_ms_max", ctypes.c_double)]
 
 
 class HdrError(RuntimeError):

@@ -19,7 +19,11 @@ FP16 output adds 2^-11 relative.
 Several results are correct where the scale choice is a near-tie or a usability test sits at
 its threshold: when the GPU used a different level than the oracle, the GPU's level must be one
 the rule could pick with its inputs perturbed within tolerance, and the GPU value must match the
-oracle's estimate at that level.
+oracle's estimate at that level. A usability test may go either way where the pivot lies within
+2 % of min_pivot, or within what FP32 arithmetic can resolve: moment sums rounded by up to
+PIVOT_N U32 relative move a pivot of a matrix of condition kappa by up to about PIVOT_N U32 kappa
+of itself (with kappa ~1e8, near-singular fits of a few samples at the frame border, the FP32
+pivot is undetermined).
 """
 from __future__ import annotations
 
@@ -33,15 +37,27 @@ U32 = 2.0 ** -24    # unit roundoff of float32
 C_FIT = 128.0       # moment sums over up to ~128 samples
 C_W = 32.0          # window evaluation and sample-position rounding
 HALF_TOL = 2.0 ** -11
+PIVOT_N = 64.0      # moment sums of up to ~64 terms: relative rounding PIVOT_N * U32
 
 
 def rel_err(g, o):
     return np.abs(g - o) / np.maximum(np.abs(o), TAU)
 
 
-def admissible_levels(c0, var, valid, pivot, count, J, M, gamma, min_pivot, delta, pivot_rel=0.02):
+def pivot_band(piv, kappa):
+    """How far an FP32 pivot of the equilibrated normal matrix may lie from the FP64 one: a few 1e-6
+    absolute for a well-conditioned matrix, and relative to the pivot about (n U32) kappa for a
+    matrix of condition kappa (entrywise relative perturbations eps of the moment sums move a pivot
+    by up to about eps kappa of itself; eps is the rounding of sums of up to PIVOT_N terms)."""
+    k = 0.0 if kappa is None else np.where(np.isfinite(kappa), kappa, 0.0)
+    return 1e-5 + PIVOT_N * U32 * k * np.abs(piv)
+
+
+def admissible_levels(c0, var, valid, pivot, count, J, M, gamma, min_pivot, delta, pivot_rel=0.02, kappa=None):
     """Set of levels the choice rule can reach when every interval end moves by up to `delta`
-    and every usability test whose pivot lies within pivot_rel of min_pivot may go either way."""
+    and every usability test whose pivot lies within pivot_rel of min_pivot, or within the FP32
+    uncertainty of the pivot given the matrix's condition number (`kappa`, optional), may go
+    either way."""
     P = [1, 3, 6]
     out = set()
 
@@ -50,10 +66,10 @@ def admissible_levels(c0, var, valid, pivot, count, J, M, gamma, min_pivot, delt
         if count[l] < P[order]:
             return [False]
         piv = pivot[l]
-        # FP32 pivots of the equilibrated matrix are good to a few 1e-6; within the band either
-        # decision is correct (the oracle reports C_0 for such fits either way)
-        if np.isfinite(piv) and abs(piv - min_pivot) <= pivot_rel * max(min_pivot, 1e-12) + 1e-5 and \
-                np.isfinite(c0[l]):
+        # within the band either decision is correct (the oracle reports C_0 for such fits either
+        # way); an FP32 factorisation cannot place the pivot of a near-singular matrix more closely
+        band = pivot_rel * max(min_pivot, 1e-12) + pivot_band(piv, None if kappa is None else kappa[l])
+        if np.isfinite(piv) and abs(piv - min_pivot) <= band and np.isfinite(c0[l]):
             return [True, False]
         return [bool(valid[l])]
 
@@ -114,12 +130,17 @@ def compare(gpu_out, gpu_choice, orc, pixels, J, M, gamma, min_pivot, rel_tol=RE
                 gch = -1
             if gch is not None and gch != och:
                 lv = orc
-                ok = lv["valid"][i, c].astype(bool)
+                kap = lv["kappa"][i, c] if "kappa" in lv else None
+                # levels the GPU may use: usable ones, and those whose usability FP32 cannot decide
+                piv = lv["pivot"][i, c]
+                ambiguous = np.isfinite(piv) & np.isfinite(lv["c0"][i, c]) & \
+                    (np.abs(piv - min_pivot) <= 0.02 * max(min_pivot, 1e-12) + pivot_band(piv, kap))
+                ok = lv["valid"][i, c].astype(bool) | ambiguous
                 tl = np.where(ok, level_tol(lv["c0"][i, c], lv["efit"][i, c], lv["ew"][i, c], rel_tol), 0.0)
                 hs = gamma * np.sqrt(np.maximum(np.where(ok, lv["var"][i, c], 0.0), 0.0))
                 delta = 4.0 * float(np.nanmax(tl)) + 1e-4 * float(hs.max())
                 adm = admissible_levels(lv["c0"][i, c], lv["var"][i, c], lv["valid"][i, c], lv["pivot"][i, c],
-                                        lv["count"][i, c], J, M, gamma, min_pivot, delta=delta)
+                                        lv["count"][i, c], J, M, gamma, min_pivot, delta=delta, kappa=kap)
                 if gch not in adm:
                     fails.append((i, c, "choice", gch, och, sorted(adm), g, o))
                     continue

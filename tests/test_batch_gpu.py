@@ -1,7 +1,11 @@
-"""Batched reconstruction: many uneven frames in one persistent, graph-recorded kernel launch.
+"""Batched reconstruction: many uneven frames in one graph-recorded launch.
 
-Each frame's result must equal its single-frame reconstruction (same per-pixel arithmetic), for
-every launch configuration the autotuner may pick; one frame is also checked against the oracle.
+Form 0 (one grid per frame) runs each frame's single-frame kernel, so its results must equal the
+single-frame reconstruction bit for bit, for every launch configuration the autotuner may pick.
+Form 1 (persistent kernels over a tile list) walks the window once per scale where the
+single-frame kernel feeds several scales from one walk, so its sums round differently: its
+frames must equal the oracle within the parity tolerance. One frame of each batch is also checked
+against the oracle.
 """
 import dataclasses
 
@@ -61,6 +65,27 @@ def _same(a, b):
         np.testing.assert_array_equal(oa, ob)
 
 
+def _against_oracle(items, got, n_pix=200):
+    for (rig, fr, _, _, _), (out, ch) in zip(items, got):
+        p = fr.params
+        if p.out_w * p.out_h == 0:
+            assert out.size == 0
+            continue
+        r = np.random.default_rng(rig)
+        pix = np.stack([r.integers(0, p.out_w, n_pix), r.integers(0, p.out_h, n_pix)], axis=1)
+        o = oracle.reconstruct(fr.sensors, p, pix, levels=True, kappa=True)
+        parity.compare(out[:, pix[:, 1], pix[:, 0]], ch[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
+                       p.ici_gamma, p.min_pivot)
+
+
+def _check(items, got, refs, form):
+    """Form 0: bit for bit the single-frame results; form 1: the oracle within tolerance."""
+    if form == 0:
+        _same(got, refs)
+    else:
+        _against_oracle(items, got)
+
+
 def test_batch_equals_single_frames_for_every_configuration(ctx):
     """Uneven frames (sizes, sensor counts 2-4, orders 0-2, 1x and 1.5x outputs) in one launch."""
     from paper_1308_4908_gb300 import hdr
@@ -72,7 +97,7 @@ def test_batch_equals_single_frames_for_every_configuration(ctx):
     for cfg in cfgs:
         for _, _, _, out, _ in items:
             out.fill_(-7.0)
-        _same(_batch(ctx, items, cfg), refs)
+        _check(items, _batch(ctx, items, cfg), refs, cfg.form)
 
 
 @pytest.mark.parametrize("form", [0, 1])
@@ -86,9 +111,9 @@ def test_batch_replays_with_new_contents(ctx, form):
     ib = _prepare(ctx, b, base_rig=20)
     ra, rb = _single(ctx, ia), _single(ctx, ib)
     cfg = hdr.hdr_batch_config(16, 0, 1, form)
-    _same(_batch(ctx, ia, cfg), ra)
-    _same(_batch(ctx, ib, cfg), rb)
-    _same(_batch(ctx, ia, cfg), ra)
+    _check(ia, _batch(ctx, ia, cfg), ra, form)
+    _check(ib, _batch(ctx, ib, cfg), rb, form)
+    _check(ia, _batch(ctx, ia, cfg), ra, form)
 
 
 def test_tuner_picks_a_configuration_and_batch_uses_it(ctx):
@@ -99,7 +124,7 @@ def test_tuner_picks_a_configuration_and_batch_uses_it(ctx):
     hf = [ctx.frame(rig, fr.params, raws, out, ch, keep) for rig, fr, raws, out, ch in items]
     best = ctx.tune_batch(hf)
     assert best.tile_h in (8, 16) and 0 <= best.ctas_per_sm <= 8 and best.cost_order in (0, 1) and best.form in (0, 1)
-    _same(_batch(ctx, items), refs)        # cfg None -> the tuned configuration
+    _check(items, _batch(ctx, items), refs, best.form)        # cfg None -> the tuned configuration
 
 
 def test_batch_frame_against_oracle(ctx):
@@ -141,7 +166,7 @@ def test_batch_with_empty_and_one_pixel_frames(ctx, form):
     frames[1] = dataclasses.replace(frames[1], params=dataclasses.replace(frames[1].params, out_w=1, out_h=1))
     items = _prepare(ctx, frames, base_rig=56)
     refs = _single(ctx, items)
-    _same(_batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form)), refs)
+    _check(items, _batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form)), refs, form)
 
 
 @pytest.mark.parametrize("form", [0, 1])

@@ -107,7 +107,7 @@ def check_levels(ctx, fr):
             gc0 = lv[c, l, pix[:, 1], pix[:, 0], 0]
             gv = lv[c, l, pix[:, 1], pix[:, 0], 1]
             ov, oc0, ovar, piv = o["valid"][:, c, l], o["c0"][:, c, l], o["var"][:, c, l], o["pivot"][:, c, l]
-            clear = np.abs(piv - p.min_pivot) > 0.02 * p.min_pivot + 1e-5
+            clear = np.abs(piv - p.min_pivot) > 0.02 * p.min_pivot + parity.pivot_band(piv, o["kappa"][:, c, l])
             both = clear & (ov == 1)
             assert np.all(np.isfinite(gc0[both])), (c, l)
             assert np.all(np.isnan(gc0[clear & (ov == 0)])), (c, l)

@@ -263,3 +263,27 @@ def test_condition_known_spectrum(n):
         # eps kappa relative
         assert got == pytest.approx(kappa, rel=1e-12 * kappa + 1e-9)
     assert oracle.condition(np.diag([1.0, 0.0, 2.0])) == math.inf
+
+
+def test_value_mode_from_raw_reproduces_the_raw_fit():
+    """Eq. 18's f and Eq. 20's s2 written out per pixel (saturated pixels excluded) and fed back in
+    value mode give the raw-mode result to rounding, including per-pixel calibration frames and a
+    saturated region; rounded to FP32 they move C_0 by a few units of FP32 rounding of its terms."""
+    fr = synth.paper_scale(size=40, seed=91)
+    r = np.random.default_rng(2)
+    s0 = fr.sensors[0]
+    s0.bias_frame = 64.0 + r.normal(0.0, 1.5, (s0.height, s0.width))
+    s0.prnu_frame = 1.0 + r.normal(0.0, 0.02, (s0.height, s0.width))
+    s0.raw[10:14, 5:30] = 4095
+    pix = np.array([[u, v] for u in range(2, 40, 5) for v in range(1, 40, 4)])
+    base = oracle.reconstruct(fr.sensors, fr.params, pix, levels=True)
+    val = oracle.reconstruct(oracle.value_sensors(fr.sensors), fr.params, pix, levels=True)
+    np.testing.assert_array_equal(val["choice"], base["choice"])
+    np.testing.assert_array_equal(val["count"], base["count"])
+    np.testing.assert_allclose(val["out"], base["out"], rtol=1e-12, atol=1e-12)
+    r32 = oracle.reconstruct(oracle.value_sensors(fr.sensors, round_to=np.float32), fr.params, pix, levels=True)
+    same = (r32["choice"] == base["choice"]) & np.isfinite(base["out"])
+    lvl = np.clip(base["choice"], 0, None)[..., None]
+    efit = np.take_along_axis(base["efit"], lvl, axis=2)[..., 0]
+    dev = np.abs(r32["out"] - base["out"])[same] / (2.0 ** -24 * efit[same])
+    assert same.mean() > 0.95 and dev.max() < 4.0, (same.mean(), dev.max())

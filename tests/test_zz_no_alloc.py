@@ -6,7 +6,8 @@ rig's per-pixel calibration frames) in a fixed device array inside the library. 
 it through the C ABI twice in a row - first a rig with per-pixel calibration frames, then a
 different rig with scalar calibration, so the second call runs over the first call's leftovers -
 and checks each result against the context-based entry point within the parity tolerance used by
-the other GPU tests. This file is named to be collected last.
+the other GPU tests; one result is also checked against the FP64 oracle, and the free device memory
+is checked to stay the same across a call. This file is named to be collected last.
 """
 import dataclasses
 
@@ -96,3 +97,34 @@ def test_noalloc_rejects_frames_beyond_its_scratch():
                                     out.data_ptr())
     assert ei.value.status == hdr.HDR_E_UNSUPPORTED
     assert "scratch" in str(ei.value)
+
+
+def test_noalloc_output_matches_the_oracle_and_allocates_nothing():
+    """The entry point's own result against the FP64 oracle on sampled pixels (parity rule), and
+    the device memory the driver reports free is the same before and after a call: a first call
+    with the same configuration loads the kernels, the second may allocate nothing."""
+    import oracle
+    from paper_1308_4908_gb300 import hdr
+    fr = _frames_rig()
+    p = fr.params
+    hp = hdr.params_struct(p)
+    raws = [torch.from_numpy(s.raw).cuda() for s in fr.sensors]
+    ptrs = [int(t.data_ptr()) for t in raws]
+    keep = []
+    descs = [hdr.sensor_desc(s, keep) for s in fr.sensors]
+    out = torch.full((3, p.out_h, p.out_w), -1.0, device="cuda")
+    choice = torch.empty((3, p.out_h, p.out_w), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    hdr.hdr_reconstruct_noalloc(0, descs, hp, ptrs, out.data_ptr(), choice.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    hdr.hdr_reconstruct_noalloc(0, descs, hp, ptrs, out.data_ptr(), choice.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    r = np.random.default_rng(12)
+    pix = np.stack([r.integers(0, p.out_w, 400), r.integers(0, p.out_h, 400)], axis=1)
+    o = oracle.reconstruct(fr.sensors, p, pix, levels=True)
+    g, gc = out.cpu().numpy(), choice.cpu().numpy()
+    parity.compare(g[:, pix[:, 1], pix[:, 0]], gc[:, pix[:, 1], pix[:, 0]], o, pix, len(p.sigmas), p.order,
+                   p.ici_gamma, p.min_pivot)
