@@ -509,7 +509,7 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
   // a usable fit's equilibrated pivots lie in (min_pivot, 1]: when min_pivot * cond_fallback >= 2
   // their spread never exceeds cond_fallback and the FP64 re-solve cannot trigger
   const bool f64_possible = p->cond_fallback > 0.0 && (p->min_pivot - 1e-4) * p->cond_fallback < 2.0;
-  if (L.mode == LPA_SEARCHED && !f64_possible) L.mode = LPA_SEARCHED_F32;
+  if (!f64_possible) L.mode = lpa_mode_to_f32(L.mode);
   if (L.mode != LPA_TABULATED) {  // each thread's sample cell in each sensor (tables need none)
     off = (off + 15) / 16 * 16;
     L.off_pos = off;
@@ -1316,7 +1316,8 @@ hdr_status lpa_launch_mode(hdr_ctx *ctx, int32_t rig_id, const hdr_params *param
   LpaLaunch L;
   s = plan(ctx, ctx->rigs[rig_id], &p, raw_dev, L, reach);
   if (s) return s;
-  L.mode = mode;
+  // the plan picked the FP32-only variant when these parameters cannot trigger the FP64 re-solve
+  L.mode = lpa_mode_f32(L.mode) ? lpa_mode_to_f32(mode) : mode;
   L.aux = aux;
   L.out = out_dev;
   L.choice = choice_dev;

@@ -423,9 +423,9 @@ struct Ici {
 
 // ---------------------------------------------------------------- kernel
 
-// Scales per walk of the window cells: the searched window of order 0 to 2 with plain FP32 sums
-// feeds up to four nested scales from one walk (their sums stay in registers); the other variants
-// walk once per scale.
+// Scales per walk of the window cells: the searched and steered windows with plain FP32 sums feed
+// up to four nested scales from one walk at orders 0 and 1, two at order 2 when the FP64 re-solve
+// is compiled out (their sums stay in registers); the other variants walk once per scale.
 #ifndef LPA_MULTI_SCALE
 #define LPA_MULTI_SCALE 2      // order 2
 #endif
@@ -434,10 +434,11 @@ struct Ici {
 #endif
 template <int ORDER, bool COMP, int MODE>
 struct MultiScale {
-  static constexpr int value = COMP ? 1
-                               : MODE == LPA_SEARCHED_F32 ? (ORDER == 2 ? LPA_MULTI_SCALE : LPA_MULTI_SCALE_LOW)
-                               : MODE == LPA_SEARCHED    ? (ORDER == 2 ? 1 : LPA_MULTI_SCALE_LOW)
-                                                         : 1;
+  static constexpr int value =
+      COMP ? 1
+      : lpa_mode_f32(MODE) ? (ORDER == 2 ? LPA_MULTI_SCALE : LPA_MULTI_SCALE_LOW)
+      : (MODE == LPA_SEARCHED || MODE == LPA_STEERED) ? (ORDER == 2 ? 1 : LPA_MULTI_SCALE_LOW)
+                                                      : 1;
 };
 
 // sensor-space positions are clamped to +-LPA_FAR px (far outside any sensor) before integer conversion
@@ -462,7 +463,7 @@ __device__ __forceinline__ float2 weights(float K, float2 fv) {
 template <int ORDER, int MODE, class MOM>
 __device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R2, float cexp, float taper,
                                             float4 Q) {
-  constexpr bool STEER = MODE == LPA_STEERED;
+  constexpr bool STEER = lpa_mode_steered(MODE);
   // the variance sums take w^2 s2 = K w for the inverse-variance weight; with the printed weight
   // K / s (fv.y = 1 / s) it is K^2
   constexpr bool LIT = MODE == LPA_LITERAL;
@@ -490,19 +491,29 @@ __device__ __forceinline__ void window_cell(MOM &m, float2 D, float2 fv, float R
 template <int ORDER, int NSP, int MODE, class MOM>
 __device__ __forceinline__ void window_cell_ms(MOM (&m)[NSP], float2 D, float2 fv, const float (&R2)[NSP],
                                                const float (&cexp)[NSP], float taper, float4 Q) {
-  constexpr bool STEER = MODE == LPA_STEERED;
+  constexpr bool STEER = lpa_mode_steered(MODE);
   constexpr bool LIT = MODE == LPA_LITERAL;
   const float2 D2 = __fmul2_rn(D, D);
   const float r2 = STEER ? fmaf(Q.x, D2.x, fmaf(Q.z, D2.y, 2.f * Q.y * (D.x * D.y))) : D2.x + D2.y;
   if (!(r2 < R2[NSP - 1] && sample_ok(fv))) return;
   float sm[15];
   if constexpr (ORDER > 0) MOM::monomials(D, D2, sm);
+  // two scales per walk (order 2): both window values first, in one paired multiply and add (the
+  // same roundings as one at a time), so that their ex2 latencies overlap (-1 %; with four scales
+  // per walk the values of scales that miss the sample cost more than that)
+  float Kq[NSP];
+  if constexpr (NSP == 2) {
+    const float2 A = __fmul2_rn(make_float2(r2, r2), make_float2(cexp[0], cexp[1]));
+    const float2 E = __fadd2_rn(make_float2(ex2_approx(A.x), ex2_approx(A.y)), make_float2(-taper, -taper));
+    Kq[0] = E.x;
+    Kq[1] = E.y;
+  }
   // largest scale first; the windows are nested, so the first one that misses ends the loop
   // (a loop with an exit, not a chain of tests: no reconvergence point per scale)
 #pragma unroll
   for (int q = NSP - 1; q >= 0; q--) {
     if (!(r2 < R2[q])) break;
-    const float K = ex2_approx(r2 * cexp[q]) - taper;
+    const float K = NSP == 2 ? Kq[q] : ex2_approx(r2 * cexp[q]) - taper;
     const float2 W = weights(K, fv);
     if constexpr (ORDER == 0) m[q].add0(W.x, W.y, (LIT ? K : W.x) * K, 1.f);
     else m[q].adds(sm, D, D2, W.x, W.y, (LIT ? K : W.x) * K);
@@ -523,7 +534,7 @@ __device__ __forceinline__ void walk_sensor(const LpaSensorK &S, int4 pos, int c
   const int PW = S.box_w >> 1, PH = S.box_h >> 1;
   const float2 *planes = reinterpret_cast<const float2 *>(smem + S.off_planes);
   const float a00 = S.A[0], a01 = S.A[1], a10 = S.A[2], a11 = S.A[3];
-  constexpr bool STEER = MODE == LPA_STEERED;
+  constexpr bool STEER = lpa_mode_steered(MODE);
   float hx, hy;
   if constexpr (STEER) {
     // sensor-space bounding box of the support D^T B D < R^2, B = A^T C A (d = A D)
@@ -792,8 +803,8 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   const size_t opix = (size_t)v * RD(L.out_w) + u;
   const float log2e = 1.4426950408889634f;
 
-  constexpr bool TAB = MODE == LPA_TABULATED, STEER = MODE == LPA_STEERED, GRAD = MODE == LPA_GRADIENTS;
-  constexpr bool F64 = MODE != LPA_SEARCHED_F32;  // the FP64 re-solve is compiled in
+  constexpr bool TAB = MODE == LPA_TABULATED, STEER = lpa_mode_steered(MODE), GRAD = MODE == LPA_GRADIENTS;
+  constexpr bool F64 = !lpa_mode_f32(MODE);  // the FP64 re-solve is compiled in
   // the pixel's point in each sensor, once: anchor (FP64 at the 8x8 block corner) + small FP32
   // step, split into sample cell and fraction; every channel and scale reads it back
   int4 *pos = reinterpret_cast<int4 *>(smem + RD(L.off_pos)) + tid;

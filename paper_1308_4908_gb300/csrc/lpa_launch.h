@@ -69,7 +69,7 @@ struct LpaLaunch {
   // the pixel's even lattice cell.
   const int4 *tab_hdr;           // {first, count, (qx_min & 0xffff) | (qx_max << 16), same for qy}
   const float4 *tab_cells;
-  // Kernel mode (LPA_SEARCHED .. LPA_SEARCHED_F32 below). Adaptive reconstruction (Sections 5.4-5.5):
+  // Kernel mode (LPA_SEARCHED .. LPA_STEERED_F32 below). Adaptive reconstruction (Sections 5.4-5.5):
   // LPA_STEERED reads the steering matrix of each output pixel from aux ([out_h][out_w][3]: C11,
   // C12, C22); LPA_GRADIENTS writes the gradient of the green fit to aux ([out_h][out_w][2]).
   // LPA_LITERAL: the searched window with the noise weight printed in Eq. 6 (K / s, not K / s2).
@@ -77,10 +77,25 @@ struct LpaLaunch {
   float *aux;
 };
 
-// LPA_SEARCHED_F32: the searched window with every fit solved in FP32 only, for parameters under
-// which the FP64 re-solve can never trigger (min_pivot * cond_fallback >= 2: a usable fit's
-// equilibrated pivots lie in (min_pivot, 1], so their spread stays below cond_fallback).
-enum { LPA_SEARCHED = 0, LPA_TABULATED = 1, LPA_STEERED = 2, LPA_GRADIENTS = 3, LPA_LITERAL = 4, LPA_SEARCHED_F32 = 5 };
+// LPA_SEARCHED_F32, LPA_STEERED_F32: the searched or steered window with every fit solved in FP32
+// only, for parameters under which the FP64 re-solve can never trigger ((min_pivot - 1e-4) *
+// cond_fallback >= 2: a usable fit's equilibrated pivots lie in (min_pivot, 1], so their spread
+// stays below cond_fallback).
+enum {
+  LPA_SEARCHED = 0,
+  LPA_TABULATED = 1,
+  LPA_STEERED = 2,
+  LPA_GRADIENTS = 3,
+  LPA_LITERAL = 4,
+  LPA_SEARCHED_F32 = 5,
+  LPA_STEERED_F32 = 6
+};
+__host__ __device__ constexpr bool lpa_mode_steered(int mode) { return mode == LPA_STEERED || mode == LPA_STEERED_F32; }
+__host__ __device__ constexpr bool lpa_mode_f32(int mode) { return mode == LPA_SEARCHED_F32 || mode == LPA_STEERED_F32; }
+// the FP32-only variant of a mode, where it has one
+__host__ __device__ constexpr int lpa_mode_to_f32(int mode) {
+  return mode == LPA_SEARCHED ? LPA_SEARCHED_F32 : mode == LPA_STEERED ? LPA_STEERED_F32 : mode;
+}
 
 // Several frames in one graph launch: the tile list is grouped by polynomial order and each
 // order's persistent kernel takes tiles from its own segment. The tile list, the segment bounds

@@ -13,7 +13,7 @@ namespace lpa_orders {
 template <int ORDER, int MODE, int TH>
 constexpr bool instantiated() {
   if (MODE == LPA_GRADIENTS) return ORDER == 1 && TH == 16;
-  if (MODE == LPA_STEERED || MODE == LPA_LITERAL) return TH == 16;
+  if (lpa_mode_steered(MODE) || MODE == LPA_LITERAL) return TH == 16;
   return true;
 }
 
@@ -33,6 +33,7 @@ const void *kernel_mode(int mode) {
     case LPA_GRADIENTS: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_GRADIENTS>();
     case LPA_LITERAL: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_LITERAL>();
     case LPA_SEARCHED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED_F32>();
+    case LPA_STEERED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED_F32>();
     default: return nullptr;
   }
 }
