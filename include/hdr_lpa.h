@@ -155,14 +155,34 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
                                 const uint16_t *const *raw_host, void *out_host, uint8_t *choice_host,
                                 void *cuda_stream);
 
+/* Parameters of the adaptive reconstruction (Sections 5.4-5.5; the three passes are described
+ * with hdr_reconstruct_adaptive below). */
+typedef struct {
+  double grad_sigma;   /* R/B scale of the pass-1 gradient fit (G uses green_ratio times it) */
+  double window_sigma; /* Gaussian scale of pass 2, in output pixels; 3 window_sigma <= 10   */
+  double alpha;        /* structure sensitivity in [0, 4] (0: gamma = 1)                      */
+  double lambda1;      /* elongation regulariser in [1e-6, 1e6]                               */
+  double lambda2;      /* scaling regulariser in [1e-12, 1e12]                                */
+  double min_eig;      /* clamp of C's eigenvalues, 1e-6 <= min_eig <= max_eig <= 1e6; the   */
+  double max_eig;      /*   staged window footprint grows by 1 / sqrt(min_eig)                */
+  double grad_scale;   /* pass 2 uses grad_scale times the gradients, in (0, 1e6]: the paper
+                          fixes lambda1 and lambda2 without stating the unit of the radiant
+                          power, so this sets that unit (1 = the unit of the rig's calibration) */
+} hdr_calpa_params;
+
 /* One frame of a batch: rig, parameters and caller-owned device buffers, as for
- * hdr_reconstruct (raw_dev[s] for s < the rig's sensor count). */
+ * hdr_reconstruct (raw_dev[s] for s < the rig's sensor count). With `calpa` set the frame is
+ * reconstructed with the adaptive windows of Sections 5.4-5.5 exactly as hdr_reconstruct_adaptive
+ * does (gradient and steering-matrix passes, then the steered fit); the two first passes run on
+ * the batch's stream before its graph launch, in scratch the context owns (the serving loop keeps
+ * a frame's scratch in its pool block). */
 typedef struct {
   int32_t rig_id;
   const hdr_params *params;
   const uint16_t *raw_dev[HDR_MAX_SENSORS];
   void *out_dev;
   uint8_t *choice_dev;          /* optional level map, NULL = not written */
+  const hdr_calpa_params *calpa; /* NULL = the window of Eq. 8; else the adaptive window */
 } hdr_frame;
 
 /* Launch configuration of a batched reconstruction. Both forms run as one CUDA-graph launch:
@@ -175,6 +195,9 @@ typedef struct {
   int32_t ctas_per_sm;          /* form 1: persistent CTAs per SM; 0 = as many as fit            */
   int32_t cost_order;           /* 1 = the most expensive frames first, 0 = the given order      */
   int32_t form;                 /* 0 or 1, see above                                              */
+  int32_t px_per_thread;        /* form 0: output pixels per thread, 0 or 1 = one; 2 = two, each
+                                   thread its pixels one after the other (tile_h 16 only: 16-row
+                                   tiles of 128 threads); adaptive frames always take one        */
 } hdr_batch_config;
 
 /* Reconstruct n_frames (1..4096) frames of any sizes, rigs, orders and scales in one graph launch
@@ -184,9 +207,10 @@ typedef struct {
  * one is still reading) and clears the tile counters. `cfg` NULL = the configuration
  * hdr_tune_batch found for batches of this kind, else the default {16, 0, 1, 0}. All frames must
  * use the same `accum` and weight_mode 0 (HDR_E_UNSUPPORTED otherwise). Asynchronous like
- * hdr_reconstruct. Results are identical to reconstructing each frame with hdr_reconstruct, except
- * that form 1 searches every window: for a frame that hdr_reconstruct reads from tabulated weights
- * (tab_weights), form 1 gives the same fit with different rounding. */
+ * hdr_reconstruct. Form 0 results are identical to reconstructing each frame with hdr_reconstruct
+ * (hdr_reconstruct_adaptive for frames with `calpa`); form 1 walks every window once per scale
+ * and searches it (no tabulated weights), so its sums round differently: the same fit within the
+ * parity tolerance. A batch with adaptive frames always runs form 0. */
 hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames,
                                  const hdr_batch_config *cfg, void *cuda_stream);
 
@@ -203,11 +227,13 @@ hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frame
  * thread. A scheduler thread admits them in arrival order while a slot and room in the server's
  * device-memory pool are free, copies their raw frames into the pool on a copy stream, and
  * repeatedly launches one batched step over the pending tiles of the admitted frames, oldest
- * frame first, at most step_tiles per step, with up to two steps queued on the device: frames that
+ * frame first, at most step_tiles per step, with up to three steps queued on the device: frames that
  * arrive while a step runs join a later one (continuous batching at tile granularity). A frame
  * whose tiles are all done is copied back to its host buffers on a second copy stream and its
- * memory returns to the pool. Each pixel is computed as hdr_reconstruct computes it, whatever
- * else shares the step. The server uses its context exclusively until hdr_server_destroy (no
+ * memory returns to the pool. Each pixel is computed as hdr_reconstruct (an adaptive request: as
+ * hdr_reconstruct_adaptive) computes it, whatever else shares the step; an adaptive request runs
+ * its gradient and steering-matrix passes in the step that takes its first tiles, into scratch in
+ * its pool block (20 bytes per output pixel), and needs the default tile height (16). The server uses its context exclusively until hdr_server_destroy (no
  * other call on that context meanwhile); rigs must be set before serving starts. A device-side
  * error fails every request whose tiles were on the device when it was seen. */
 typedef struct hdr_server hdr_server;
@@ -227,6 +253,8 @@ typedef struct {
   void *out_host;               /* host output [3][out_h][out_w] of out_dtype, written at completion */
   uint8_t *choice_host;         /* optional host level map, NULL = not produced                  */
   int32_t stream_id;            /* caller's video stream, for its own bookkeeping               */
+  int32_t adaptive;             /* 1 = the adaptive reconstruction (Sections 5.4-5.5) with calpa */
+  hdr_calpa_params calpa;       /* copied at submission; read when adaptive = 1                  */
 } hdr_request;
 
 typedef struct {
@@ -334,18 +362,7 @@ hdr_status hdr_calib_exposure(hdr_ctx *ctx, const float *flat_mean, const float 
  * determinant normalisation: the fit's solution does not depend on a constant factor of the
  * weights), the weights of pass 2 are Gaussian in the output-pixel distance, and the clamp of
  * C's eigenvalues bounds every window between k sigma_J / sqrt(max_eig) and k sigma_J / sqrt(min_eig). */
-typedef struct {
-  double grad_sigma;   /* R/B scale of the pass-1 gradient fit (G uses green_ratio times it) */
-  double window_sigma; /* Gaussian scale of pass 2, in output pixels; 3 window_sigma <= 10   */
-  double alpha;        /* structure sensitivity in [0, 4] (0: gamma = 1)                      */
-  double lambda1;      /* elongation regulariser in [1e-6, 1e6]                               */
-  double lambda2;      /* scaling regulariser in [1e-12, 1e12]                                */
-  double min_eig;      /* clamp of C's eigenvalues, 1e-6 <= min_eig <= max_eig <= 1e6; the   */
-  double max_eig;      /*   staged window footprint grows by 1 / sqrt(min_eig)                */
-  double grad_scale;   /* pass 2 uses grad_scale times the gradients, in (0, 1e6]: the paper
-                          fixes lambda1 and lambda2 without stating the unit of the radiant
-                          power, so this sets that unit (1 = the unit of the rig's calibration) */
-} hdr_calpa_params;
+/* hdr_calpa_params: defined with the frame description above. */
 
 /* Defaults: grad_sigma 1.2, window_sigma 1, alpha 0.3, lambda1 1, lambda2 1e-3 (as the paper
  * fixes them), eigenvalues clamped to [0.25, 16], grad_scale 0.1 (chosen on synthetic HDR scenes

@@ -121,6 +121,20 @@ hdr_status check_calpa(const hdr_calpa_params *c) {
 
 }  // namespace
 
+hdr_status lpa_check_calpa(const hdr_calpa_params *c) { return check_calpa(c); }
+
+double lpa_calpa_reach(const hdr_calpa_params *calpa) { return 1.0 / std::sqrt(calpa->min_eig); }
+
+hdr_status lpa_calpa_prepare(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const hdr_calpa_params *calpa,
+                             const uint16_t *const *raw_dev, float *scratch, cudaStream_t st) {
+  const size_t npx = (size_t)params->out_w * params->out_h;
+  if (npx == 0) return HDR_OK;
+  float *grad = scratch, *metric = scratch + npx * 2;
+  hdr_status s = hdr_calpa_gradients(ctx, rig_id, params, calpa, raw_dev, grad, st);
+  if (s) return s;
+  return hdr_calpa_metric(ctx, params->out_w, params->out_h, calpa, grad, metric, st);
+}
+
 extern "C" {
 
 void hdr_calpa_params_default(hdr_calpa_params *c) {
@@ -194,7 +208,7 @@ hdr_status hdr_reconstruct_steered(hdr_ctx *ctx, int32_t rig_id, const hdr_param
   if (!params) return lpa_fail(HDR_E_INVALID, "params is NULL");
   if (!metric_dev && (long long)params->out_w * params->out_h > 0) return lpa_fail(HDR_E_INVALID, "metric_dev is NULL");
   return lpa_launch_mode(ctx, rig_id, params, raw_dev, LPA_STEERED, const_cast<float *>(metric_dev),
-                         1.0 / std::sqrt(calpa->min_eig), out_dev, choice_dev, (cudaStream_t)cuda_stream);
+                         lpa_calpa_reach(calpa), out_dev, choice_dev, (cudaStream_t)cuda_stream);
 }
 
 hdr_status hdr_reconstruct_adaptive(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,

@@ -942,17 +942,19 @@ double frame_cost(const hdr_params &p, int n_sensors) {
 }
 
 uint64_t batch_kind(const hdr_ctx *ctx, int n, const hdr_frame *frames) {
-  uint64_t orders = 0, max_s = 0, scales = 0, px = 0;
+  uint64_t orders = 0, max_s = 0, scales = 0, px = 0, adaptive = 0;
   for (int f = 0; f < n; f++) {
     const hdr_params *p = frames[f].params;
     orders |= 1ull << p->order;
+    adaptive |= frames[f].calpa ? 1 : 0;
     max_s = std::max<uint64_t>(max_s, ctx->rigs[frames[f].rig_id].n);
     scales = std::max<uint64_t>(scales, p->n_scales);
     px += (uint64_t)p->out_w * p->out_h;
   }
   uint64_t bucket = 0;
   while ((1ull << (bucket + 1)) <= px / 65536 + 1) bucket++;
-  return orders | (max_s << 4) | (scales << 8) | (bucket << 12) | ((uint64_t)frames[0].params->accum << 20);
+  return orders | (max_s << 4) | (scales << 8) | (bucket << 12) | ((uint64_t)frames[0].params->accum << 20) |
+         (adaptive << 21);
 }
 
 hdr_status check_batch(hdr_ctx *ctx, int32_t n, const hdr_frame *frames) {
@@ -971,6 +973,10 @@ hdr_status check_batch(hdr_ctx *ctx, int32_t n, const hdr_frame *frames) {
       return fail(HDR_E_INVALID, "frame %d: all frames of a batch must use the same accum", f);
     if (!F.out_dev && (long long)F.params->out_w * F.params->out_h > 0)
       return fail(HDR_E_INVALID, "frame %d: output pointer is NULL", f);
+    if (F.calpa) {
+      st = lpa_check_calpa(F.calpa);
+      if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
+    }
   }
   return HDR_OK;
 }
@@ -1088,16 +1094,57 @@ hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *
 // all of them) as independent kernel nodes of one graph, recorded once per shape; a replay only
 // updates the nodes' parameters.
 hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *ranges,
-                            const hdr_batch_config &cfg, cudaStream_t stream) {
+                            const hdr_batch_config &cfg, cudaStream_t stream, float *const *scratch) {
   BatchState &B = ctx->batch;
   TableHold hold(ctx->tabs);  // the plans of every frame stay valid until the launch
   std::vector<LpaLaunch> plans(n);
   std::vector<int> grid(n, 0);
+  // adaptive frames: gradients and steering matrices (5 floats per output pixel) in the caller's
+  // scratch, else in one context buffer shared by the batch
+  std::vector<float *> aux(n, nullptr);
+  if (!scratch) {
+    size_t total = 0;
+    for (int f = 0; f < n; f++)
+      if (frames[f].calpa) total += (size_t)frames[f].params->out_w * frames[f].params->out_h * 5;
+    if (total) {
+      void *base = nullptr;
+      hdr_status st = lpa_ctx_calpa_scratch(ctx, total * sizeof(float), &base);
+      if (st) return st;
+      float *p = static_cast<float *>(base);
+      for (int f = 0; f < n; f++)
+        if (frames[f].calpa) {
+          aux[f] = p;
+          p += (size_t)frames[f].params->out_w * frames[f].params->out_h * 5;
+        }
+    }
+  } else {
+    for (int f = 0; f < n; f++) aux[f] = frames[f].calpa ? scratch[f] : nullptr;
+  }
   for (int f = 0; f < n; f++) {
     const hdr_frame &F = frames[f];
-    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, true}, ctx->rigs[F.rig_id], F.params, F.raw_dev,
-                             plans[f], cfg.tile_h);
+    const size_t npx = (size_t)F.params->out_w * F.params->out_h;
+    if (F.calpa && npx > 0 && !aux[f]) return fail(HDR_E_INVALID, "frame %d: no scratch for the adaptive passes", f);
+    // the adaptive passes 1 and 2 of a frame run with the launch that takes its first tile
+    if (F.calpa && npx > 0 && (!ranges || ranges[f].x == 0)) {
+      hdr_status st = lpa_calpa_prepare(ctx, F.rig_id, F.params, F.calpa, F.raw_dev, aux[f], stream);
+      if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
+    }
+    hdr_params sp;
+    const hdr_params *pp = F.params;
+    if (F.calpa) {  // the steered window is searched (offsets and weights differ per pixel)
+      sp = *F.params;
+      sp.tab_weights = 0;
+      pp = &sp;
+    }
+    hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, !F.calpa}, ctx->rigs[F.rig_id],
+                             pp, F.raw_dev, plans[f], F.calpa ? 16 : cfg.tile_h,
+                             F.calpa ? lpa_calpa_reach(F.calpa) : 1.0);
     if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
+    if (F.calpa) {
+      plans[f].mode = lpa_mode_f32(plans[f].mode) ? LPA_STEERED_F32 : LPA_STEERED;
+      plans[f].aux = aux[f] + npx * 2;  // the steering matrices
+    }
+    plans[f].px = (cfg.px_per_thread == 2 && !F.calpa) ? 2 : 1;
     plans[f].out = F.out_dev;
     plans[f].choice = F.choice_dev;
     plans[f].levels = nullptr;
@@ -1112,7 +1159,8 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
     if (grid[f] > 0) order.push_back(f);
   if (cfg.cost_order) {
     std::vector<double> cost(n);
-    for (int f = 0; f < n; f++) cost[f] = frame_cost(*frames[f].params, ctx->rigs[frames[f].rig_id].n) * grid[f];
+    for (int f = 0; f < n; f++)
+      cost[f] = frame_cost(*frames[f].params, ctx->rigs[frames[f].rig_id].n) * grid[f] * (frames[f].calpa ? 3.0 : 1.0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   }
   if (order.empty()) return HDR_OK;
@@ -1122,16 +1170,18 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
   std::vector<void *> args(order.size());
   for (size_t k = 0; k < order.size(); k++) {
     const LpaLaunch &L = plans[order[k]];
-    const void *fn = lpa_kernel(L.order, comp, false, L.mode, cfg.tile_h);
-    if (!fn) return fail(HDR_E_INTERNAL, "no kernel for order %d, mode %d, tile height %d", L.order, L.mode, cfg.tile_h);
+    const void *fn = lpa_kernel(L.order, comp, false, L.mode, L.tile_h, L.px);
+    if (!fn)
+      return fail(HDR_E_INTERNAL, "no kernel for order %d, mode %d, tile height %d, %d pixels per thread", L.order,
+                  L.mode, L.tile_h, L.px);
     CUDA_TRY(lpa_opt_in(fn));
     // grid size and shared memory are set on each replay: graphs are kept per sequence of kernels
-    key.push_back({L.order * 8 + L.mode, comp ? 1 : 0, cfg.tile_h, 0, 0});
+    key.push_back({L.order * 8 + L.mode, comp ? 1 : 0, L.tile_h, L.px, 0});
     args[k] = &plans[order[k]];
     kp[k] = cudaKernelNodeParams{};
     kp[k].func = const_cast<void *>(fn);
     kp[k].gridDim = dim3((unsigned)grid[order[k]]);
-    kp[k].blockDim = dim3((unsigned)(LPA_TILE * cfg.tile_h));
+    kp[k].blockDim = dim3((unsigned)(LPA_TILE * L.tile_h / L.px));
     kp[k].sharedMemBytes = L.smem_bytes;
     kp[k].kernelParams = &args[k];
   }
@@ -1176,11 +1226,11 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
 
 // One batched launch over the listed tiles of several frames (see hdr_reconstruct_batch).
 hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, const int2 *ranges,
-                         const hdr_batch_config *cfg_in, cudaStream_t stream) {
+                         const hdr_batch_config *cfg_in, cudaStream_t stream, float *const *scratch) {
   hdr_status st = check_batch(ctx, n_frames, frames);
   if (st) return st;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  hdr_batch_config cfg = {16, 0, 1, 0};
+  hdr_batch_config cfg = {16, 0, 1, 0, 1};
   if (cfg_in) {
     cfg = *cfg_in;
   } else {
@@ -1190,7 +1240,12 @@ hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames
   if (cfg.tile_h != 8 && cfg.tile_h != 16) return fail(HDR_E_INVALID, "tile_h must be 8 or 16");
   if (cfg.ctas_per_sm < 0 || cfg.ctas_per_sm > 8) return fail(HDR_E_INVALID, "ctas_per_sm must be in [0, 8]");
   if (cfg.form != 0 && cfg.form != 1) return fail(HDR_E_INVALID, "form must be 0 or 1");
-  if (cfg.form == 0) return batch_run_frames(ctx, n_frames, frames, ranges, cfg, stream);
+  if (cfg.px_per_thread < 0 || cfg.px_per_thread > 2) return fail(HDR_E_INVALID, "px_per_thread must be 0, 1 or 2");
+  if (cfg.px_per_thread == 2 && (cfg.tile_h != 16 || cfg.form != 0))
+    return fail(HDR_E_INVALID, "two pixels per thread need tile_h 16 and form 0");
+  for (int f = 0; f < n_frames; f++)
+    if (frames[f].calpa) cfg.form = 0;  // the persistent kernels have no steered window
+  if (cfg.form == 0) return batch_run_frames(ctx, n_frames, frames, ranges, cfg, stream, scratch);
   uint32_t smem[3];
   int n_tiles[3];
   st = batch_plan(ctx, n_frames, frames, ranges, cfg, smem, n_tiles);
@@ -1347,10 +1402,12 @@ extern "C" hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_f
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
-  hdr_batch_config win = {16, 0, 1, 0};
+  hdr_batch_config win = {16, 0, 1, 0, 1};
   float win_ms = 1e30f;
-  const hdr_batch_config cands[] = {{16, 0, 1, 0}, {8, 0, 1, 0}, {16, 0, 0, 0}, {16, 0, 1, 1}, {16, 1, 1, 1},
-                                    {16, 2, 1, 1}, {8, 0, 1, 1},  {8, 2, 1, 1},  {8, 4, 1, 1},  {16, 0, 0, 1}};
+  // form, tile height, pixels per thread, persistent CTAs per SM and frame order
+  const hdr_batch_config cands[] = {{16, 0, 1, 0, 1}, {8, 0, 1, 0, 1}, {16, 0, 1, 0, 2}, {16, 0, 0, 0, 1},
+                                    {16, 0, 1, 1, 1}, {16, 1, 1, 1, 1}, {16, 2, 1, 1, 1}, {8, 0, 1, 1, 1},
+                                    {8, 2, 1, 1, 1},  {8, 4, 1, 1, 1},  {16, 0, 0, 1, 1}};
   for (const hdr_batch_config &c : cands) {
     st = hdr_reconstruct_batch(ctx, n_frames, frames, &c, cuda_stream);  // warm-up (and graph record)
     if (st == HDR_E_UNSUPPORTED) continue;

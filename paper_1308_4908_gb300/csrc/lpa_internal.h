@@ -4,10 +4,19 @@
 
 #include "hdr_lpa.h"
 
-// One persistent launch over tiles [ranges[f].x, ranges[f].y) of each frame (all tiles when
-// ranges is NULL); the implementation behind hdr_reconstruct_batch.
+// One batched launch over tiles [ranges[f].x, ranges[f].y) of each frame (all tiles when ranges
+// is NULL); the implementation behind hdr_reconstruct_batch. Adaptive frames (calpa set) keep
+// their gradients and steering matrices in scratch[f] (5 floats per output pixel), or, when
+// scratch is NULL, in scratch the context owns; their first two passes run in the launch that
+// takes their first tile.
 hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, const int2 *ranges,
-                         const hdr_batch_config *cfg, cudaStream_t stream);
+                         const hdr_batch_config *cfg, cudaStream_t stream, float *const *scratch = nullptr);
+// Validate adaptive-reconstruction parameters.
+hdr_status lpa_check_calpa(const hdr_calpa_params *c);
+// Passes 1 and 2 of the adaptive reconstruction of one frame into scratch (gradients [2 npx],
+// then steering matrices [3 npx]) on `st`.
+hdr_status lpa_calpa_prepare(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const hdr_calpa_params *calpa,
+                             const uint16_t *const *raw_dev, float *scratch, cudaStream_t st);
 int lpa_ctx_device(const hdr_ctx *ctx);
 // Sensors of a rig (0 if the rig is not defined) and each sensor's raw pitch and height.
 int lpa_ctx_rig_sensors(const hdr_ctx *ctx, int rig_id);
@@ -23,6 +32,8 @@ hdr_status lpa_take_status(hdr_ctx *ctx);
 // is written). The window is always searched.
 hdr_status lpa_launch_mode(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_dev,
                            int mode, float *aux, double reach, void *out_dev, uint8_t *choice_dev, cudaStream_t st);
+// Staging reach of the steered window for these adaptive parameters (1 / sqrt(min_eig)).
+double lpa_calpa_reach(const hdr_calpa_params *calpa);
 // Device scratch of at least `bytes` owned by the context for the adaptive reconstruction
 // (growing it waits for the device).
 hdr_status lpa_ctx_calpa_scratch(hdr_ctx *ctx, size_t bytes, void **ptr);

@@ -672,11 +672,12 @@ __device__ __forceinline__ T reread(const T &x) {
 // global descriptor, whose tensor maps the bulk copies use (otherwise `maps` is &L).
 // `phase` is the parity of the CTA's mbarrier use for this tile. Returns false when the CTA must
 // stop (a bounded wait ran out here or in another CTA).
-template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS, int MODE = LPA_SEARCHED>
+template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS, int MODE = LPA_SEARCHED, int PX = 1>
 __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch *maps, int tile, unsigned char *smem, uint64_t *mbar,
                                              uint32_t phase, int *fp_x0, int *fp_y0,
                                              Anchor (*anchors)[LPA_MAX_SENSORS]) {
-  constexpr int NT = LPA_TILE * TH;
+  constexpr int NT = LPA_TILE * TH;  // threads
+  constexpr int TR = TH * PX;        // tile rows: PX pixels per thread, TH rows apart
   const int tid = threadIdx.x;
   // descriptor fields used across the pixel loops: with a shared-memory descriptor they are read
   // again at each use rather than held in registers through the loops
@@ -684,7 +685,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   // once any CTA's bounded wait has run out, later CTAs retire at once
   if (*reinterpret_cast<volatile unsigned int *>(L.status) & LPA_ERR_TIMEOUT) return false;
   const int tu = tile % L.tiles_x, tv = tile / L.tiles_x;
-  const int u0 = tu * LPA_TILE, v0 = tv * TH;
+  const int u0 = tu * LPA_TILE, v0 = tv * TR;
   const int S = L.n_sensors;
 
   if (tid < S) {
@@ -694,7 +695,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
     double mnx = 1e300, mny = 1e300;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      double uu = u0 + (k & 1) * (LPA_TILE - 1), vv = v0 + (k >> 1) * (TH - 1);
+      double uu = u0 + (k & 1) * (LPA_TILE - 1), vv = v0 + (k >> 1) * (TR - 1);
       double qx = Sk.G[0] * uu + Sk.G[1] * vv + Sk.G[2];
       double qy = Sk.G[3] * uu + Sk.G[4] * vv + Sk.G[5];
       mnx = fmin(mnx, fmin(fmax(qx, -LPA_FAR), LPA_FAR));
@@ -707,7 +708,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
     fp_x0[tid] = x0;
     fp_y0[tid] = y0;
   }
-  constexpr int NA = 2 * (TH / LPA_ANCHOR);  // anchor blocks per tile
+  constexpr int NA = 2 * (TR / LPA_ANCHOR);  // anchor blocks per tile
   if (tid >= 32 && tid < 32 + NA * S) {
     const int k = tid - 32, a = k % NA, s = k / NA;
     const LpaSensorK &Sk = L.s[s];
@@ -788,179 +789,186 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   }
   __syncthreads();
 
-  // pixel of this thread: warp = parity class x half tile, lanes 8 x 4 at stride 2
-  const int warp = tid >> 5, lane = tid & 31;
-  const int par = warp & 3, hf = warp >> 2;
-  const int u = u0 + 2 * (lane & 7) + (par & 1);
-  const int v = v0 + 2 * ((lane >> 3) + 4 * hf) + (par >> 1);
-  const bool pix = (u < RD(L.out_w)) && (v < RD(L.out_h));
-  const int ab = ((u - u0) >> 3) + 2 * ((v - v0) >> 3);  // < NA
-  const int du = (u - u0) & 7, dv = (v - v0) & 7;
-  constexpr int P = n_unknowns(ORDER);
-  const int J = RD(L.n_scales);
-  const int NL = J + ORDER;
-  const size_t plane_px = (size_t)RD(L.out_w) * RD(L.out_h);
-  const size_t opix = (size_t)v * RD(L.out_w) + u;
-  const float log2e = 1.4426950408889634f;
-
-  constexpr bool TAB = MODE == LPA_TABULATED, STEER = lpa_mode_steered(MODE), GRAD = MODE == LPA_GRADIENTS;
-  constexpr bool F64 = !lpa_mode_f32(MODE);  // the FP64 re-solve is compiled in
-  // the pixel's point in each sensor, once: anchor (FP64 at the 8x8 block corner) + small FP32
-  // step, split into sample cell and fraction; every channel and scale reads it back
-  int4 *pos = reinterpret_cast<int4 *>(smem + RD(L.off_pos)) + tid;
-  if constexpr (!TAB) {
+  constexpr bool TAB_ = MODE == LPA_TABULATED;
+  if constexpr (!TAB_) {
     if (RD(L.off_pos) == 0u) {  // a plan without the position table (offset 0 holds a raw box)
       if (tid == 0) atomicOr(L.status, LPA_ERR_BOUNDS);
       return false;
     }
-#pragma unroll 1
-    for (int s = 0; s < S; s++) {
-      const Anchor &an = anchors[ab][s];
-      const LpaSensorK &Sk = L.s[s];
-      const float px = an.fx + (float)du * Sk.Gf[0] + (float)dv * Sk.Gf[1];
-      const float py = an.fy + (float)du * Sk.Gf[2] + (float)dv * Sk.Gf[3];
-      const float flx = floorf(px), fly = floorf(py);
-      pos[s * NT] = make_int4(an.ix + (int)flx, an.iy + (int)fly, __float_as_int(px - flx), __float_as_int(py - fly));
-    }
   }
-  float4 Q = make_float4(1.f, 0.f, 1.f, 0.f);  // steering matrix of this pixel (Section 5.4)
-  if constexpr (STEER)
-    if (pix) Q = make_float4(L.aux[opix * 3], L.aux[opix * 3 + 1], L.aux[opix * 3 + 2], 0.f);
-
-  using MOM = typename MomentsSel<ORDER, COMP>::type;
-  // the fit of one (channel, scale) from its moments: factorised unless no lane of the warp has as
-  // many samples as unknowns (such a fit is not usable whatever its pivots; on near-translational
-  // rigs the lanes share one sample layout, so whole warps qualify)
-  auto fit_of = [&](const MOM &m) {
-    FitOut f;
-    if (__all_sync(LPA_FULL, m.count() < (float)P)) {
-      f.valid = false;
-      f.c0 = f.var = f.c1 = f.c2 = 0.f;
-      f.dmin = f.dmax = 0.f;
-    } else {
-      f = solve_with_fallback<P, MOM, GRAD, F64>(m, RD(L.min_pivot), RD(L.cond_fallback));
-    }
-    return f;
-  };
-  auto put_level = [&](int c, int level, const FitOut &f) {
-    if (DIAG && pix) {
-      float *o = L.levels + (((size_t)c * NL + level) * plane_px + opix) * 2;
-      o[0] = f.valid ? f.c0 : __int_as_float(0x7fffffff);
-      o[1] = f.valid ? f.var : __int_as_float(0x7fffffff);
-    }
-  };
-  // order fallback at the largest scale (m holds its moments when any lane needs it), then the store
-  auto finish = [&](int c, Ici &ici, const MOM &m) {
-    const bool need = ici.choice == 255 && pix;
-    if (DIAG || __any_sync(LPA_FULL, need)) {
-      auto take = [&](const FitOut &f, int i) {
-        put_level(c, J + i, f);
-        if (ici.choice == 255 && f.valid) {
-          ici.choice = J + i;
-          ici.val = f.c0;
-        }
-      };
-      if constexpr (ORDER >= 1) take(fallback_fit<ORDER, 0, F64>(m, RD(L.min_pivot), RD(L.cond_fallback)), 0);
-      if constexpr (ORDER >= 2) take(fallback_fit<ORDER, 1, F64>(m, RD(L.min_pivot), RD(L.cond_fallback)), 1);
-    }
-    if (pix) {
-      if (RD(L.out_half))
-        reinterpret_cast<__half *>(RD(L.out))[c * plane_px + opix] = __float2half_rn(ici.val);
-      else
-        reinterpret_cast<float *>(RD(L.out))[c * plane_px + opix] = ici.val;
-      if (RD(L.choice)) RD(L.choice)[c * plane_px + opix] = (uint8_t)ici.choice;
-    }
-  };
-
-  // the persistent many-frame kernel walks once per scale (its register budget, shared by every
-  // frame it serves, has no room for the sums of several scales)
-  constexpr int NSP = GLOBAL_MAPS ? 1 : MultiScale<ORDER, COMP, MODE>::value;
-  if constexpr (NSP > 1) {
-    if (J >= 2) {
-      // all scales of a channel from one walk per sensor (up to NSP scales per pass): slot q of
-      // a pass holds scale j0 + q - lead, so that the pass's largest scale is always the last slot
+  // PX output pixels per thread, one after the other: slot k takes the rows k TH .. k TH + TH - 1
 #pragma unroll 1
-      for (int c = 0; c < 3; c++) {
-        Ici ici;
-        ici.reset(pix);
-        MOM m[NSP];
-        const float gsc = (c == 1) ? RD(L.green_ratio) : 1.f;
-        // the first pass takes what the later full passes leave (the small scales), so that the
-        // largest scales share the longest walk
-        const int npass = (J + NSP - 1) / NSP;
-#pragma unroll 1
-        for (int pass = 0, j0 = 0, nj = J - NSP * (npass - 1); pass < npass; pass++, j0 += nj, nj = NSP) {
-          if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
-          const int lead = NSP - nj;
-          float R2s[NSP], cxs[NSP];
-#pragma unroll
-          for (int q = 0; q < NSP; q++) {
-            const float sg = RD(L.sigma[q >= lead ? j0 + q - lead : j0]) * gsc;
-            const float Rq = RD(L.trunc_k) * sg;
-            R2s[q] = q >= lead ? Rq * Rq : -1.f;
-            cxs[q] = -log2e / (2.f * sg * sg);
-            m[q].zero();
+  for (int slot = 0; slot < PX; slot++) {
+    // pixel of this thread: warp = parity class x half tile, lanes 8 x 4 at stride 2
+    const int warp = tid >> 5, lane = tid & 31;
+    const int par = warp & 3, hf = warp >> 2;
+    const int u = u0 + 2 * (lane & 7) + (par & 1);
+    const int v = v0 + 2 * ((lane >> 3) + 4 * hf) + (par >> 1) + slot * TH;
+    const bool pix = (u < RD(L.out_w)) && (v < RD(L.out_h));
+    const int ab = ((u - u0) >> 3) + 2 * ((v - v0) >> 3);  // < NA
+    const int du = (u - u0) & 7, dv = (v - v0) & 7;
+    constexpr int P = n_unknowns(ORDER);
+    const int J = RD(L.n_scales);
+    const int NL = J + ORDER;
+    const size_t plane_px = (size_t)RD(L.out_w) * RD(L.out_h);
+    const size_t opix = (size_t)v * RD(L.out_w) + u;
+    const float log2e = 1.4426950408889634f;
+
+    constexpr bool TAB = MODE == LPA_TABULATED, STEER = lpa_mode_steered(MODE), GRAD = MODE == LPA_GRADIENTS;
+    constexpr bool F64 = !lpa_mode_f32(MODE);  // the FP64 re-solve is compiled in
+    // the pixel's point in each sensor, once: anchor (FP64 at the 8x8 block corner) + small FP32
+    // step, split into sample cell and fraction; every channel and scale reads it back
+    int4 *pos = reinterpret_cast<int4 *>(smem + RD(L.off_pos)) + tid;
+    if constexpr (!TAB) {
+  #pragma unroll 1
+      for (int s = 0; s < S; s++) {
+        const Anchor &an = anchors[ab][s];
+        const LpaSensorK &Sk = L.s[s];
+        const float px = an.fx + (float)du * Sk.Gf[0] + (float)dv * Sk.Gf[1];
+        const float py = an.fy + (float)du * Sk.Gf[2] + (float)dv * Sk.Gf[3];
+        const float flx = floorf(px), fly = floorf(py);
+        pos[s * NT] = make_int4(an.ix + (int)flx, an.iy + (int)fly, __float_as_int(px - flx), __float_as_int(py - fly));
+      }
+    }
+    float4 Q = make_float4(1.f, 0.f, 1.f, 0.f);  // steering matrix of this pixel (Section 5.4)
+    if constexpr (STEER)
+      if (pix) Q = make_float4(L.aux[opix * 3], L.aux[opix * 3 + 1], L.aux[opix * 3 + 2], 0.f);
+
+    using MOM = typename MomentsSel<ORDER, COMP>::type;
+    // the fit of one (channel, scale) from its moments: factorised unless no lane of the warp has as
+    // many samples as unknowns (such a fit is not usable whatever its pivots; on near-translational
+    // rigs the lanes share one sample layout, so whole warps qualify)
+    auto fit_of = [&](const MOM &m) {
+      FitOut f;
+      if (__all_sync(LPA_FULL, m.count() < (float)P)) {
+        f.valid = false;
+        f.c0 = f.var = f.c1 = f.c2 = 0.f;
+        f.dmin = f.dmax = 0.f;
+      } else {
+        f = solve_with_fallback<P, MOM, GRAD, F64>(m, RD(L.min_pivot), RD(L.cond_fallback));
+      }
+      return f;
+    };
+    auto put_level = [&](int c, int level, const FitOut &f) {
+      if (DIAG && pix) {
+        float *o = L.levels + (((size_t)c * NL + level) * plane_px + opix) * 2;
+        o[0] = f.valid ? f.c0 : __int_as_float(0x7fffffff);
+        o[1] = f.valid ? f.var : __int_as_float(0x7fffffff);
+      }
+    };
+    // order fallback at the largest scale (m holds its moments when any lane needs it), then the store
+    auto finish = [&](int c, Ici &ici, const MOM &m) {
+      const bool need = ici.choice == 255 && pix;
+      if (DIAG || __any_sync(LPA_FULL, need)) {
+        auto take = [&](const FitOut &f, int i) {
+          put_level(c, J + i, f);
+          if (ici.choice == 255 && f.valid) {
+            ici.choice = J + i;
+            ici.val = f.c0;
           }
-          const float R = RD(L.trunc_k) * RD(L.sigma[j0 + nj - 1]) * gsc;
-          const float taper = RD(L.taper);
-          const bool act = DIAG ? pix : !ici.done;
-#pragma unroll 1
-          for (int s = 0; s < S; s++)
-            walk_sensor<MODE, 1>(L.s[s], pos[s * NT], c, R, fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q,
-                                 [&](float2 D, float2 fv) { window_cell_ms<ORDER, NSP, MODE>(m, D, fv, R2s, cxs, taper, Q); });
-          // the fits in ascending scale order, always from slot 0: the later slots move down one
-          // place after each fit, so that slot 0 ends with the pass's largest scale
-          // the fits in ascending scale order
-#pragma unroll
-          for (int q = 0; q < NSP; q++) {
-            if (q >= lead) {
-              if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
-              const FitOut f = fit_of(m[q]);
-              put_level(c, j0 + q - lead, f);
-              ici.step(f, j0 + q - lead, RD(L.ici_gamma));
+        };
+        if constexpr (ORDER >= 1) take(fallback_fit<ORDER, 0, F64>(m, RD(L.min_pivot), RD(L.cond_fallback)), 0);
+        if constexpr (ORDER >= 2) take(fallback_fit<ORDER, 1, F64>(m, RD(L.min_pivot), RD(L.cond_fallback)), 1);
+      }
+      if (pix) {
+        if (RD(L.out_half))
+          reinterpret_cast<__half *>(RD(L.out))[c * plane_px + opix] = __float2half_rn(ici.val);
+        else
+          reinterpret_cast<float *>(RD(L.out))[c * plane_px + opix] = ici.val;
+        if (RD(L.choice)) RD(L.choice)[c * plane_px + opix] = (uint8_t)ici.choice;
+      }
+    };
+
+    // the persistent many-frame kernel walks once per scale (its register budget, shared by every
+    // frame it serves, has no room for the sums of several scales)
+    constexpr int NSP = GLOBAL_MAPS ? 1 : MultiScale<ORDER, COMP, MODE>::value;
+    if constexpr (NSP > 1) {
+      if (J >= 2) {
+        // all scales of a channel from one walk per sensor (up to NSP scales per pass): slot q of
+        // a pass holds scale j0 + q - lead, so that the pass's largest scale is always the last slot
+  #pragma unroll 1
+        for (int c = 0; c < 3; c++) {
+          Ici ici;
+          ici.reset(pix);
+          MOM m[NSP];
+          const float gsc = (c == 1) ? RD(L.green_ratio) : 1.f;
+          // the first pass takes what the later full passes leave (the small scales), so that the
+          // largest scales share the longest walk
+          const int npass = (J + NSP - 1) / NSP;
+  #pragma unroll 1
+          for (int pass = 0, j0 = 0, nj = J - NSP * (npass - 1); pass < npass; pass++, j0 += nj, nj = NSP) {
+            if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
+            const int lead = NSP - nj;
+            float R2s[NSP], cxs[NSP];
+  #pragma unroll
+            for (int q = 0; q < NSP; q++) {
+              const float sg = RD(L.sigma[q >= lead ? j0 + q - lead : j0]) * gsc;
+              const float Rq = RD(L.trunc_k) * sg;
+              R2s[q] = q >= lead ? Rq * Rq : -1.f;
+              cxs[q] = -log2e / (2.f * sg * sg);
+              m[q].zero();
+            }
+            const float R = RD(L.trunc_k) * RD(L.sigma[j0 + nj - 1]) * gsc;
+            const float taper = RD(L.taper);
+            const bool act = DIAG ? pix : !ici.done;
+  #pragma unroll 1
+            for (int s = 0; s < S; s++)
+              walk_sensor<MODE, 1>(L.s[s], pos[s * NT], c, R, fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q,
+                                   [&](float2 D, float2 fv) { window_cell_ms<ORDER, NSP, MODE>(m, D, fv, R2s, cxs, taper, Q); });
+            // the fits in ascending scale order, always from slot 0: the later slots move down one
+            // place after each fit, so that slot 0 ends with the pass's largest scale
+            // the fits in ascending scale order
+  #pragma unroll
+            for (int q = 0; q < NSP; q++) {
+              if (q >= lead) {
+                if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
+                const FitOut f = fit_of(m[q]);
+                put_level(c, j0 + q - lead, f);
+                ici.step(f, j0 + q - lead, RD(L.ici_gamma));
+              }
             }
           }
+          finish(c, ici, m[NSP - 1]);
         }
-        finish(c, ici, m[NSP - 1]);
+        continue;  // next pixel slot
       }
-      return true;
     }
-  }
 
-#pragma unroll 1
-  for (int c = GRAD ? 1 : 0; c < (GRAD ? 2 : 3); c++) {  // the gradient pass fits the green channel only
-    Ici ici;
-    ici.reset(pix);
-    MOM m;
-    const float gsc = (c == 1) ? RD(L.green_ratio) : 1.f;
-#pragma unroll 1
-    for (int j = 0; j < J; j++) {
-      if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
-      m.zero();
-      const float sg = RD(L.sigma[j]) * gsc;
-      const float R = RD(L.trunc_k) * sg, R2 = R * R;
-      const float cexp = -log2e / (2.f * sg * sg);
-      const bool act = DIAG ? pix : !ici.done;
-#pragma unroll 1
-      for (int s = 0; s < S; s++) {
-        if constexpr (TAB)
-          accumulate_table<ORDER>(m, L, s, c, j, u, v, fp_x0[s], fp_y0[s], smem, act, L.status);
-        else
-          accumulate_sensor<ORDER, COMP, MODE>(m, L.s[s], pos[s * NT], c, R, R2, cexp, RD(L.taper),
-                                                fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q);
-      }
-      const FitOut f = fit_of(m);
-      if constexpr (GRAD) {  // Section 5.4: the order-1 fit's linear coefficients; 0 if not usable
-        if (pix) {
-          L.aux[opix * 2] = f.valid ? f.c1 : 0.f;
-          L.aux[opix * 2 + 1] = f.valid ? f.c2 : 0.f;
+  #pragma unroll 1
+    for (int c = GRAD ? 1 : 0; c < (GRAD ? 2 : 3); c++) {  // the gradient pass fits the green channel only
+      Ici ici;
+      ici.reset(pix);
+      MOM m;
+      const float gsc = (c == 1) ? RD(L.green_ratio) : 1.f;
+  #pragma unroll 1
+      for (int j = 0; j < J; j++) {
+        if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
+        m.zero();
+        const float sg = RD(L.sigma[j]) * gsc;
+        const float R = RD(L.trunc_k) * sg, R2 = R * R;
+        const float cexp = -log2e / (2.f * sg * sg);
+        const bool act = DIAG ? pix : !ici.done;
+  #pragma unroll 1
+        for (int s = 0; s < S; s++) {
+          if constexpr (TAB)
+            accumulate_table<ORDER>(m, L, s, c, j, u, v, fp_x0[s], fp_y0[s], smem, act, L.status);
+          else
+            accumulate_sensor<ORDER, COMP, MODE>(m, L.s[s], pos[s * NT], c, R, R2, cexp, RD(L.taper),
+                                                  fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q);
         }
-        break;
+        const FitOut f = fit_of(m);
+        if constexpr (GRAD) {  // Section 5.4: the order-1 fit's linear coefficients; 0 if not usable
+          if (pix) {
+            L.aux[opix * 2] = f.valid ? f.c1 : 0.f;
+            L.aux[opix * 2 + 1] = f.valid ? f.c2 : 0.f;
+          }
+          break;
+        }
+        put_level(c, j, f);
+        ici.step(f, j, RD(L.ici_gamma));
       }
-      put_level(c, j, f);
-      ici.step(f, j, RD(L.ici_gamma));
+      if constexpr (!GRAD) finish(c, ici, m);
     }
-    if constexpr (!GRAD) finish(c, ici, m);
   }
   return true;
 #undef RD
@@ -978,14 +986,17 @@ struct FrameOccupancy {
       (ORDER == 2 && MultiScale<ORDER, COMP, MODE>::value > 1) ? LPA_M2_CTAS_256 * 16 / TH : 16 / TH * 2;
 };
 
-template <int ORDER, bool COMP, bool DIAG, int TH, int MODE = LPA_SEARCHED>
+// PX pixels per thread: a CTA of 16 x TH threads reconstructs a 16 x (TH PX) tile, each thread its
+// pixels one after the other (the staged footprint and its conversion serve PX times the pixels).
+template <int ORDER, bool COMP, bool DIAG, int TH, int MODE = LPA_SEARCHED, int PX = 1>
 __global__ void __launch_bounds__(LPA_TILE *TH, (FrameOccupancy<ORDER, COMP, TH, MODE>::value)) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
-  __shared__ Anchor anchors[4][LPA_MAX_SENSORS];
+  __shared__ Anchor anchors[2 * TH * PX / LPA_ANCHOR][LPA_MAX_SENSORS];
   __shared__ __align__(8) uint64_t mbar;
   if (threadIdx.x == 0) mbar_init(&mbar, 1);
-  process_tile<ORDER, COMP, DIAG, TH, false, MODE>(L, &L, L.tile0 + blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0, anchors);
+  process_tile<ORDER, COMP, DIAG, TH, false, MODE, PX>(L, &L, L.tile0 + blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0,
+                                                       anchors);
 }
 
 // Resident CTAs per SM the persistent kernel is compiled for (register cap 64K / (threads x this)):

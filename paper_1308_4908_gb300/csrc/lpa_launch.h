@@ -58,7 +58,8 @@ struct LpaLaunch {
   uint32_t smem_bytes;
   uint32_t off_pos;              // byte offset of each thread's pixel position in each sensor
                                  // (int4 {ix, iy, fx bits, fy bits}, [n_sensors][threads])
-  int tile_h;                    // tile height the plan was made for
+  int tile_h;                    // tile height (rows) the plan was made for
+  int px;                        // output pixels per thread (0 or 1: one; 2: two, 16-row tiles)
   int tile0;                     // single-frame grid: CTA b reconstructs tile tile0 + b
   int tile_count;                // single-frame grid size; 0 = every tile from tile0 on
   // Tabulated window weights (NULL = the window is searched and evaluated per pixel). Entry

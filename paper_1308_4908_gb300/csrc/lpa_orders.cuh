@@ -2,45 +2,55 @@
 // lpa_m0.cu, lpa_m1.cu and lpa_m2.cu, which compile in parallel).
 //
 // Instantiated per order: the searched window (Eq. 8) with and without the level maps, the
-// tabulated window (Section 8), tile heights 8 and 16; the steered window (Section 5.4) and the
-// printed noise weight K / s at tile height 16; the gradient pass (Section 5.4) for order 1 only.
+// tabulated window (Section 8), tile heights 8 and 16, and 16-row tiles with two pixels per
+// thread; the steered window (Section 5.4) and the printed noise weight K / s at tile height 16;
+// the gradient pass (Section 5.4) for order 1 only.
 #pragma once
 #include "lpa_dispatch.h"
 #include "lpa_kernel.cuh"
 
 namespace lpa_orders {
 
-template <int ORDER, int MODE, int TH>
+template <int ORDER, int MODE, int TH, int PX>
 constexpr bool instantiated() {
+  if (PX == 2)  // two pixels per thread: 16-row tiles of 8-row CTAs, the windows batches use
+    return TH == 8 && (MODE == LPA_SEARCHED || MODE == LPA_SEARCHED_F32 || MODE == LPA_TABULATED);
   if (MODE == LPA_GRADIENTS) return ORDER == 1 && TH == 16;
   if (lpa_mode_steered(MODE) || MODE == LPA_LITERAL) return TH == 16;
   return true;
 }
 
-template <int ORDER, bool COMP, bool DIAG, int TH, int MODE>
+template <int ORDER, bool COMP, bool DIAG, int TH, int MODE, int PX>
 const void *kernel_fn() {
-  if constexpr (!instantiated<ORDER, MODE, TH>() || (DIAG && MODE != LPA_SEARCHED && MODE != LPA_SEARCHED_F32))
+  if constexpr (!instantiated<ORDER, MODE, TH, PX>() ||
+                (DIAG && (PX != 1 || (MODE != LPA_SEARCHED && MODE != LPA_SEARCHED_F32))))
     return nullptr;
-  else return (const void *)lpa::lpa_reconstruct<ORDER, COMP, DIAG, TH, MODE>;
+  else return (const void *)lpa::lpa_reconstruct<ORDER, COMP, DIAG, TH, MODE, PX>;
 }
 
-template <int ORDER, bool COMP, bool DIAG, int TH>
+template <int ORDER, bool COMP, bool DIAG, int TH, int PX = 1>
 const void *kernel_mode(int mode) {
   switch (mode) {
-    case LPA_SEARCHED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED>();
-    case LPA_TABULATED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_TABULATED>();
-    case LPA_STEERED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED>();
-    case LPA_GRADIENTS: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_GRADIENTS>();
-    case LPA_LITERAL: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_LITERAL>();
-    case LPA_SEARCHED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED_F32>();
-    case LPA_STEERED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED_F32>();
+    case LPA_SEARCHED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED, PX>();
+    case LPA_TABULATED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_TABULATED, PX>();
+    case LPA_STEERED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED, PX>();
+    case LPA_GRADIENTS: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_GRADIENTS, PX>();
+    case LPA_LITERAL: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_LITERAL, PX>();
+    case LPA_SEARCHED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED_F32, PX>();
+    case LPA_STEERED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED_F32, PX>();
     default: return nullptr;
   }
 }
 
-// The single-frame kernel of this order for a configuration; nullptr if not instantiated.
+// The single-frame kernel of this order for a configuration (tile_h rows per tile, px pixels per
+// thread: CTAs of 16 x tile_h / px threads); nullptr if not instantiated.
 template <int ORDER>
-const void *kernel(bool comp, bool diag, int mode, int tile_h) {
+const void *kernel(bool comp, bool diag, int mode, int tile_h, int px) {
+  if (px == 2) {
+    if (tile_h != 16 || diag) return nullptr;
+    return comp ? kernel_mode<ORDER, true, false, 8, 2>(mode) : kernel_mode<ORDER, false, false, 8, 2>(mode);
+  }
+  if (px != 1) return nullptr;
   if (tile_h == 8) {
     if (comp) return diag ? kernel_mode<ORDER, true, true, 8>(mode) : kernel_mode<ORDER, true, false, 8>(mode);
     return diag ? kernel_mode<ORDER, false, true, 8>(mode) : kernel_mode<ORDER, false, false, 8>(mode);
@@ -53,13 +63,14 @@ const void *kernel(bool comp, bool diag, int mode, int tile_h) {
 template <int ORDER>
 cudaError_t launch(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st) {
   // the diagnostic (level maps) kernel is instantiated for the searched window only
-  const void *fn = kernel<ORDER>(comp, diag, L.mode, L.tile_h);
+  const int px = L.px > 1 ? L.px : 1;
+  const void *fn = kernel<ORDER>(comp, diag, L.mode, L.tile_h, px);
   if (!fn) return cudaErrorInvalidConfiguration;
   cudaError_t e = lpa_opt_in(fn);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_count > 0 ? L.tile_count : L.tiles_x * L.tiles_y - L.tile0;
   void *args[] = {const_cast<LpaLaunch *>(&L)};
-  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)(LPA_TILE * L.tile_h)), args, L.smem_bytes, st);
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)(LPA_TILE * L.tile_h / px)), args, L.smem_bytes, st);
 }
 
 template <int ORDER, bool COMP, int TH>
@@ -100,8 +111,8 @@ int batch_ctas_per_sm(bool comp, int tile_h, uint32_t smem_bytes) {
   cudaError_t lpa_launch_order##N(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st) {             \
     return lpa_orders::launch<N>(L, comp, diag, st);                                                       \
   }                                                                                                        \
-  const void *lpa_kernel_order##N(bool comp, bool diag, int mode, int tile_h) {                            \
-    return lpa_orders::kernel<N>(comp, diag, mode, tile_h);                                                \
+  const void *lpa_kernel_order##N(bool comp, bool diag, int mode, int tile_h, int px) {                    \
+    return lpa_orders::kernel<N>(comp, diag, mode, tile_h, px);                                            \
   }                                                                                                        \
   cudaError_t lpa_launch_batch_order##N(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st) { \
     return lpa_orders::launch_batch<N>(B, comp, tile_h, grid, st);                                         \

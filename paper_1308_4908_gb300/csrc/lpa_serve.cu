@@ -83,6 +83,8 @@ struct Job {
   size_t out_bytes = 0;
   uint8_t *choice_dev = nullptr;
   size_t choice_bytes = 0;
+  float *scratch_dev = nullptr;     // adaptive requests: gradients and steering matrices
+  size_t scratch_bytes = 0;
   int tiles = 0, next_tile = 0, steps = 0;
   int inflight = 0;                 // launched steps holding tiles of this frame, not yet complete
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -203,6 +205,8 @@ struct hdr_server {
       j.out_dev = p + o;
       o += align256(j.out_bytes);
       j.choice_dev = j.req.choice_host ? reinterpret_cast<uint8_t *>(p + o) : nullptr;
+      o += align256(j.choice_bytes);
+      j.scratch_dev = j.scratch_bytes ? reinterpret_cast<float *>(p + o) : nullptr;
       j.t_admit = Clock::now();
       if (!have_first) {
         have_first = true;
@@ -255,6 +259,7 @@ struct hdr_server {
     if (steps.size() >= kMaxInflight) return false;
     std::vector<hdr_frame> frames;
     std::vector<int2> ranges;
+    std::vector<float *> scratch;
     Step st;
     long budget = cfg.step_tiles > 0 ? cfg.step_tiles : (1L << 40);
     for (uint64_t t : active) {
@@ -267,7 +272,9 @@ struct hdr_server {
       for (int s = 0; s < j.n_sensors; s++) f.raw_dev[s] = j.raw_dev[s];
       f.out_dev = j.out_dev;
       f.choice_dev = j.choice_dev;
+      f.calpa = j.req.adaptive ? &j.req.calpa : nullptr;
       frames.push_back(f);
+      scratch.push_back(j.scratch_dev);
       ranges.push_back(make_int2(j.next_tile, j.next_tile + take));
       budget -= take;
       st.members.push_back(t);
@@ -278,7 +285,8 @@ struct hdr_server {
     st.ev = timing_event();
     lock.unlock();
     if (st.ev_begin) cudaEventRecord(st.ev_begin, compute);
-    hdr_status s = lpa_batch_run(ctx, (int)frames.size(), frames.data(), ranges.data(), &cfg.batch, compute);
+    hdr_status s = lpa_batch_run(ctx, (int)frames.size(), frames.data(), ranges.data(), &cfg.batch, compute,
+                                 scratch.data());
     lock.lock();
     if (s == HDR_OK && !st.ev) s = lpa_fail(HDR_E_CUDA, "cudaEventCreate failed");
     if (s == HDR_OK) {
@@ -394,6 +402,8 @@ hdr_status hdr_server_create(hdr_ctx *ctx, const hdr_server_config *cfg, hdr_ser
   if (cfg->batch.ctas_per_sm < 0 || cfg->batch.ctas_per_sm > 8)
     return lpa_fail(HDR_E_INVALID, "batch.ctas_per_sm must be in [0, 8]");
   if (cfg->batch.form != 0 && cfg->batch.form != 1) return lpa_fail(HDR_E_INVALID, "batch.form must be 0 or 1");
+  if (cfg->batch.px_per_thread < 0 || cfg->batch.px_per_thread > 2)
+    return lpa_fail(HDR_E_INVALID, "batch.px_per_thread must be 0, 1 or 2");
   hdr_server *s = new (std::nothrow) hdr_server();
   if (!s) return lpa_fail(HDR_E_NOMEM, "host allocation failed");
   s->ctx = ctx;
@@ -428,6 +438,13 @@ hdr_status hdr_submit(hdr_server *srv, const hdr_request *req, uint64_t *ticket)
   if (st) return st;
   if (req->params.weight_mode != 0)
     return lpa_fail(HDR_E_UNSUPPORTED, "the serving loop uses the inverse-variance weight (weight_mode 0)");
+  if (req->adaptive != 0 && req->adaptive != 1) return lpa_fail(HDR_E_INVALID, "adaptive must be 0 or 1");
+  if (req->adaptive) {
+    st = lpa_check_calpa(&req->calpa);
+    if (st) return st;
+    if (srv->cfg.batch.tile_h != 16)
+      return lpa_fail(HDR_E_UNSUPPORTED, "adaptive requests need a server with 16-row tiles");
+  }
   if (!req->out_host && (long long)req->params.out_w * req->params.out_h > 0)
     return lpa_fail(HDR_E_INVALID, "out_host is NULL");
   for (int s = 0; s < ns; s++)
@@ -445,7 +462,8 @@ hdr_status hdr_submit(hdr_server *srv, const hdr_request *req, uint64_t *ticket)
   const size_t px = (size_t)req->params.out_w * req->params.out_h * 3;
   j.out_bytes = px * (req->params.out_dtype ? 2 : 4);
   j.choice_bytes = req->choice_host ? px : 0;
-  bytes += align256(j.out_bytes) + align256(j.choice_bytes);
+  j.scratch_bytes = req->adaptive ? px / 3 * 5 * sizeof(float) : 0;  // 5 floats per output pixel
+  bytes += align256(j.out_bytes) + align256(j.choice_bytes) + align256(j.scratch_bytes);
   j.bytes = std::max<size_t>(bytes, 256);
   if (j.bytes > srv->cfg.pool_bytes) return lpa_fail(HDR_E_UNSUPPORTED, "the frame needs more memory than the pool holds");
   const int th = srv->cfg.batch.tile_h;

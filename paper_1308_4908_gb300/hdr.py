@@ -51,12 +51,12 @@ class hdr_calpa_params(ctypes.Structure):
 class hdr_frame(ctypes.Structure):
     _fields_ = [("rig_id", ctypes.c_int32), ("params", ctypes.c_void_p),
                 ("raw_dev", ctypes.c_void_p * HDR_MAX_SENSORS), ("out_dev", ctypes.c_void_p),
-                ("choice_dev", ctypes.c_void_p)]
+                ("choice_dev", ctypes.c_void_p), ("calpa", ctypes.c_void_p)]
 
 
 class hdr_batch_config(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("cost_order", ctypes.c_int32),
-                ("form", ctypes.c_int32)]
+                ("form", ctypes.c_int32), ("px_per_thread", ctypes.c_int32)]
 
 
 class hdr_server_config(ctypes.Structure):
@@ -67,7 +67,8 @@ class hdr_server_config(ctypes.Structure):
 class hdr_request(ctypes.Structure):
     _fields_ = [("rig_id", ctypes.c_int32), ("params", hdr_params),
                 ("raw_host", ctypes.c_void_p * HDR_MAX_SENSORS), ("out_host", ctypes.c_void_p),
-                ("choice_host", ctypes.c_void_p), ("stream_id", ctypes.c_int32)]
+                ("choice_host", ctypes.c_void_p), ("stream_id", ctypes.c_int32), ("adaptive", ctypes.c_int32),
+                ("calpa", hdr_calpa_params)]
 
 
 class hdr_result(ctypes.Structure):
@@ -452,11 +453,15 @@ class Context:
                             choice.data_ptr() if choice is not None else None, self._stream(stream))
         return out
 
-    def frame(self, rig_id: int, params, raws, out, choice=None, keep: Optional[list] = None) -> hdr_frame:
-        """hdr_frame for a batch; `keep` collects the ctypes objects the frame points at."""
+    def frame(self, rig_id: int, params, raws, out, choice=None, keep: Optional[list] = None,
+              calpa: Optional[hdr_calpa_params] = None) -> hdr_frame:
+        """hdr_frame for a batch; `keep` collects the ctypes objects the frame points at (it must be
+        given when `calpa` selects the adaptive reconstruction)."""
         hp = params if isinstance(params, hdr_params) else params_struct(params)
         if keep is not None:
             keep.append(hp)
+            if calpa is not None:
+                keep.append(calpa)
         f = hdr_frame()
         f.rig_id = int(rig_id)
         f.params = ctypes.addressof(hp)
@@ -464,6 +469,7 @@ class Context:
             f.raw_dev[i] = int(r.data_ptr())
         f.out_dev = out.data_ptr()
         f.choice_dev = choice.data_ptr() if choice is not None else None
+        f.calpa = ctypes.addressof(calpa) if calpa is not None else None
         return f
 
     def reconstruct_batch(self, frames: Sequence[hdr_frame], cfg: Optional[hdr_batch_config] = None, stream=None):
@@ -582,8 +588,13 @@ class Server:
         self._held = {}
 
     def submit(self, rig_id: int, params, raws_host: Sequence[np.ndarray], out_host: np.ndarray,
-               choice_host: Optional[np.ndarray] = None, stream_id: int = 0) -> int:
+               choice_host: Optional[np.ndarray] = None, stream_id: int = 0,
+               calpa: Optional[hdr_calpa_params] = None) -> int:
+        """Queue one frame; with `calpa` the adaptive reconstruction of Sections 5.4-5.5."""
         req = hdr_request()
+        if calpa is not None:
+            req.adaptive = 1
+            req.calpa = calpa
         req.rig_id = int(rig_id)
         req.params = params if isinstance(params, hdr_params) else params_struct(params)
         for i, r in enumerate(raws_host):

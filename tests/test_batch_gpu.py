@@ -94,6 +94,7 @@ def test_batch_equals_single_frames_for_every_configuration(ctx):
     refs = _single(ctx, items)
     cfgs = [hdr.hdr_batch_config(th, per_sm, order, 1) for th in (16, 8) for per_sm in (0, 1) for order in (1, 0)]
     cfgs += [hdr.hdr_batch_config(th, 0, order, 0) for th in (16, 8) for order in (1, 0)]
+    cfgs += [hdr.hdr_batch_config(16, 0, order, 0, 2) for order in (1, 0)]   # two pixels per thread
     for cfg in cfgs:
         for _, _, _, out, _ in items:
             out.fill_(-7.0)
@@ -124,6 +125,7 @@ def test_tuner_picks_a_configuration_and_batch_uses_it(ctx):
     hf = [ctx.frame(rig, fr.params, raws, out, ch, keep) for rig, fr, raws, out, ch in items]
     best = ctx.tune_batch(hf)
     assert best.tile_h in (8, 16) and 0 <= best.ctas_per_sm <= 8 and best.cost_order in (0, 1) and best.form in (0, 1)
+    assert best.px_per_thread in (1, 2)
     _check(items, _batch(ctx, items), refs, best.form)        # cfg None -> the tuned configuration
 
 
@@ -155,6 +157,10 @@ def test_batch_rejects_bad_input(ctx):
         ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(12, 0, 1, 0))
     with pytest.raises(hdr.HdrError):
         ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(16, 0, 1, 2))
+    with pytest.raises(hdr.HdrError):
+        ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(8, 0, 1, 0, 2))    # two pixels per thread: 16 rows
+    with pytest.raises(hdr.HdrError):
+        ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(16, 0, 1, 1, 2))   # and form 0 only
 
 
 @pytest.mark.parametrize("form", [0, 1])
