@@ -727,10 +727,11 @@ def run_tab_study(args):
     rows = []
     for order in (0, 1, 2):
         row = {"order": order}
-        o = oracle.reconstruct(fr.sensors, dataclasses.replace(fr.params, order=order), pix)
+        o = oracle.reconstruct(fr.sensors, dataclasses.replace(fr.params, order=order), pix, levels=True, kappa=True)
         for tab in (1, 0):
             p = dataclasses.replace(fr.params, order=order, tab_weights=tab)
-            out = ctx.reconstruct(0, p, raws)
+            ch = torch.empty((3, p.out_h, p.out_w), dtype=torch.uint8, device="cuda")
+            out = ctx.reconstruct(0, p, raws, choice=ch)
             st = torch.cuda.current_stream()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
             for k in range(10):
@@ -742,18 +743,20 @@ def run_tab_study(args):
             ctx.check()
             ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
             g = out.cpu().numpy()[:, pix[:, 1], pix[:, 0]].T
-            ok = np.isfinite(o["out"]) & np.isfinite(g)
-            rel = np.abs(g - o["out"])[ok] / np.maximum(np.abs(o["out"][ok]), 1e-2)
+            gc = ch.cpu().numpy()[:, pix[:, 1], pix[:, 0]].T
+            e = error_stats([(g, gc, o)])
             key = "tabulated" if tab else "searched"
             row[key] = {"ms": round(ms, 3), "mpx_s": round(p.out_w * p.out_h / ms / 1e3, 1),
-                        "max_rel_err": float(rel.max()), "median_rel_err": float(np.median(rel))}
+                        "max_rel_err": e["max"], "median_rel_err": e["median"],
+                        "level_mismatch_frac": e["level_mismatch_frac"]}
         row["speedup"] = round(row["searched"]["ms"] / row["tabulated"]["ms"], 3)
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
     ctx.close()
     print(json.dumps({"study": "tabulated weights", "workload": f"3 x {args.size}^2 RGGB, pure translations "
                       "U(-1.5, 1.5) px, 1x output, 4 scales with the interval rule",
-                      "error": "|gpu - oracle| / max(|oracle|, 1e-2) on 2000 random pixels x 3 channels",
+                      "error": "|gpu - oracle| / max(|oracle|, 1e-2) on 2000 random pixels x 3 channels; "
+                               "where the GPU took another admissible level, against the oracle at that level",
                       "rows": rows}), flush=True)
 
 

@@ -280,6 +280,9 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
   L.tab_hdr = nullptr;
   L.tab_cells = nullptr;
   if (!env.tabs || !env.tabulate || p->tab_weights != 1 || !is_identity_linear(p->out_affine)) return HDR_OK;
+  // order 2: the searched window feeds two scales from one walk, the table walks once per scale;
+  // on the translational paper rig the searched kernel is the faster one (4.04 against 4.14 ms)
+  if (p->order == 2) return HDR_OK;
   for (int s = 0; s < rig.n; s++)
     if (!is_identity_linear(rig.s[s].d.affine)) return HDR_OK;
   const int J = p->n_scales;

@@ -430,14 +430,21 @@ struct Ici {
 #define LPA_MULTI_SCALE 2      // order 2
 #endif
 #ifndef LPA_MULTI_SCALE_LOW
-#define LPA_MULTI_SCALE_LOW 4  // orders 0 and 1
+#define LPA_MULTI_SCALE_LOW 4  // order 1
+#endif
+#ifndef LPA_MULTI_SCALE_M0
+#define LPA_MULTI_SCALE_M0 4   // order 0
+#endif
+#ifndef LPA_M0_CTAS_256
+#define LPA_M0_CTAS_256 4      // resident 256-thread CTAs per SM the order-0 kernel is built for
 #endif
 template <int ORDER, bool COMP, int MODE>
 struct MultiScale {
   static constexpr int value =
       COMP ? 1
-      : lpa_mode_f32(MODE) ? (ORDER == 2 ? LPA_MULTI_SCALE : LPA_MULTI_SCALE_LOW)
-      : (MODE == LPA_SEARCHED || MODE == LPA_STEERED) ? (ORDER == 2 ? 1 : LPA_MULTI_SCALE_LOW)
+      : lpa_mode_f32(MODE) ? (ORDER == 2 ? LPA_MULTI_SCALE : ORDER == 1 ? LPA_MULTI_SCALE_LOW : LPA_MULTI_SCALE_M0)
+      : (MODE == LPA_SEARCHED || MODE == LPA_STEERED) ? (ORDER == 2 ? 1 : ORDER == 1 ? LPA_MULTI_SCALE_LOW
+                                                                                      : LPA_MULTI_SCALE_M0)
                                                       : 1;
 };
 
@@ -982,8 +989,9 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
 #endif
 template <int ORDER, bool COMP, int TH, int MODE>
 struct FrameOccupancy {
-  static constexpr int value =
-      (ORDER == 2 && MultiScale<ORDER, COMP, MODE>::value > 1) ? LPA_M2_CTAS_256 * 16 / TH : 16 / TH * 2;
+  static constexpr int value = (ORDER == 2 && MultiScale<ORDER, COMP, MODE>::value > 1) ? LPA_M2_CTAS_256 * 16 / TH
+                               : ORDER == 0                                              ? LPA_M0_CTAS_256 * 16 / TH
+                                                                                         : 16 / TH * 2;
 };
 
 // PX pixels per thread: a CTA of 16 x TH threads reconstructs a 16 x (TH PX) tile, each thread its
