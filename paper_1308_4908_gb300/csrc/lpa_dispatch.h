@@ -51,7 +51,7 @@ cudaError_t lpa_launch_order1(const LpaLaunch &L, bool comp, bool diag, cudaStre
 cudaError_t lpa_launch_order2(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st);
 
 // The single-frame kernel of order M for that configuration (for graph kernel nodes): mode is one
-// of LPA_SEARCHED .. LPA_STEERED_F32, tile_h the rows of a tile, px the pixels per thread (the CTA
+// of LPA_SEARCHED .. LPA_TABULATED_F32, tile_h the rows of a tile, px the pixels per thread (the CTA
 // has 16 x tile_h / px threads); nullptr where that combination is not instantiated.
 const void *lpa_kernel_order0(bool comp, bool diag, int mode, int tile_h, int px);
 const void *lpa_kernel_order1(bool comp, bool diag, int mode, int tile_h, int px);

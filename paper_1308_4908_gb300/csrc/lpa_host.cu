@@ -276,17 +276,21 @@ int floor_div2_parity(long long v) { return (int)(((v % 2) + 2) % 2); }
 // (bxe + ox + 2 qx, bye + oy + 2 qy), bxe = even part of u + floor(G2) - ox, at offsets
 // d = (2 qx - rx, 2 qy - ry) with rx = parity(u + floor(G2) - ox) + frac(G2): the same for every
 // pixel of one parity class. The window cells (|d| < k sigma), offsets and weights are listed once.
-hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p, LpaLaunch &L) {
+hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p, bool f64_possible, LpaLaunch &L) {
   L.tab_hdr = nullptr;
   L.tab_cells = nullptr;
+  L.tab_nsp = 0;
   if (!env.tabs || !env.tabulate || p->tab_weights != 1 || !is_identity_linear(p->out_affine)) return HDR_OK;
-  // order 2: the searched window feeds two scales from one walk, the table walks once per scale;
-  // on the translational paper rig the searched kernel is the faster one (4.04 against 4.14 ms)
-  if (p->order == 2) return HDR_OK;
+  // order 2 with the FP64 re-solve compiled in walks once per scale (the sums of two scales do not
+  // fit beside it), the searched window with it compiled out feeds two scales from one walk; the
+  // latter is the faster (4.04 against 4.14 ms on the translational paper rig)
+  if (p->order == 2 && f64_possible) return HDR_OK;
   for (int s = 0; s < rig.n; s++)
     if (!is_identity_linear(rig.s[s].d.affine)) return HDR_OK;
   const int J = p->n_scales;
-  std::vector<double> inputs = {(double)rig.n, (double)J, p->trunc_k, p->green_ratio};
+  const int nsp = lpa_scales_per_walk(p->order, p->accum != 0, f64_possible ? LPA_TABULATED : LPA_TABULATED_F32);
+  const int npass = lpa_n_passes(J, nsp);
+  std::vector<double> inputs = {(double)rig.n, (double)J, p->trunc_k, p->green_ratio, (double)nsp};
   for (int j = 0; j < J; j++) inputs.push_back(p->sigma[j]);
   for (int s = 0; s < rig.n; s++) {
     inputs.push_back(L.s[s].G[2]);
@@ -294,11 +298,12 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
     L.s[s].ix_shift = (int)std::floor(L.s[s].G[2]);
     L.s[s].iy_shift = (int)std::floor(L.s[s].G[5]);
   }
-  const size_t n_hdr = (size_t)rig.n * 16 * J;
+  const size_t n_hdr = (size_t)rig.n * 16 * npass * 2;
   auto known = env.tabs->by_inputs.find(inputs);
   if (known != env.tabs->by_inputs.end()) {
     L.tab_hdr = static_cast<const int4 *>(known->second);
     L.tab_cells = reinterpret_cast<const float4 *>(static_cast<const int4 *>(known->second) + n_hdr);
+    L.tab_nsp = nsp;
     L.mode = LPA_TABULATED;
     return HDR_OK;
   }
@@ -316,37 +321,69 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
           const double gscale = (ox != oy) ? p->green_ratio : 1.0;  // phases (1,0), (0,1): G
           const double rx = floor_div2_parity((long long)pu + (long long)flx - ox) + (gx - flx);
           const double ry = floor_div2_parity((long long)pv + (long long)fly - oy) + (gy - fly);
-          for (int j = 0; j < J; j++) {
-            const double sg = p->sigma[j] * gscale, R = p->trunc_k * sg, R2 = R * R;
-            int4 &h = hdr[((((size_t)s * 2 + pu) * 2 + pv) * 4 + ph) * J + j];
-            h.x = (int)cells.size();
-            int qxmin = 1 << 14, qxmax = -(1 << 14), qymin = 1 << 14, qymax = -(1 << 14);
+          for (int pass = 0, j0 = 0, nj = lpa_first_pass_scales(J, nsp); pass < npass; pass++, j0 += nj, nj = nsp) {
+            // the cells inside the window of the pass's largest scale, nearest first (ties by lattice
+            // position, so that the table is a function of its inputs); slot q holds scale
+            // j0 + q - lead, and its cells are the first n_q
+            const int lead = nsp - nj;
+            double sg[4], R2[4];
+            for (int q = 0; q < nsp; q++) {
+              sg[q] = p->sigma[q >= lead ? j0 + q - lead : j0] * gscale;
+              const double R = p->trunc_k * sg[q];
+              R2[q] = q >= lead ? R * R : -1.0;
+            }
+            const double R = p->trunc_k * sg[nsp - 1];
+            struct Cell {
+              double r2, dx, dy;
+              int qx, qy;
+            };
+            std::vector<Cell> in;
             const int x0 = (int)std::floor((rx - R) / 2) - 1, x1 = (int)std::ceil((rx + R) / 2) + 1;
             const int y0 = (int)std::floor((ry - R) / 2) - 1, y1 = (int)std::ceil((ry + R) / 2) + 1;
             for (int qy = y0; qy <= y1; qy++)
               for (int qx = x0; qx <= x1; qx++) {
                 const double dx = 2.0 * qx - rx, dy = 2.0 * qy - ry, r2 = dx * dx + dy * dy;
-                if (!(r2 < R2)) continue;
-                const double K = std::exp(-r2 / (2.0 * sg * sg)) - taper;  // Eq. 8, truncated and tapered
-                float4 c;
-                c.x = (float)dx;
-                c.y = (float)dy;
-                c.z = (float)K;
-                const int q = (qy << 16) | (qx & 0xffff);
-                memcpy(&c.w, &q, 4);
-                cells.push_back(c);
-                qxmin = std::min(qxmin, qx);
-                qxmax = std::max(qxmax, qx);
-                qymin = std::min(qymin, qy);
-                qymax = std::max(qymax, qy);
+                if (r2 < R2[nsp - 1]) in.push_back({r2, dx, dy, qx, qy});
               }
-            h.y = (int)cells.size() - h.x;
-            if (h.y == 0) qxmin = qxmax = qymin = qymax = 0;
-            h.z = pack(qxmin, qxmax);
-            h.w = pack(qymin, qymax);
+            std::sort(in.begin(), in.end(), [](const Cell &a, const Cell &b) {
+              return a.r2 != b.r2 ? a.r2 < b.r2 : a.qy != b.qy ? a.qy < b.qy : a.qx < b.qx;
+            });
+            int4 *h = &hdr[(((((size_t)s * 2 + pu) * 2 + pv) * 4 + ph) * npass + pass) * 2];
+            h[0].x = (int)(cells.size() / 2);
+            h[0].y = (int)in.size();
+            int nq[4] = {0, 0, 0, 0};
+            int qxmin = 1 << 14, qxmax = -(1 << 14), qymin = 1 << 14, qymax = -(1 << 14);
+            for (const Cell &e : in) {
+              float4 g, k;
+              g.x = (float)e.dx;
+              g.y = (float)e.dy;
+              const int q = (e.qy << 16) | (e.qx & 0xffff);
+              memcpy(&g.z, &q, 4);
+              g.w = 0.f;
+              float kv[4] = {0.f, 0.f, 0.f, 0.f};
+              for (int t = 0; t < nsp; t++)
+                if (e.r2 < R2[t]) {
+                  kv[t] = (float)(std::exp(-e.r2 / (2.0 * sg[t] * sg[t])) - taper);  // Eq. 8, truncated and tapered
+                  nq[t]++;
+                }
+              k = make_float4(kv[0], kv[1], kv[2], kv[3]);
+              cells.push_back(g);
+              cells.push_back(k);
+              qxmin = std::min(qxmin, e.qx);
+              qxmax = std::max(qxmax, e.qx);
+              qymin = std::min(qymin, e.qy);
+              qymax = std::max(qymax, e.qy);
+            }
+            if (in.empty()) qxmin = qxmax = qymin = qymax = 0;
+            h[0].z = pack(qxmin, qxmax);
+            h[0].w = pack(qymin, qymax);
+            h[1] = make_int4(nq[0], nq[1], nq[2], nq[3]);
           }
         }
   }
+  // one padding cell: the kernel loads the cell after each one it reads
+  cells.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+  cells.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
   // content hash (FNV-1a) -> device copy
   const size_t nb = hdr.size() * sizeof(int4) + cells.size() * sizeof(float4);
   uint64_t hsh = 1469598103934665603ull;
@@ -394,6 +431,7 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
   env.tabs->by_inputs.emplace(std::move(inputs), it->second);
   L.tab_hdr = static_cast<const int4 *>(it->second);
   L.tab_cells = reinterpret_cast<const float4 *>(static_cast<const int4 *>(it->second) + hdr.size());
+  L.tab_nsp = nsp;
   L.mode = LPA_TABULATED;
   return HDR_OK;
 }
@@ -503,17 +541,17 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
     }
   }
   L.tx_bytes = tx;
-  if (p->weight_mode == 1) {  // the printed noise weight K / s: searched window, its own kernel
-    L.mode = LPA_LITERAL;
-  } else {
-    hdr_status st = build_tables(env, rig, p, L);
-    if (st) return st;
-  }
   // a usable fit's equilibrated pivots lie in (min_pivot, 1]: when min_pivot * cond_fallback >= 2
   // their spread never exceeds cond_fallback and the FP64 re-solve cannot trigger
   const bool f64_possible = p->cond_fallback > 0.0 && (p->min_pivot - 1e-4) * p->cond_fallback < 2.0;
+  if (p->weight_mode == 1) {  // the printed noise weight K / s: searched window, its own kernel
+    L.mode = LPA_LITERAL;
+  } else {
+    hdr_status st = build_tables(env, rig, p, f64_possible, L);
+    if (st) return st;
+  }
   if (!f64_possible) L.mode = lpa_mode_to_f32(L.mode);
-  if (L.mode != LPA_TABULATED) {  // each thread's sample cell in each sensor (tables need none)
+  if (!lpa_mode_tab(L.mode)) {  // each thread's sample cell in each sensor (tables need none)
     off = (off + 15) / 16 * 16;
     L.off_pos = off;
     off += (uint32_t)(rig.n * 16 * LPA_TILE * tile_h);

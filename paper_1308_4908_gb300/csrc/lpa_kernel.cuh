@@ -423,29 +423,12 @@ struct Ici {
 
 // ---------------------------------------------------------------- kernel
 
-// Scales per walk of the window cells: the searched and steered windows with plain FP32 sums feed
-// up to four nested scales from one walk at orders 0 and 1, two at order 2 when the FP64 re-solve
-// is compiled out (their sums stay in registers); the other variants walk once per scale.
-#ifndef LPA_MULTI_SCALE
-#define LPA_MULTI_SCALE 2      // order 2
-#endif
-#ifndef LPA_MULTI_SCALE_LOW
-#define LPA_MULTI_SCALE_LOW 4  // order 1
-#endif
-#ifndef LPA_MULTI_SCALE_M0
-#define LPA_MULTI_SCALE_M0 4   // order 0
-#endif
 #ifndef LPA_M0_CTAS_256
 #define LPA_M0_CTAS_256 4      // resident 256-thread CTAs per SM the order-0 kernel is built for
 #endif
 template <int ORDER, bool COMP, int MODE>
 struct MultiScale {
-  static constexpr int value =
-      COMP ? 1
-      : lpa_mode_f32(MODE) ? (ORDER == 2 ? LPA_MULTI_SCALE : ORDER == 1 ? LPA_MULTI_SCALE_LOW : LPA_MULTI_SCALE_M0)
-      : (MODE == LPA_SEARCHED || MODE == LPA_STEERED) ? (ORDER == 2 ? 1 : ORDER == 1 ? LPA_MULTI_SCALE_LOW
-                                                                                      : LPA_MULTI_SCALE_M0)
-                                                      : 1;
+  static constexpr int value = lpa_scales_per_walk(ORDER, COMP, MODE);
 };
 
 // sensor-space positions are clamped to +-LPA_FAR px (far outside any sensor) before integer conversion
@@ -620,12 +603,23 @@ __device__ __forceinline__ void accumulate_sensor(typename MomentsSel<ORDER, COM
   });
 }
 
-// The window of one pixel read from the tabulated cells (Section 8; see LpaLaunch::tab_hdr): the
+// The windows of one pass read from the tabulated cells (Section 8; see LpaLaunch::tab_hdr): the
 // pixel's even lattice cell in each colour phase follows from integer arithmetic, and every cell
-// carries its offset and weight, so nothing is searched or evaluated per pixel.
-template <int ORDER, class MOM>
-__device__ __forceinline__ void accumulate_table(MOM &m, const LpaLaunch &L, int s, int c, int j, int u, int v, int x0,
-                                                 int y0, const unsigned char *smem, bool active, unsigned *status) {
+// carries its offset and its weight at each scale of the pass, so nothing is searched or evaluated
+// per pixel. The cells are sorted by distance and the windows are nested: cells n_{q-1} .. n_q - 1
+// lie in the windows of slots q .. NSP - 1 and are added to those sums only (no per-cell test).
+#ifndef LPA_TAB_PREFETCH
+#define LPA_TAB_PREFETCH 1
+#endif
+#ifndef LPA_TAB_UNROLL
+#define LPA_TAB_UNROLL 4
+#endif
+constexpr int kTabUnroll = LPA_TAB_UNROLL;
+template <int ORDER, int NSP, class MOM>
+__device__ __forceinline__ void accumulate_table(MOM (&m)[NSP], const LpaLaunch &L, int s, int c, int pass, int npass,
+                                                 int u, int v, int x0, int y0, const unsigned char *smem, bool active,
+                                                 unsigned *status) {
+  static_assert(NSP >= 1 && NSP <= 4, "a table cell holds four weights");
   const LpaSensorK &S = L.s[s];
   const int PW = S.box_w >> 1, PH = S.box_h >> 1;
   const float2 *planes = reinterpret_cast<const float2 *>(smem + S.off_planes);
@@ -638,26 +632,54 @@ __device__ __forceinline__ void accumulate_table(MOM &m, const LpaLaunch &L, int
     const int oy = (c == 0) ? 0 : (c == 2 ? 1 : sub);
     const int ph = ox + 2 * oy;
     const int cb = (((ix - ox) & ~1) - x0) >> 1, rb = (((iy - oy) & ~1) - y0) >> 1;
-    const int4 h = __ldg(&L.tab_hdr[(base + ph) * L.n_scales + j]);
+    const int4 *hp = L.tab_hdr + 2 * ((base + ph) * npass + pass);
+    const int4 h = __ldg(hp), nc = __ldg(hp + 1);
     const int qx0 = (int)(short)(h.z & 0xffff), qx1 = h.z >> 16, qy0 = (int)(short)(h.w & 0xffff), qy1 = h.w >> 16;
     if (!(cb + qx0 >= 0 && cb + qx1 < PW && rb + qy0 >= 0 && rb + qy1 < PH)) {
       if (active && h.y > 0) atomicOr(status, LPA_ERR_BOUNDS);
       continue;
     }
     const float2 *pl = planes + ph * (PW * PH) + rb * PW + cb;
-    const float4 *cell = L.tab_cells + h.x;
-#pragma unroll 2
-    for (int k = 0; k < h.y; k++) {
-      const float4 t = __ldg(cell + k);
-      const int q = __float_as_int(t.w);
-      const float2 fv = pl[(q >> 16) * PW + (int)(short)(q & 0xffff)];
-      if (active && sample_ok(fv)) {
-        const float2 W = weights(t.z, fv);  // tabulated window weight x inverse variance, times f
-        if constexpr (ORDER == 0) {
-          m.add0(W.x, W.y, W.x * t.z, 1.f);
-        } else {
-          const float2 D = make_float2(t.x, t.y);
-          m.add2(D, __fmul2_rn(D, D), W.x, W.y, W.x * t.z);
+    const float4 *cell = L.tab_cells + 2 * (size_t)h.x;
+    const int n[4] = {nc.x, nc.y, nc.z, nc.w};
+    int k = 0;
+#if LPA_TAB_PREFETCH
+    // the next cell's two records are loaded while this one is added (the table ends with one
+    // padding cell, so that the load after a list's last cell stays inside it)
+    float4 gn = __ldg(cell), kn = __ldg(cell + 1);
+#endif
+#pragma unroll
+    for (int q0 = 0; q0 < NSP; q0++) {
+      const int kend = min(n[q0], h.y);
+#pragma unroll(kTabUnroll)
+      for (; k < kend; k++) {
+#if LPA_TAB_PREFETCH
+        const float4 g = gn, kw = kn;
+        gn = __ldg(cell + 2 * k + 2);
+        kn = __ldg(cell + 2 * k + 3);
+#else
+        const float4 g = __ldg(cell + 2 * k);
+        const float4 kw = __ldg(cell + 2 * k + 1);
+#endif
+        const int qc = __float_as_int(g.z);
+        const float2 fv = pl[(qc >> 16) * PW + (int)(short)(qc & 0xffff)];
+        if (active && sample_ok(fv)) {
+          const float Kq[4] = {kw.x, kw.y, kw.z, kw.w};
+          const float2 D = make_float2(g.x, g.y);
+          const float2 D2 = __fmul2_rn(D, D);
+          if constexpr (ORDER > 0 && NSP == 1) {  // compensated sums: one scale per pass
+            const float2 W = weights(Kq[0], fv);
+            m[0].add2(D, D2, W.x, W.y, W.x * Kq[0]);
+          } else {
+            float sm[15];
+            if constexpr (ORDER > 0) MOM::monomials(D, D2, sm);
+#pragma unroll
+            for (int q = q0; q < NSP; q++) {
+              const float2 W = weights(Kq[q], fv);  // tabulated window weight x inverse variance, times f
+              if constexpr (ORDER == 0) m[q].add0(W.x, W.y, W.x * Kq[q], 1.f);
+              else m[q].adds(sm, D, D2, W.x, W.y, W.x * Kq[q]);
+            }
+          }
         }
       }
     }
@@ -796,9 +818,15 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   }
   __syncthreads();
 
-  constexpr bool TAB_ = MODE == LPA_TABULATED;
+  constexpr bool TAB_ = lpa_mode_tab(MODE);
   if constexpr (!TAB_) {
     if (RD(L.off_pos) == 0u) {  // a plan without the position table (offset 0 holds a raw box)
+      if (tid == 0) atomicOr(L.status, LPA_ERR_BOUNDS);
+      return false;
+    }
+  } else {
+    // a table built for another number of scales per pass (its passes would not be this kernel's)
+    if (RD(L.tab_nsp) != (GLOBAL_MAPS ? 1 : MultiScale<ORDER, COMP, MODE>::value) || L.tab_hdr == nullptr) {
       if (tid == 0) atomicOr(L.status, LPA_ERR_BOUNDS);
       return false;
     }
@@ -821,7 +849,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
     const size_t opix = (size_t)v * RD(L.out_w) + u;
     const float log2e = 1.4426950408889634f;
 
-    constexpr bool TAB = MODE == LPA_TABULATED, STEER = lpa_mode_steered(MODE), GRAD = MODE == LPA_GRADIENTS;
+    constexpr bool TAB = lpa_mode_tab(MODE), STEER = lpa_mode_steered(MODE), GRAD = MODE == LPA_GRADIENTS;
     constexpr bool F64 = !lpa_mode_f32(MODE);  // the FP64 re-solve is compiled in
     // the pixel's point in each sensor, once: anchor (FP64 at the 8x8 block corner) + small FP32
     // step, split into sample cell and fraction; every channel and scale reads it back
@@ -889,8 +917,8 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
     // the persistent many-frame kernel walks once per scale (its register budget, shared by every
     // frame it serves, has no room for the sums of several scales)
     constexpr int NSP = GLOBAL_MAPS ? 1 : MultiScale<ORDER, COMP, MODE>::value;
-    if constexpr (NSP > 1) {
-      if (J >= 2) {
+    if constexpr (NSP > 1 || TAB) {
+      if (TAB || J >= 2) {
         // all scales of a channel from one walk per sensor (up to NSP scales per pass): slot q of
         // a pass holds scale j0 + q - lead, so that the pass's largest scale is always the last slot
   #pragma unroll 1
@@ -901,9 +929,9 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
           const float gsc = (c == 1) ? RD(L.green_ratio) : 1.f;
           // the first pass takes what the later full passes leave (the small scales), so that the
           // largest scales share the longest walk
-          const int npass = (J + NSP - 1) / NSP;
+          const int npass = lpa_n_passes(J, NSP);
   #pragma unroll 1
-          for (int pass = 0, j0 = 0, nj = J - NSP * (npass - 1); pass < npass; pass++, j0 += nj, nj = NSP) {
+          for (int pass = 0, j0 = 0, nj = lpa_first_pass_scales(J, NSP); pass < npass; pass++, j0 += nj, nj = NSP) {
             if (!DIAG && __all_sync(LPA_FULL, ici.done)) break;
             const int lead = NSP - nj;
             float R2s[NSP], cxs[NSP];
@@ -919,11 +947,13 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
             const float taper = RD(L.taper);
             const bool act = DIAG ? pix : !ici.done;
   #pragma unroll 1
-            for (int s = 0; s < S; s++)
-              walk_sensor<MODE, 1>(L.s[s], pos[s * NT], c, R, fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q,
-                                   [&](float2 D, float2 fv) { window_cell_ms<ORDER, NSP, MODE>(m, D, fv, R2s, cxs, taper, Q); });
-            // the fits in ascending scale order, always from slot 0: the later slots move down one
-            // place after each fit, so that slot 0 ends with the pass's largest scale
+            for (int s = 0; s < S; s++) {
+              if constexpr (TAB)
+                accumulate_table<ORDER, NSP>(m, L, s, c, pass, npass, u, v, fp_x0[s], fp_y0[s], smem, act, L.status);
+              else
+                walk_sensor<MODE, 1>(L.s[s], pos[s * NT], c, R, fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q,
+                                     [&](float2 D, float2 fv) { window_cell_ms<ORDER, NSP, MODE>(m, D, fv, R2s, cxs, taper, Q); });
+            }
             // the fits in ascending scale order
   #pragma unroll
             for (int q = 0; q < NSP; q++) {
@@ -956,13 +986,9 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
         const float cexp = -log2e / (2.f * sg * sg);
         const bool act = DIAG ? pix : !ici.done;
   #pragma unroll 1
-        for (int s = 0; s < S; s++) {
-          if constexpr (TAB)
-            accumulate_table<ORDER>(m, L, s, c, j, u, v, fp_x0[s], fp_y0[s], smem, act, L.status);
-          else
-            accumulate_sensor<ORDER, COMP, MODE>(m, L.s[s], pos[s * NT], c, R, R2, cexp, RD(L.taper),
-                                                  fp_x0[s], fp_y0[s], smem, act, RD(L.status), Q);
-        }
+        for (int s = 0; s < S; s++)
+          accumulate_sensor<ORDER, COMP, MODE>(m, L.s[s], pos[s * NT], c, R, R2, cexp, RD(L.taper), fp_x0[s],
+                                                fp_y0[s], smem, act, RD(L.status), Q);
         const FitOut f = fit_of(m);
         if constexpr (GRAD) {  // Section 5.4: the order-1 fit's linear coefficients; 0 if not usable
           if (pix) {

@@ -62,15 +62,19 @@ struct LpaLaunch {
   int px;                        // output pixels per thread (0 or 1: one; 2: two, 16-row tiles)
   int tile0;                     // single-frame grid: CTA b reconstructs tile tile0 + b
   int tile_count;                // single-frame grid size; 0 = every tile from tile0 on
-  // Tabulated window weights (NULL = the window is searched and evaluated per pixel). Entry
-  // ((((s * 2 + pu) * 2 + pv) * 4 + phase) * n_scales + j) of tab_hdr gives the first cell, the
-  // number of cells and the cell-offset bounds of sensor s, output parity (pu, pv), colour phase
-  // (ox + 2 oy) and scale j; a cell is {dx, dy, K, (qy << 16) | (qx & 0xffff)}: the offset of the
-  // sample from the pixel's point in reference px, its window weight and its lattice offset from
-  // the pixel's even lattice cell.
-  const int4 *tab_hdr;           // {first, count, (qx_min & 0xffff) | (qx_max << 16), same for qy}
+  // Tabulated window weights (NULL = the window is searched and evaluated per pixel), in passes of
+  // tab_nsp scales as the kernel walks them (lpa_scale_passes). Entry
+  // ((((s * 2 + pu) * 2 + pv) * 4 + phase) * n_pass + pass) of tab_hdr, two int4, describes the
+  // cells of sensor s, output parity (pu, pv) and colour phase (ox + 2 oy) inside the window of the
+  // pass's largest scale, sorted by distance: {first cell, number of cells, qx bounds, qy bounds}
+  // and {n_0 .. n_3}, the cells of slot q's scale being the first n_q (0 for the slots a short
+  // first pass leaves empty). A cell is two float4: {dx, dy, bits of (qy << 16) | (qx & 0xffff),
+  // 0}, the offset of the sample from the pixel's point in reference px and its lattice offset from
+  // the pixel's even lattice cell, and {K_0 .. K_3}, its window weight at the scale of each slot.
+  const int4 *tab_hdr;           // bounds packed as (min & 0xffff) | (max << 16)
   const float4 *tab_cells;
-  // Kernel mode (LPA_SEARCHED .. LPA_STEERED_F32 below). Adaptive reconstruction (Sections 5.4-5.5):
+  int tab_nsp;                   // scales per pass the table was built for
+  // Kernel mode (LPA_SEARCHED .. LPA_TABULATED_F32 below). Adaptive reconstruction (Sections 5.4-5.5):
   // LPA_STEERED reads the steering matrix of each output pixel from aux ([out_h][out_w][3]: C11,
   // C12, C22); LPA_GRADIENTS writes the gradient of the green fit to aux ([out_h][out_w][2]).
   // LPA_LITERAL: the searched window with the noise weight printed in Eq. 6 (K / s, not K / s2).
@@ -78,10 +82,10 @@ struct LpaLaunch {
   float *aux;
 };
 
-// LPA_SEARCHED_F32, LPA_STEERED_F32: the searched or steered window with every fit solved in FP32
-// only, for parameters under which the FP64 re-solve can never trigger ((min_pivot - 1e-4) *
-// cond_fallback >= 2: a usable fit's equilibrated pivots lie in (min_pivot, 1], so their spread
-// stays below cond_fallback).
+// LPA_SEARCHED_F32, LPA_STEERED_F32, LPA_TABULATED_F32: the searched, steered or tabulated window
+// with every fit solved in FP32 only, for parameters under which the FP64 re-solve can never
+// trigger ((min_pivot - 1e-4) * cond_fallback >= 2: a usable fit's equilibrated pivots lie in
+// (min_pivot, 1], so their spread stays below cond_fallback).
 enum {
   LPA_SEARCHED = 0,
   LPA_TABULATED = 1,
@@ -89,14 +93,47 @@ enum {
   LPA_GRADIENTS = 3,
   LPA_LITERAL = 4,
   LPA_SEARCHED_F32 = 5,
-  LPA_STEERED_F32 = 6
+  LPA_STEERED_F32 = 6,
+  LPA_TABULATED_F32 = 7
 };
 __host__ __device__ constexpr bool lpa_mode_steered(int mode) { return mode == LPA_STEERED || mode == LPA_STEERED_F32; }
-__host__ __device__ constexpr bool lpa_mode_f32(int mode) { return mode == LPA_SEARCHED_F32 || mode == LPA_STEERED_F32; }
+__host__ __device__ constexpr bool lpa_mode_tab(int mode) { return mode == LPA_TABULATED || mode == LPA_TABULATED_F32; }
+__host__ __device__ constexpr bool lpa_mode_f32(int mode) {
+  return mode == LPA_SEARCHED_F32 || mode == LPA_STEERED_F32 || mode == LPA_TABULATED_F32;
+}
 // the FP32-only variant of a mode, where it has one
 __host__ __device__ constexpr int lpa_mode_to_f32(int mode) {
-  return mode == LPA_SEARCHED ? LPA_SEARCHED_F32 : mode == LPA_STEERED ? LPA_STEERED_F32 : mode;
+  return mode == LPA_SEARCHED    ? LPA_SEARCHED_F32
+         : mode == LPA_STEERED   ? LPA_STEERED_F32
+         : mode == LPA_TABULATED ? LPA_TABULATED_F32
+                                 : mode;
 }
+
+// Scales per walk of the window cells: the searched, steered and tabulated windows with plain FP32
+// sums feed up to four nested scales from one walk at orders 0 and 1, two at order 2 when the FP64
+// re-solve is compiled out (their sums stay in registers); the other variants walk once per scale.
+#ifndef LPA_MULTI_SCALE
+#define LPA_MULTI_SCALE 2      // order 2
+#endif
+#ifndef LPA_MULTI_SCALE_LOW
+#define LPA_MULTI_SCALE_LOW 4  // order 1
+#endif
+#ifndef LPA_MULTI_SCALE_M0
+#define LPA_MULTI_SCALE_M0 4   // order 0
+#endif
+__host__ __device__ constexpr int lpa_scales_per_walk(int order, bool comp, int mode) {
+  return comp ? 1
+         : lpa_mode_f32(mode)
+             ? (order == 2 ? LPA_MULTI_SCALE : order == 1 ? LPA_MULTI_SCALE_LOW : LPA_MULTI_SCALE_M0)
+         : (mode == LPA_SEARCHED || mode == LPA_STEERED || mode == LPA_TABULATED)
+             ? (order == 2 ? 1 : order == 1 ? LPA_MULTI_SCALE_LOW : LPA_MULTI_SCALE_M0)
+             : 1;
+}
+// The passes over J scales in walks of nsp: the first pass takes what the later full passes leave
+// (the small scales), so that the largest scales share the longest walk. Pass k covers scales
+// j0 .. j0 + nj - 1 in slots lead .. nsp - 1 (lead = nsp - nj).
+__host__ __device__ constexpr int lpa_n_passes(int J, int nsp) { return (J + nsp - 1) / nsp; }
+__host__ __device__ constexpr int lpa_first_pass_scales(int J, int nsp) { return J - nsp * (lpa_n_passes(J, nsp) - 1); }
 
 // Several frames in one graph launch: the tile list is grouped by polynomial order and each
 // order's persistent kernel takes tiles from its own segment. The tile list, the segment bounds

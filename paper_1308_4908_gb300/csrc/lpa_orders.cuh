@@ -14,7 +14,7 @@ namespace lpa_orders {
 template <int ORDER, int MODE, int TH, int PX>
 constexpr bool instantiated() {
   if (PX == 2)  // two pixels per thread: 16-row tiles of 8-row CTAs, the windows batches use
-    return TH == 8 && (MODE == LPA_SEARCHED || MODE == LPA_SEARCHED_F32 || MODE == LPA_TABULATED);
+    return TH == 8 && (MODE == LPA_SEARCHED || MODE == LPA_SEARCHED_F32 || lpa_mode_tab(MODE));
   if (MODE == LPA_GRADIENTS) return ORDER == 1 && TH == 16;
   if (lpa_mode_steered(MODE) || MODE == LPA_LITERAL) return TH == 16;
   return true;
@@ -38,6 +38,7 @@ const void *kernel_mode(int mode) {
     case LPA_LITERAL: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_LITERAL, PX>();
     case LPA_SEARCHED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED_F32, PX>();
     case LPA_STEERED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED_F32, PX>();
+    case LPA_TABULATED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_TABULATED_F32, PX>();
     default: return nullptr;
   }
 }

@@ -173,17 +173,15 @@ def translational(size, seed, shifts):
 
 @pytest.mark.parametrize("order", [0, 1, 2])
 def test_tabulated_weights_match_the_oracle(ctx, order):
-    """Translation-only rigs at 1x output read their windows from the per-frame table (Section 8)
-    at orders 0 and 1: every pixel within tolerance of the oracle; the searched path gives the same
-    fit up to rounding (the two paths are different code: their outputs are not bit-identical). At
-    order 2 the searched window, which feeds two scales from one walk, is the faster path and is
-    kept: the switch changes nothing."""
+    """Translation-only rigs at 1x output read their windows from the per-frame table (Section 8):
+    every pixel within tolerance of the oracle; the searched path gives the same fit up to
+    rounding (the two paths are different code: their outputs are not bit-identical)."""
     fr = translational(96, 1040 + order, [(0.0, 0.0), (0.4, 0.45), (-1.3, 0.7)])
     p = dataclasses.replace(fr.params, order=order)
     _, g, _ = check_frame(ctx, fr, p)
     q = dataclasses.replace(p, tab_weights=0)
     _, h, _ = check_frame(ctx, fr, q)
-    assert np.array_equal(g["out"], h["out"]) == (order == 2)
+    assert not np.array_equal(g["out"], h["out"])
 
 
 def test_tabulated_weights_other_shifts_and_scales(ctx):
@@ -192,6 +190,25 @@ def test_tabulated_weights_other_shifts_and_scales(ctx):
     check_frame(ctx, fr, dataclasses.replace(fr.params, sigmas=(0.7,)))
     check_frame(ctx, fr, dataclasses.replace(fr.params, order=1, sigmas=tuple(0.5 + 0.2 * i for i in range(8))))
     check_frame(ctx, fr, dataclasses.replace(fr.params, out_dtype=1), extra=parity.HALF_TOL)
+
+
+@pytest.mark.parametrize("order,sigmas,extra", [
+    (2, (0.6, 0.9, 1.3), {}),                       # two scales per pass: a short first pass
+    (0, (0.5, 0.7, 0.9, 1.2, 1.6), {}),             # four per pass: passes of 1 and 4 scales
+    (2, (1.1,), {}),                                # one scale in the second slot of one pass
+    (1, (0.6, 0.9, 1.3, 1.8), {"accum": 1}),        # compensated sums: one scale per pass
+    (1, (0.6, 0.9, 1.3, 1.8), {"cond_fallback": 1.0}),  # the FP64 re-solve compiled in
+])
+def test_tabulated_weights_passes(ctx, order, sigmas, extra):
+    """The table holds the cells of each pass's largest window, nearest first, with one weight per
+    scale of the pass: scale counts that leave the first pass short, a single scale, compensated
+    sums (one scale per pass) and the FP64 re-solve variant all match the oracle, and differ from
+    the searched path only by rounding."""
+    fr = translational(72, 1070 + order, [(0.25, -0.6), (-1.4, 0.35), (0.9, 1.2)])
+    p = dataclasses.replace(fr.params, order=order, sigmas=sigmas, **extra)
+    _, g, _ = check_frame(ctx, fr, p)
+    _, h, _ = check_frame(ctx, fr, dataclasses.replace(p, tab_weights=0))
+    assert not np.array_equal(g["out"], h["out"])
 
 
 def test_tabulated_weights_only_for_translations(ctx):

@@ -37,15 +37,15 @@ def _ctx(max_tables=None):
 
 
 def _translational(n, seed):
-    """n small frames whose sensors are pure translations (distinct per frame), 1x output, orders 0
-    and 1 (the orders that read tabulated weights): each plans a weight table of its own."""
+    """n small frames whose sensors are pure translations (distinct per frame), 1x output, orders
+    0, 1, 2 in turn: each plans a tabulated weight table of its own."""
     frames = synth.batching(n_frames=n, size_cap=80, seed=seed)
     for k, fr in enumerate(frames):
         w, h = fr.sensors[0].width, fr.sensors[0].height
         for i, s in enumerate(fr.sensors):
             s.affine = np.asarray(synth.affine_about_center(w, h, 0.31 * i - 0.23 + 0.07 * k, 0.11 * k - 0.4 * i))
             s.raw = synth.simulate_raw(fr.scene, s, seed, 100 * k + i)
-        frames[k] = dataclasses.replace(fr, params=dataclasses.replace(fr.params, out_w=w, out_h=h, order=k % 2,
+        frames[k] = dataclasses.replace(fr, params=dataclasses.replace(fr.params, out_w=w, out_h=h, order=k % 3,
                                                                         out_affine=synth.output_affine(w, h, w, h)))
     return frames
 
