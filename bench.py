@@ -301,6 +301,8 @@ def run_batching(ctx, frames, dev, reps: int = 10):
     t_forms = [timed(lambda f=f: ctx.reconstruct_batch(hf, hdr.hdr_batch_config(16, 0, 1, f), stream)) for f in (0, 1)]
     t_px2 = timed(lambda: ctx.reconstruct_batch(hf, hdr.hdr_batch_config(16, 0, 1, 0, 2), stream))
     t_th8 = timed(lambda: ctx.reconstruct_batch(hf, hdr.hdr_batch_config(8, 0, 1, 0), stream))
+    t_st2 = [timed(lambda th=th: ctx.reconstruct_batch(hf, hdr.hdr_batch_config(th, 0, 1, 0, 1, 2), stream))
+             for th in (16, 8)]
     t_plain = timed(plain)
     return {"workload": "batching: 16 frames, raw sizes from {512^2, 1280x720, 1920x1080, 2048^2}, 2-4 sensors "
                         "(ND 1, 1/8, 1/64, 1/512), order 0-2, output 1x or 1.5x, 4 scales with ICI",
@@ -308,10 +310,13 @@ def run_batching(ctx, frames, dev, reps: int = 10):
             "batched": {"ms": round(t_batch, 3), "mpx_s": round(px / t_batch / 1e3, 1), "gpu_launches": 1,
                         "config": {"form": ("graph of per-frame grids", "persistent per-order kernels")[best.form],
                                    "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm,
-                                   "cost_order": best.cost_order, "px_per_thread": max(best.px_per_thread, 1)}},
+                                   "cost_order": best.cost_order, "px_per_thread": max(best.px_per_thread, 1),
+                                   "stages": max(best.stages, 1)}},
             "forms_ms": {"graph of per-frame grids (16-row tiles)": round(t_forms[0], 3),
                          "graph of per-frame grids (8-row tiles)": round(t_th8, 3),
                          "graph of per-frame grids (16-row tiles, two pixels per thread)": round(t_px2, 3),
+                         "graph of per-frame grids (16-row tiles, two staging buffers)": round(t_st2[0], 3),
+                         "graph of per-frame grids (8-row tiles, two staging buffers)": round(t_st2[1], 3),
                          "persistent per-order kernels (16-row tiles, as many CTAs as fit)": round(t_forms[1], 3)},
             "per_frame": {"ms": round(t_plain, 3), "mpx_s": round(px / t_plain / 1e3, 1), "gpu_launches": len(frames)},
             "speedup": round(t_plain / t_batch, 3), "l2": "flushed between timed repetitions"}

@@ -198,6 +198,11 @@ typedef struct {
   int32_t px_per_thread;        /* form 0: output pixels per thread, 0 or 1 = one; 2 = two, each
                                    thread its pixels one after the other (tile_h 16 only: 16-row
                                    tiles of 128 threads); adaptive frames always take one        */
+  int32_t stages;               /* form 0: staging buffers per CTA, 0 or 1 = one tile per CTA; 2 =
+                                   each CTA takes four tiles and bulk-copies the next tile's raw
+                                   footprints into a second buffer while it reconstructs the
+                                   current one (one pixel per thread; frames with compensated sums
+                                   or adaptive windows take one). Results are identical.          */
 } hdr_batch_config;
 
 /* Reconstruct n_frames (1..4096) frames of any sizes, rigs, orders and scales in one graph launch
@@ -214,8 +219,8 @@ typedef struct {
 hdr_status hdr_reconstruct_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames,
                                  const hdr_batch_config *cfg, void *cuda_stream);
 
-/* Autotuner: times every candidate configuration (form, tile height 8/16, CTAs per SM, frame
- * order) on this batch, keeps the fastest for batches of the same kind (orders present, largest
+/* Autotuner: times every candidate configuration (form, tile height 8/16, pixels per thread,
+ * staging buffers, CTAs per SM, frame order) on this batch, keeps the fastest for batches of the same kind (orders present, largest
  * sensor count, scale count, output-size bucket) and writes it to *best. Synchronous. */
 hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, hdr_batch_config *best,
                           void *cuda_stream);

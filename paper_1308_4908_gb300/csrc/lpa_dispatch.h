@@ -52,14 +52,15 @@ cudaError_t lpa_launch_order2(const LpaLaunch &L, bool comp, bool diag, cudaStre
 
 // The single-frame kernel of order M for that configuration (for graph kernel nodes): mode is one
 // of LPA_SEARCHED .. LPA_TABULATED_F32, tile_h the rows of a tile, px the pixels per thread (the CTA
-// has 16 x tile_h / px threads); nullptr where that combination is not instantiated.
-const void *lpa_kernel_order0(bool comp, bool diag, int mode, int tile_h, int px);
-const void *lpa_kernel_order1(bool comp, bool diag, int mode, int tile_h, int px);
-const void *lpa_kernel_order2(bool comp, bool diag, int mode, int tile_h, int px);
-inline const void *lpa_kernel(int order, bool comp, bool diag, int mode, int tile_h, int px = 1) {
-  return order == 0   ? lpa_kernel_order0(comp, diag, mode, tile_h, px)
-         : order == 1 ? lpa_kernel_order1(comp, diag, mode, tile_h, px)
-                      : lpa_kernel_order2(comp, diag, mode, tile_h, px);
+// has 16 x tile_h / px threads), stages the staging buffers per CTA (the grid is then
+// lpa_grid_ctas(tiles, stages)); nullptr where that combination is not instantiated.
+const void *lpa_kernel_order0(bool comp, bool diag, int mode, int tile_h, int px, int stages);
+const void *lpa_kernel_order1(bool comp, bool diag, int mode, int tile_h, int px, int stages);
+const void *lpa_kernel_order2(bool comp, bool diag, int mode, int tile_h, int px, int stages);
+inline const void *lpa_kernel(int order, bool comp, bool diag, int mode, int tile_h, int px = 1, int stages = 1) {
+  return order == 0   ? lpa_kernel_order0(comp, diag, mode, tile_h, px, stages)
+         : order == 1 ? lpa_kernel_order1(comp, diag, mode, tile_h, px, stages)
+                      : lpa_kernel_order2(comp, diag, mode, tile_h, px, stages);
 }
 
 // Persistent launch of order M over its segment of a many-frame tile list (tile height 8 or 16).

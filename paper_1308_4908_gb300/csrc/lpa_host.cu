@@ -439,12 +439,17 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
 #ifndef LPA_FRAME_TILE_H
 #define LPA_FRAME_TILE_H 16  // tile height of single-frame launches
 #endif
+#ifndef LPA_FRAME_STAGES
+#define LPA_FRAME_STAGES 1   // staging buffers per CTA of single-frame launches
+#endif
 
 // Fill the launch descriptor for one frame. raw: device pointers per sensor.
 // reach: the largest window grows by this factor (the steered window of Section 5.4 reaches
 // 1 / sqrt(smallest eigenvalue of C) times the isotropic radius).
+// stages: 2 = the two-buffer kernel (each CTA copies its next tile while computing the current one)
+// where it is built (plain sums, the searched or tabulated window), else 1.
 hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, const uint16_t *const *raw,
-                    LpaLaunch &L, int tile_h = 16, double reach = 1.0) {
+                    LpaLaunch &L, int tile_h = 16, double reach = 1.0, int stages = 1) {
   memset(&L, 0, sizeof(L));
   L.n_sensors = rig.n;
   L.order = p->order;
@@ -556,25 +561,41 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
     L.off_pos = off;
     off += (uint32_t)(rig.n * 16 * LPA_TILE * tile_h);
   }
-  L.smem_bytes = off;
   int max_smem = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, env.device));
+  L.stages = 1;
+  for (int s = 0; s < rig.n; s++) L.s[s].off_raw2 = L.s[s].off_raw;
+  if (stages == 2 && lpa_stages2_built(L.mode, p->accum != 0)) {
+    // the second buffer's raw boxes, where they fit beside the rest (else one buffer)
+    uint32_t off2 = off, at[LPA_MAX_SENSORS];
+    for (int s = 0; s < rig.n; s++) {
+      off2 = (off2 + 127) / 128 * 128;
+      at[s] = off2;
+      off2 += (uint32_t)(L.s[s].box_w * L.s[s].box_h * 2);
+    }
+    if ((int)off2 <= max_smem - 1024) {
+      for (int s = 0; s < rig.n; s++) L.s[s].off_raw2 = at[s];
+      off = off2;
+      L.stages = 2;
+    }
+  }
+  L.smem_bytes = off;
   if ((int)off > max_smem - 1024)
     return fail(HDR_E_UNSUPPORTED, "staging needs %u bytes of shared memory (limit %d)", off, max_smem - 1024);
   return HDR_OK;
 }
 
 hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
-                double reach = 1.0, bool tabulate = true) {
+                double reach = 1.0, bool tabulate = true, int stages = 1) {
   return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, tabulate}, rig, p, raw, L,
-                  LPA_FRAME_TILE_H, reach);
+                  LPA_FRAME_TILE_H, reach, stages);
 }
 
 // plan() of a single-frame call through the context's plan cache.
 hdr_status cached_plan(hdr_ctx *ctx, int32_t rig_id, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
-                       bool tabulate) {
+                       bool tabulate, int stages) {
   const Rig &rig = ctx->rigs[rig_id];
-  std::vector<uint8_t> key(sizeof(int32_t) + 2 * sizeof(uint64_t) + sizeof(hdr_params) + 1 + rig.n * sizeof(void *));
+  std::vector<uint8_t> key(sizeof(int32_t) + 2 * sizeof(uint64_t) + sizeof(hdr_params) + 2 + rig.n * sizeof(void *));
   uint8_t *k = key.data();
   memcpy(k, &rig_id, sizeof(int32_t));
   k += sizeof(int32_t);
@@ -585,13 +606,14 @@ hdr_status cached_plan(hdr_ctx *ctx, int32_t rig_id, const hdr_params *p, const 
   memcpy(k, p, sizeof(hdr_params));
   k += sizeof(hdr_params);
   *k++ = tabulate ? 1 : 0;
+  *k++ = (uint8_t)stages;
   memcpy(k, raw, rig.n * sizeof(void *));
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) {
     L = it->second;
     return HDR_OK;
   }
-  hdr_status st = plan(ctx, rig, p, raw, L, 1.0, tabulate);
+  hdr_status st = plan(ctx, rig, p, raw, L, 1.0, tabulate, stages);
   if (st) return st;
   if (ctx->plans.size() >= 256) ctx->plans.clear();
   ctx->plans.emplace(std::move(key), L);
@@ -630,7 +652,7 @@ hdr_status reconstruct_impl(hdr_ctx *ctx, int32_t rig_id, const hdr_params *para
     return fail(HDR_E_UNSUPPORTED, "the level maps are computed with the inverse-variance weight (weight_mode 0)");
   LpaLaunch L;
   // the diagnostic (level maps) kernel searches every window
-  st = cached_plan(ctx, rig_id, params, raw_dev, L, levels_dev == nullptr);
+  st = cached_plan(ctx, rig_id, params, raw_dev, L, levels_dev == nullptr, levels_dev ? 1 : LPA_FRAME_STAGES);
   if (st) return st;
   L.out = out_dev;
   L.choice = choice_dev;
@@ -872,7 +894,7 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
   const size_t plane = (size_t)params->out_w * params->out_h;
   const size_t esize = params->out_dtype ? 2 : 4;
   LpaLaunch L;
-  st = cached_plan(ctx, rig_id, params, raw_dev, L, true);
+  st = cached_plan(ctx, rig_id, params, raw_dev, L, true, LPA_FRAME_STAGES);
   if (st) return st;
   L.out = ctx->out_stage;
   L.choice = choice_host ? ctx->choice_stage : nullptr;
@@ -1177,15 +1199,16 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
       sp.tab_weights = 0;
       pp = &sp;
     }
+    const int px = (cfg.px_per_thread == 2 && !F.calpa) ? 2 : 1;
     hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, !F.calpa}, ctx->rigs[F.rig_id],
                              pp, F.raw_dev, plans[f], F.calpa ? 16 : cfg.tile_h,
-                             F.calpa ? lpa_calpa_reach(F.calpa) : 1.0);
+                             F.calpa ? lpa_calpa_reach(F.calpa) : 1.0, (F.calpa || px != 1) ? 1 : cfg.stages);
     if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
     if (F.calpa) {
       plans[f].mode = lpa_mode_f32(plans[f].mode) ? LPA_STEERED_F32 : LPA_STEERED;
       plans[f].aux = aux[f] + npx * 2;  // the steering matrices
     }
-    plans[f].px = (cfg.px_per_thread == 2 && !F.calpa) ? 2 : 1;
+    plans[f].px = px;
     plans[f].out = F.out_dev;
     plans[f].choice = F.choice_dev;
     plans[f].levels = nullptr;
@@ -1211,17 +1234,17 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
   std::vector<void *> args(order.size());
   for (size_t k = 0; k < order.size(); k++) {
     const LpaLaunch &L = plans[order[k]];
-    const void *fn = lpa_kernel(L.order, comp, false, L.mode, L.tile_h, L.px);
+    const void *fn = lpa_kernel(L.order, comp, false, L.mode, L.tile_h, L.px, L.stages);
     if (!fn)
-      return fail(HDR_E_INTERNAL, "no kernel for order %d, mode %d, tile height %d, %d pixels per thread", L.order,
-                  L.mode, L.tile_h, L.px);
+      return fail(HDR_E_INTERNAL, "no kernel for order %d, mode %d, tile height %d, %d pixels per thread, %d stages",
+                  L.order, L.mode, L.tile_h, L.px, L.stages);
     CUDA_TRY(lpa_opt_in(fn));
     // grid size and shared memory are set on each replay: graphs are kept per sequence of kernels
-    key.push_back({L.order * 8 + L.mode, comp ? 1 : 0, L.tile_h, L.px, 0});
+    key.push_back({L.order * 8 + L.mode, comp ? 1 : 0, L.tile_h, L.px, L.stages});
     args[k] = &plans[order[k]];
     kp[k] = cudaKernelNodeParams{};
     kp[k].func = const_cast<void *>(fn);
-    kp[k].gridDim = dim3((unsigned)grid[order[k]]);
+    kp[k].gridDim = dim3((unsigned)lpa_grid_ctas(grid[order[k]], L.stages));
     kp[k].blockDim = dim3((unsigned)(LPA_TILE * L.tile_h / L.px));
     kp[k].sharedMemBytes = L.smem_bytes;
     kp[k].kernelParams = &args[k];
@@ -1271,7 +1294,7 @@ hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames
   hdr_status st = check_batch(ctx, n_frames, frames);
   if (st) return st;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  hdr_batch_config cfg = {16, 0, 1, 0, 1};
+  hdr_batch_config cfg = {16, 0, 1, 0, 1, 1};
   if (cfg_in) {
     cfg = *cfg_in;
   } else {
@@ -1284,6 +1307,9 @@ hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames
   if (cfg.px_per_thread < 0 || cfg.px_per_thread > 2) return fail(HDR_E_INVALID, "px_per_thread must be 0, 1 or 2");
   if (cfg.px_per_thread == 2 && (cfg.tile_h != 16 || cfg.form != 0))
     return fail(HDR_E_INVALID, "two pixels per thread need tile_h 16 and form 0");
+  if (cfg.stages < 0 || cfg.stages > 2) return fail(HDR_E_INVALID, "stages must be 0, 1 or 2");
+  if (cfg.stages == 2 && (cfg.px_per_thread == 2 || cfg.form != 0))
+    return fail(HDR_E_INVALID, "two staging buffers need one pixel per thread and form 0");
   for (int f = 0; f < n_frames; f++)
     if (frames[f].calpa) cfg.form = 0;  // the persistent kernels have no steered window
   if (cfg.form == 0) return batch_run_frames(ctx, n_frames, frames, ranges, cfg, stream, scratch);
@@ -1443,12 +1469,13 @@ extern "C" hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_f
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
-  hdr_batch_config win = {16, 0, 1, 0, 1};
+  hdr_batch_config win = {16, 0, 1, 0, 1, 1};
   float win_ms = 1e30f;
-  // form, tile height, pixels per thread, persistent CTAs per SM and frame order
-  const hdr_batch_config cands[] = {{16, 0, 1, 0, 1}, {8, 0, 1, 0, 1}, {16, 0, 1, 0, 2}, {16, 0, 0, 0, 1},
-                                    {16, 0, 1, 1, 1}, {16, 1, 1, 1, 1}, {16, 2, 1, 1, 1}, {8, 0, 1, 1, 1},
-                                    {8, 2, 1, 1, 1},  {8, 4, 1, 1, 1},  {16, 0, 0, 1, 1}};
+  // form, tile height, pixels per thread, staging buffers, persistent CTAs per SM and frame order
+  const hdr_batch_config cands[] = {{16, 0, 1, 0, 1, 1}, {8, 0, 1, 0, 1, 1}, {16, 0, 1, 0, 2, 1}, {16, 0, 1, 0, 1, 2},
+                                    {8, 0, 1, 0, 1, 2},  {16, 0, 0, 0, 1, 1}, {16, 0, 1, 1, 1, 1}, {16, 1, 1, 1, 1, 1},
+                                    {16, 2, 1, 1, 1, 1}, {8, 0, 1, 1, 1, 1},  {8, 2, 1, 1, 1, 1},  {8, 4, 1, 1, 1, 1},
+                                    {16, 0, 0, 1, 1, 1}};
   for (const hdr_batch_config &c : cands) {
     st = hdr_reconstruct_batch(ctx, n_frames, frames, &c, cuda_stream);  // warm-up (and graph record)
     if (st == HDR_E_UNSUPPORTED) continue;

@@ -701,10 +701,54 @@ __device__ __forceinline__ T reread(const T &x) {
 // global descriptor, whose tensor maps the bulk copies use (otherwise `maps` is &L).
 // `phase` is the parity of the CTA's mbarrier use for this tile. Returns false when the CTA must
 // stop (a bounded wait ran out here or in another CTA).
-template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS, int MODE = LPA_SEARCHED, int PX = 1>
+// The staged footprint of tile `tile` (TR output rows) in each sensor, by threads 0 .. S - 1: the
+// sensor-space bounding box of the tile's pixel points, grown by the largest window's half extent
+// and the margin; x origin on a 16-byte boundary.
+template <int TR>
+__device__ __forceinline__ void stage_footprint(const LpaLaunch &L, int tile, int *fp_x0, int *fp_y0) {
+  const int tid = threadIdx.x;
+  if (tid >= L.n_sensors) return;
+  const int u0 = (tile % L.tiles_x) * LPA_TILE, v0 = (tile / L.tiles_x) * TR;
+  const LpaSensorK &Sk = L.s[tid];
+  double mnx = 1e300, mny = 1e300;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    double uu = u0 + (k & 1) * (LPA_TILE - 1), vv = v0 + (k >> 1) * (TR - 1);
+    double qx = Sk.G[0] * uu + Sk.G[1] * vv + Sk.G[2];
+    double qy = Sk.G[3] * uu + Sk.G[4] * vv + Sk.G[5];
+    mnx = fmin(mnx, fmin(fmax(qx, -LPA_FAR), LPA_FAR));
+    mny = fmin(mny, fmin(fmax(qy, -LPA_FAR), LPA_FAR));
+  }
+  int x0 = (int)floor(mnx - Sk.ext_x);
+  int y0 = (int)floor(mny - Sk.ext_y);
+  x0 -= ((x0 % 8) + 8) % 8;
+  y0 -= (y0 & 1);
+  fp_x0[tid] = x0;
+  fp_y0[tid] = y0;
+}
+
+// One thread issues the bulk tensor copies of every sensor's footprint into staging buffer `stage`
+// and the byte count they complete on `mbar`.
+template <bool GLOBAL_MAPS>
+__device__ __forceinline__ void stage_issue(const LpaLaunch &L, const LpaLaunch *maps, unsigned char *smem, int stage,
+                                            uint64_t *mbar, const int *fp_x0, const int *fp_y0) {
+  const int S = L.n_sensors;
+  // tensor maps kept in global memory are rewritten between launches at the same addresses:
+  // make this launch's contents visible to the tensor-map proxy before the copies use them
+  if (GLOBAL_MAPS)
+    for (int s = 0; s < S; s++) tensormap_acquire(&maps->s[s].tmap);
+  mbar_arrive_expect_tx(mbar, L.tx_bytes);
+  for (int s = 0; s < S; s++)
+    tma_load_2d(smem + (stage ? L.s[s].off_raw2 : L.s[s].off_raw), &maps->s[s].tmap, fp_x0[s], fp_y0[s], mbar);
+}
+
+// STAGED: the footprint (fp_x0, fp_y0) and the copies of this tile into buffer `stage` were issued
+// before the call (the caller waits for copies in flight if this returns false).
+template <int ORDER, bool COMP, bool DIAG, int TH, bool GLOBAL_MAPS, int MODE = LPA_SEARCHED, int PX = 1,
+          bool STAGED = false>
 __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch *maps, int tile, unsigned char *smem, uint64_t *mbar,
                                              uint32_t phase, int *fp_x0, int *fp_y0,
-                                             Anchor (*anchors)[LPA_MAX_SENSORS]) {
+                                             Anchor (*anchors)[LPA_MAX_SENSORS], int stage = 0) {
   constexpr int NT = LPA_TILE * TH;  // threads
   constexpr int TR = TH * PX;        // tile rows: PX pixels per thread, TH rows apart
   const int tid = threadIdx.x;
@@ -717,26 +761,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   const int u0 = tu * LPA_TILE, v0 = tv * TR;
   const int S = L.n_sensors;
 
-  if (tid < S) {
-    // staged footprint: sensor-space bounding box of the tile's pixel points, grown by the
-    // largest window's half extent and the margin; x origin on a 16-byte boundary
-    const LpaSensorK &Sk = L.s[tid];
-    double mnx = 1e300, mny = 1e300;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      double uu = u0 + (k & 1) * (LPA_TILE - 1), vv = v0 + (k >> 1) * (TR - 1);
-      double qx = Sk.G[0] * uu + Sk.G[1] * vv + Sk.G[2];
-      double qy = Sk.G[3] * uu + Sk.G[4] * vv + Sk.G[5];
-      mnx = fmin(mnx, fmin(fmax(qx, -LPA_FAR), LPA_FAR));
-      mny = fmin(mny, fmin(fmax(qy, -LPA_FAR), LPA_FAR));
-    }
-    int x0 = (int)floor(mnx - Sk.ext_x);
-    int y0 = (int)floor(mny - Sk.ext_y);
-    x0 -= ((x0 % 8) + 8) % 8;
-    y0 -= (y0 & 1);
-    fp_x0[tid] = x0;
-    fp_y0[tid] = y0;
-  }
+  if constexpr (!STAGED) stage_footprint<TR>(L, tile, fp_x0, fp_y0);
   constexpr int NA = 2 * (TR / LPA_ANCHOR);  // anchor blocks per tile
   if (tid >= 32 && tid < 32 + NA * S) {
     const int k = tid - 32, a = k % NA, s = k / NA;
@@ -748,14 +773,8 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
     anchors[a][s] = Anchor{(int)flx, (int)fly, (float)(qx - flx), (float)(qy - fly)};
   }
   __syncthreads();
-  if (tid == 0) {
-    // tensor maps kept in global memory are rewritten between launches at the same addresses:
-    // make this launch's contents visible to the tensor-map proxy before the copies use them
-    if (GLOBAL_MAPS)
-      for (int s = 0; s < S; s++) tensormap_acquire(&maps->s[s].tmap);
-    mbar_arrive_expect_tx(mbar, L.tx_bytes);
-    for (int s = 0; s < S; s++) tma_load_2d(smem + L.s[s].off_raw, &maps->s[s].tmap, fp_x0[s], fp_y0[s], mbar);
-  }
+  if constexpr (!STAGED)
+    if (tid == 0) stage_issue<GLOBAL_MAPS>(L, maps, smem, 0, mbar, fp_x0, fp_y0);
   bool landed = mbar_wait_bounded(mbar, phase, 1u << 20);
   landed = __syncthreads_and(landed);
   if (!landed) {
@@ -771,7 +790,7 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   constexpr bool LIT = MODE == LPA_LITERAL;
   for (int s = 0; s < S; s++) {
     const LpaSensorK &Sk = L.s[s];
-    const uint16_t *raw = reinterpret_cast<const uint16_t *>(smem + Sk.off_raw);
+    const uint16_t *raw = reinterpret_cast<const uint16_t *>(smem + (stage ? Sk.off_raw2 : Sk.off_raw));
     float2 *planes = reinterpret_cast<float2 *>(smem + Sk.off_planes);
     const int bw = Sk.box_w, n = bw * Sk.box_h, PW = bw >> 1, PP = (bw >> 1) * (Sk.box_h >> 1);
     const int x0 = fp_x0[s], y0 = fp_y0[s];
@@ -1022,15 +1041,51 @@ struct FrameOccupancy {
 
 // PX pixels per thread: a CTA of 16 x TH threads reconstructs a 16 x (TH PX) tile, each thread its
 // pixels one after the other (the staged footprint and its conversion serve PX times the pixels).
-template <int ORDER, bool COMP, bool DIAG, int TH, int MODE = LPA_SEARCHED, int PX = 1>
+// STAGES 2: CTA b takes the tiles tile0 + b + k gridDim.x of the launch's range and copies each
+// next tile's raw boxes into the other staging buffer before it reconstructs the current tile, so
+// that the copies land while it computes.
+template <int ORDER, bool COMP, bool DIAG, int TH, int MODE = LPA_SEARCHED, int PX = 1, int STAGES = 1>
 __global__ void __launch_bounds__(LPA_TILE *TH, (FrameOccupancy<ORDER, COMP, TH, MODE>::value)) lpa_reconstruct(const __grid_constant__ LpaLaunch L) {
+  static_assert(STAGES == 1 || STAGES == 2, "one or two staging buffers");
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ int fp_x0[LPA_MAX_SENSORS], fp_y0[LPA_MAX_SENSORS];
+  __shared__ int fp_x0[STAGES][LPA_MAX_SENSORS], fp_y0[STAGES][LPA_MAX_SENSORS];
   __shared__ Anchor anchors[2 * TH * PX / LPA_ANCHOR][LPA_MAX_SENSORS];
-  __shared__ __align__(8) uint64_t mbar;
-  if (threadIdx.x == 0) mbar_init(&mbar, 1);
-  process_tile<ORDER, COMP, DIAG, TH, false, MODE, PX>(L, &L, L.tile0 + blockIdx.x, smem, &mbar, 0u, fp_x0, fp_y0,
-                                                       anchors);
+  __shared__ __align__(8) uint64_t mbar[STAGES];
+  if (threadIdx.x < STAGES) mbar_init(&mbar[threadIdx.x], 1);
+  if constexpr (STAGES == 1) {
+    process_tile<ORDER, COMP, DIAG, TH, false, MODE, PX>(L, &L, L.tile0 + blockIdx.x, smem, &mbar[0], 0u, fp_x0[0],
+                                                         fp_y0[0], anchors);
+  } else {
+    constexpr int TR = TH * PX;
+    const int end = L.tile_count > 0 ? L.tile0 + L.tile_count : L.tiles_x * L.tiles_y;
+    int t = L.tile0 + (int)blockIdx.x;
+    if (t >= end) return;
+    stage_footprint<TR>(L, t, fp_x0[0], fp_y0[0]);
+    __syncthreads();  // the footprint and the barrier initialisation before the copies
+    if (threadIdx.x == 0) stage_issue<false>(L, &L, smem, 0, &mbar[0], fp_x0[0], fp_y0[0]);
+    // the k-th tile of this CTA uses buffer k & 1 at mbarrier phase (k >> 1) & 1; the buffer the
+    // next tile takes was last read by the previous tile, which every thread has finished
+    for (int k = 0; t < end; k++, t += (int)gridDim.x) {
+      const int st = k & 1, nx = t + (int)gridDim.x;
+      const bool ahead = nx < end;
+      if (ahead) {
+        stage_footprint<TR>(L, nx, fp_x0[st ^ 1], fp_y0[st ^ 1]);
+        __syncthreads();
+        if (threadIdx.x == 0) stage_issue<false>(L, &L, smem, st ^ 1, &mbar[st ^ 1], fp_x0[st ^ 1], fp_y0[st ^ 1]);
+      }
+      const bool ok = process_tile<ORDER, COMP, DIAG, TH, false, MODE, PX, true>(
+          L, &L, t, smem, &mbar[st], (uint32_t)((k >> 1) & 1), fp_x0[st], fp_y0[st], anchors, st);
+      if (!__syncthreads_and(ok)) {
+        // let the copies in flight land before the CTA retires (a wait on a completed phase
+        // returns at once)
+        if (threadIdx.x == 0) {
+          mbar_wait_bounded(&mbar[st], (uint32_t)((k >> 1) & 1), 1u << 20);
+          if (ahead) mbar_wait_bounded(&mbar[st ^ 1], (uint32_t)(((k + 1) >> 1) & 1), 1u << 20);
+        }
+        return;
+      }
+    }
+  }
 }
 
 // Resident CTAs per SM the persistent kernel is compiled for (register cap 64K / (threads x this)):

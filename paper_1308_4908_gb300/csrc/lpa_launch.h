@@ -9,6 +9,7 @@
 #define LPA_TILE 16         // output tile width in pixels; the height TH is 8 or 16 (one thread per pixel)
 #define LPA_ANCHOR 8        // edge of the output blocks whose sensor positions are anchored in FP64
 #define LPA_MARGIN 4        // staging margin in sensor px around every window box
+#define LPA_STAGED_TILES 4  // tiles per CTA of the single-frame kernel with two staging buffers
 
 // Device status word bits (read and cleared by hdr_check).
 #define LPA_ERR_TIMEOUT 1u  // a bounded mbarrier wait ran out
@@ -27,6 +28,7 @@ struct alignas(64) LpaSensorK {
   int box_w, box_h;         // staged footprint in elements; box_w % 8 == 0, box_h even
   float ext_x, ext_y;       // half extent of the window box in sensor px incl. margin (max scale)
   uint32_t off_raw;         // byte offset of the raw box in dynamic shared memory
+  uint32_t off_raw2;        // the second staging buffer's raw box (= off_raw with one buffer)
   uint32_t off_planes;      // byte offset of the four colour-phase planes (float2 each)
   int ix_shift, iy_shift;   // tabulated weights: floor of the translation of G (sensor px)
   const float *bias;        // optional per-pixel frames [height][width] (device)
@@ -61,7 +63,11 @@ struct LpaLaunch {
   int tile_h;                    // tile height (rows) the plan was made for
   int px;                        // output pixels per thread (0 or 1: one; 2: two, 16-row tiles)
   int tile0;                     // single-frame grid: CTA b reconstructs tile tile0 + b
-  int tile_count;                // single-frame grid size; 0 = every tile from tile0 on
+  int tile_count;                // tiles of the launch from tile0 on; 0 = every tile from tile0 on
+  // Staging buffers per CTA of the single-frame kernel: 1 = one tile per CTA; 2 = each CTA takes
+  // LPA_STAGED_TILES tiles (tile0 + b + k grid) and copies the next tile's raw boxes into the
+  // second buffer while it reconstructs the current one.
+  int stages;
   // Tabulated window weights (NULL = the window is searched and evaluated per pixel), in passes of
   // tab_nsp scales as the kernel walks them (lpa_scale_passes). Entry
   // ((((s * 2 + pu) * 2 + pv) * 4 + phase) * n_pass + pass) of tab_hdr, two int4, describes the
@@ -134,6 +140,16 @@ __host__ __device__ constexpr int lpa_scales_per_walk(int order, bool comp, int 
 // j0 .. j0 + nj - 1 in slots lead .. nsp - 1 (lead = nsp - nj).
 __host__ __device__ constexpr int lpa_n_passes(int J, int nsp) { return (J + nsp - 1) / nsp; }
 __host__ __device__ constexpr int lpa_first_pass_scales(int J, int nsp) { return J - nsp * (lpa_n_passes(J, nsp) - 1); }
+
+// The two-buffer single-frame kernel is built for plain sums with the searched or tabulated window.
+__host__ __device__ constexpr bool lpa_stages2_built(int mode, bool comp) {
+  return !comp && (mode == LPA_SEARCHED || mode == LPA_SEARCHED_F32 || lpa_mode_tab(mode));
+}
+// CTAs of a single-frame launch over `tiles` tiles: one per tile, or one per LPA_STAGED_TILES tiles
+// with two staging buffers.
+__host__ __device__ constexpr int lpa_grid_ctas(int tiles, int stages) {
+  return stages == 2 ? (tiles + LPA_STAGED_TILES - 1) / LPA_STAGED_TILES : tiles;
+}
 
 // Several frames in one graph launch: the tile list is grouped by polynomial order and each
 // order's persistent kernel takes tiles from its own segment. The tile list, the segment bounds

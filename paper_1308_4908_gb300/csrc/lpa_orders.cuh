@@ -20,33 +20,40 @@ constexpr bool instantiated() {
   return true;
 }
 
-template <int ORDER, bool COMP, bool DIAG, int TH, int MODE, int PX>
+template <int ORDER, bool COMP, bool DIAG, int TH, int MODE, int PX, int STAGES>
 const void *kernel_fn() {
   if constexpr (!instantiated<ORDER, MODE, TH, PX>() ||
-                (DIAG && (PX != 1 || (MODE != LPA_SEARCHED && MODE != LPA_SEARCHED_F32))))
+                (DIAG && (PX != 1 || (MODE != LPA_SEARCHED && MODE != LPA_SEARCHED_F32))) ||
+                (STAGES == 2 && (DIAG || PX != 1 || !lpa_stages2_built(MODE, COMP))))
     return nullptr;
-  else return (const void *)lpa::lpa_reconstruct<ORDER, COMP, DIAG, TH, MODE, PX>;
+  else return (const void *)lpa::lpa_reconstruct<ORDER, COMP, DIAG, TH, MODE, PX, STAGES>;
 }
 
-template <int ORDER, bool COMP, bool DIAG, int TH, int PX = 1>
+template <int ORDER, bool COMP, bool DIAG, int TH, int PX = 1, int STAGES = 1>
 const void *kernel_mode(int mode) {
   switch (mode) {
-    case LPA_SEARCHED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED, PX>();
-    case LPA_TABULATED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_TABULATED, PX>();
-    case LPA_STEERED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED, PX>();
-    case LPA_GRADIENTS: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_GRADIENTS, PX>();
-    case LPA_LITERAL: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_LITERAL, PX>();
-    case LPA_SEARCHED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED_F32, PX>();
-    case LPA_STEERED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED_F32, PX>();
-    case LPA_TABULATED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_TABULATED_F32, PX>();
+    case LPA_SEARCHED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED, PX, STAGES>();
+    case LPA_TABULATED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_TABULATED, PX, STAGES>();
+    case LPA_STEERED: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED, PX, STAGES>();
+    case LPA_GRADIENTS: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_GRADIENTS, PX, STAGES>();
+    case LPA_LITERAL: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_LITERAL, PX, STAGES>();
+    case LPA_SEARCHED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_SEARCHED_F32, PX, STAGES>();
+    case LPA_STEERED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_STEERED_F32, PX, STAGES>();
+    case LPA_TABULATED_F32: return kernel_fn<ORDER, COMP, DIAG, TH, LPA_TABULATED_F32, PX, STAGES>();
     default: return nullptr;
   }
 }
 
 // The single-frame kernel of this order for a configuration (tile_h rows per tile, px pixels per
-// thread: CTAs of 16 x tile_h / px threads); nullptr if not instantiated.
+// thread: CTAs of 16 x tile_h / px threads; stages staging buffers per CTA); nullptr if not
+// instantiated.
 template <int ORDER>
-const void *kernel(bool comp, bool diag, int mode, int tile_h, int px) {
+const void *kernel(bool comp, bool diag, int mode, int tile_h, int px, int stages) {
+  if (stages == 2) {
+    if (px != 1 || diag || comp) return nullptr;
+    return tile_h == 8 ? kernel_mode<ORDER, false, false, 8, 1, 2>(mode) : kernel_mode<ORDER, false, false, 16, 1, 2>(mode);
+  }
+  if (stages != 1) return nullptr;
   if (px == 2) {
     if (tile_h != 16 || diag) return nullptr;
     return comp ? kernel_mode<ORDER, true, false, 8, 2>(mode) : kernel_mode<ORDER, false, false, 8, 2>(mode);
@@ -65,11 +72,12 @@ template <int ORDER>
 cudaError_t launch(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st) {
   // the diagnostic (level maps) kernel is instantiated for the searched window only
   const int px = L.px > 1 ? L.px : 1;
-  const void *fn = kernel<ORDER>(comp, diag, L.mode, L.tile_h, px);
+  const int stages = L.stages > 1 ? L.stages : 1;
+  const void *fn = kernel<ORDER>(comp, diag, L.mode, L.tile_h, px, stages);
   if (!fn) return cudaErrorInvalidConfiguration;
   cudaError_t e = lpa_opt_in(fn);
   if (e != cudaSuccess) return e;
-  const int grid = L.tile_count > 0 ? L.tile_count : L.tiles_x * L.tiles_y - L.tile0;
+  const int grid = lpa_grid_ctas(L.tile_count > 0 ? L.tile_count : L.tiles_x * L.tiles_y - L.tile0, stages);
   void *args[] = {const_cast<LpaLaunch *>(&L)};
   return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)(LPA_TILE * L.tile_h / px)), args, L.smem_bytes, st);
 }
@@ -112,8 +120,8 @@ int batch_ctas_per_sm(bool comp, int tile_h, uint32_t smem_bytes) {
   cudaError_t lpa_launch_order##N(const LpaLaunch &L, bool comp, bool diag, cudaStream_t st) {             \
     return lpa_orders::launch<N>(L, comp, diag, st);                                                       \
   }                                                                                                        \
-  const void *lpa_kernel_order##N(bool comp, bool diag, int mode, int tile_h, int px) {                    \
-    return lpa_orders::kernel<N>(comp, diag, mode, tile_h, px);                                            \
+  const void *lpa_kernel_order##N(bool comp, bool diag, int mode, int tile_h, int px, int stages) {        \
+    return lpa_orders::kernel<N>(comp, diag, mode, tile_h, px, stages);                                    \
   }                                                                                                        \
   cudaError_t lpa_launch_batch_order##N(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st) { \
     return lpa_orders::launch_batch<N>(B, comp, tile_h, grid, st);                                         \

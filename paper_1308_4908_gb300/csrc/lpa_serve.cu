@@ -404,6 +404,9 @@ hdr_status hdr_server_create(hdr_ctx *ctx, const hdr_server_config *cfg, hdr_ser
   if (cfg->batch.form != 0 && cfg->batch.form != 1) return lpa_fail(HDR_E_INVALID, "batch.form must be 0 or 1");
   if (cfg->batch.px_per_thread < 0 || cfg->batch.px_per_thread > 2)
     return lpa_fail(HDR_E_INVALID, "batch.px_per_thread must be 0, 1 or 2");
+  if (cfg->batch.stages < 0 || cfg->batch.stages > 2) return lpa_fail(HDR_E_INVALID, "batch.stages must be 0, 1 or 2");
+  if (cfg->batch.stages == 2 && (cfg->batch.px_per_thread == 2 || cfg->batch.form != 0))
+    return lpa_fail(HDR_E_INVALID, "batch.stages 2 needs one pixel per thread and form 0");
   hdr_server *s = new (std::nothrow) hdr_server();
   if (!s) return lpa_fail(HDR_E_NOMEM, "host allocation failed");
   s->ctx = ctx;

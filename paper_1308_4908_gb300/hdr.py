@@ -56,7 +56,8 @@ class hdr_frame(ctypes.Structure):
 
 class hdr_batch_config(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("cost_order", ctypes.c_int32),
-                ("form", ctypes.c_int32), ("px_per_thread", ctypes.c_int32)]
+                ("form", ctypes.c_int32), ("px_per_thread", ctypes.c_int32),
+                ("stages", ctypes.c_int32)]
 
 
 class hdr_server_config(ctypes.Structure):

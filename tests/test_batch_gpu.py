@@ -95,6 +95,7 @@ def test_batch_equals_single_frames_for_every_configuration(ctx):
     cfgs = [hdr.hdr_batch_config(th, per_sm, order, 1) for th in (16, 8) for per_sm in (0, 1) for order in (1, 0)]
     cfgs += [hdr.hdr_batch_config(th, 0, order, 0) for th in (16, 8) for order in (1, 0)]
     cfgs += [hdr.hdr_batch_config(16, 0, order, 0, 2) for order in (1, 0)]   # two pixels per thread
+    cfgs += [hdr.hdr_batch_config(th, 0, 1, 0, 1, 2) for th in (16, 8)]      # two staging buffers
     for cfg in cfgs:
         for _, _, _, out, _ in items:
             out.fill_(-7.0)
@@ -125,7 +126,7 @@ def test_tuner_picks_a_configuration_and_batch_uses_it(ctx):
     hf = [ctx.frame(rig, fr.params, raws, out, ch, keep) for rig, fr, raws, out, ch in items]
     best = ctx.tune_batch(hf)
     assert best.tile_h in (8, 16) and 0 <= best.ctas_per_sm <= 8 and best.cost_order in (0, 1) and best.form in (0, 1)
-    assert best.px_per_thread in (1, 2)
+    assert best.px_per_thread in (1, 2) and best.stages in (1, 2)
     _check(items, _batch(ctx, items), refs, best.form)        # cfg None -> the tuned configuration
 
 
@@ -161,6 +162,46 @@ def test_batch_rejects_bad_input(ctx):
         ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(8, 0, 1, 0, 2))    # two pixels per thread: 16 rows
     with pytest.raises(hdr.HdrError):
         ctx.reconstruct_batch(hf[:1], hdr.hdr_batch_config(16, 0, 1, 1, 2))   # and form 0 only
+    for bad in (hdr.hdr_batch_config(16, 0, 1, 0, 1, 3), hdr.hdr_batch_config(16, 0, 1, 0, 1, -1),
+                hdr.hdr_batch_config(16, 0, 1, 1, 1, 2),                     # two staging buffers: form 0
+                hdr.hdr_batch_config(16, 0, 1, 0, 2, 2)):                    # and one pixel per thread
+        with pytest.raises(hdr.HdrError):
+            ctx.reconstruct_batch(hf[:1], bad)
+
+
+@pytest.mark.parametrize("stages", [1, 2])
+def test_staging_depth_spans_and_ranges(ctx, stages):
+    """Two staging buffers: each CTA takes four tiles strided over the launch's tile range and
+    copies the next tile while it computes the current one. Frames of 1 to 16 tiles (fewer tiles
+    than a CTA takes, ragged last CTA), tile heights 16 and 8, and served steps of 7 tiles (tile
+    sub-ranges of frames): every result bit-identical to the single-frame kernel."""
+    import dataclasses
+    from paper_1308_4908_gb300 import hdr
+    frames = synth.batching(n_frames=5, size_cap=64, seed=2010)
+    sizes = [(16, 16), (20, 9), (48, 17), (33, 40), (64, 64)]
+    # the frames' own output mappings, cropped to these sizes
+    frames = [dataclasses.replace(fr, params=dataclasses.replace(fr.params, out_w=w, out_h=h))
+              for fr, (w, h) in zip(frames, sizes)]
+    items = _prepare(ctx, frames, base_rig=0)
+    refs = _single(ctx, items)
+    for th in (16, 8):
+        _same(_batch(ctx, items, hdr.hdr_batch_config(th, 0, 1, 0, 1, stages)), refs)
+    srv = hdr.Server(ctx, pool_bytes=64 << 20, step_tiles=7, batch=hdr.hdr_batch_config(16, 0, 1, 0, 1, stages))
+    try:
+        bufs, tickets = [], []
+        for rig, fr, _, _, _ in items:
+            p = fr.params
+            out = np.full((3, p.out_h, p.out_w), -7.0, np.float32)
+            ch = np.zeros((3, p.out_h, p.out_w), np.uint8)
+            bufs.append((out, ch))
+            tickets.append(srv.submit(rig, p, [np.ascontiguousarray(s.raw) for s in fr.sensors], out, ch))
+        for t in tickets:
+            assert srv.poll(t, -1).status == 0
+    finally:
+        srv.close()
+    for (out, ch), (ro, rc) in zip(bufs, refs):
+        np.testing.assert_array_equal(ch, rc)
+        np.testing.assert_array_equal(out, ro)
 
 
 @pytest.mark.parametrize("form", [0, 1])
@@ -175,8 +216,8 @@ def test_batch_with_empty_and_one_pixel_frames(ctx, form):
     _check(items, _batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form)), refs, form)
 
 
-@pytest.mark.parametrize("form", [0, 1])
-def test_batch_with_translational_frames(ctx, form):
+@pytest.mark.parametrize("form,stages", [(0, 1), (0, 2), (1, 1)])
+def test_batch_with_translational_frames(ctx, form, stages):
     """Frames whose rigs are pure translations use tabulated weights in form 0 (and the searched
     window in the persistent form): each equals its single-frame result within the parity
     tolerance and is bit-identical to it in form 0."""
@@ -192,7 +233,7 @@ def test_batch_with_translational_frames(ctx, form):
                                                                         out_affine=synth.output_affine(w, h, w, h)))
     items = _prepare(ctx, frames, base_rig=60 - 3)
     refs = _single(ctx, items)
-    got = _batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form))
+    got = _batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form, 1, stages))
     if form == 0:
         _same(got, refs)
     else:
