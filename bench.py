@@ -1026,7 +1026,7 @@ def run_ours(args, world, rank, local, pg):
                          "algorithmic_gflop_per_launch": round(flops / 1e9, 3)},
             "e2e": ({"value": round(px * world / e2e_s / 1e6, 2), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3, 3),
-                     "api": "hdr_reconstruct_host (pinned host buffers; copies in, reconstruction and copies out pipelined over 4 row bands)"}
+                     "api": "hdr_reconstruct_host (pinned host buffers; copies in, reconstruction and copies out pipelined over 16 row bands on two streams)"}
                     if e2e_s else None),
             "gpu_launches": args.steps,
             "clocks": clk.summary(),

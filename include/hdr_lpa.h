@@ -147,10 +147,13 @@ hdr_status hdr_reconstruct_levels(hdr_ctx *ctx, int32_t rig_id, const hdr_params
 
 /* End-to-end variant with HOST buffers: copies raw_host[s] ([height][pitch_elems]) to
  * device staging owned by the context, reconstructs, copies the output back to out_host
- * (and choice to choice_host when non-NULL) and waits. Staging grows on demand. Outputs of 32
- * or more tile rows run in 4 row bands: the raw rows a band's windows reach are copied in while
- * the previous band is reconstructed, and each finished band is copied out while the next one
- * runs (copy streams owned by the context; pinned host buffers make the copies asynchronous). */
+ * (and choice to choice_host when non-NULL) and waits. Staging grows on demand. The output
+ * runs in row bands of at least 8 tile rows, at most 16: the raw rows a band's windows reach are
+ * copied in while the previous band is reconstructed, and each finished band is copied out
+ * while the next one runs (copy streams owned by the context; pinned host buffers make the
+ * copies asynchronous). Consecutive bands alternate between cuda_stream and a second stream of
+ * the context, so that one band's CTAs fill the SMs the previous band's last wave leaves idle;
+ * the work starts after earlier work on cuda_stream and cuda_stream is ordered after all of it. */
 hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
                                 const uint16_t *const *raw_host, void *out_host, uint8_t *choice_host,
                                 void *cuda_stream);

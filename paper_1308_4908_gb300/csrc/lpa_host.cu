@@ -135,6 +135,18 @@ struct TableHold {
   ~TableHold() { c.hold--; }
 };
 
+#ifndef LPA_FRAME_STAGES
+#define LPA_FRAME_STAGES 1   // staging buffers per CTA of single-frame launches
+#endif
+#ifndef LPA_HOST_BANDS
+#define LPA_HOST_BANDS 16    // most row bands of hdr_reconstruct_host (each of at least 8 tile rows)
+#endif
+#ifndef LPA_HOST_BAND_STREAMS
+#define LPA_HOST_BAND_STREAMS 2  // compute streams the row bands alternate on
+#endif
+constexpr int kMaxBands = 16;
+static_assert(LPA_HOST_BANDS >= 1 && LPA_HOST_BANDS <= kMaxBands, "row bands of the host-buffer path");
+
 struct hdr_ctx {
   int device = 0;
   PlanCache tabs;
@@ -151,7 +163,8 @@ struct hdr_ctx {
   size_t choice_cap = 0;
   // copy streams and band events of the host-buffer entry point (created on first use)
   cudaStream_t h2d = nullptr, d2h = nullptr;
-  cudaEvent_t ev_in[8] = {}, ev_done[8] = {};
+  cudaEvent_t ev_in[kMaxBands] = {}, ev_done[kMaxBands] = {};
+  cudaStream_t band2 = nullptr;  // host-buffer path: the second stream the row bands alternate on
   // gradient and steering-matrix planes of the adaptive reconstruction
   void *calpa = nullptr;
   size_t calpa_cap = 0;
@@ -438,9 +451,6 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
 
 #ifndef LPA_FRAME_TILE_H
 #define LPA_FRAME_TILE_H 16  // tile height of single-frame launches
-#endif
-#ifndef LPA_FRAME_STAGES
-#define LPA_FRAME_STAGES 1   // staging buffers per CTA of single-frame launches
 #endif
 
 // Fill the launch descriptor for one frame. raw: device pointers per sensor.
@@ -733,7 +743,8 @@ void hdr_destroy(hdr_ctx *ctx) {
   for (auto &t : ctx->tabs.retired) cudaFree(t.first);
   if (ctx->h2d) cudaStreamDestroy(ctx->h2d);
   if (ctx->d2h) cudaStreamDestroy(ctx->d2h);
-  for (int b = 0; b < 8; b++) {
+  if (ctx->band2) cudaStreamDestroy(ctx->band2);
+  for (int b = 0; b < kMaxBands; b++) {
     if (ctx->ev_in[b]) cudaEventDestroy(ctx->ev_in[b]);
     if (ctx->ev_done[b]) cudaEventDestroy(ctx->ev_done[b]);
   }
@@ -902,20 +913,26 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
   if (!ctx->h2d) {
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking));
-    for (int b = 0; b < 8; b++) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->band2, cudaStreamNonBlocking));
+    for (int b = 0; b < kMaxBands; b++) {
       CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_in[b], cudaEventDisableTiming));
       CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_done[b], cudaEventDisableTiming));
     }
   }
   // Bands of tile rows: the raw rows a band's windows can reach are copied in (on the copy
   // stream) while the previous band is reconstructed, and a finished band's output rows are
-  // copied out while the next one is reconstructed.
+  // copied out while the next one is reconstructed. Consecutive bands run on two streams
+  // (`stream` and a second one; a band waits only for its own input rows), so that a band's first
+  // CTAs fill the SMs its predecessor's last wave leaves idle.
   const int rows = L.tiles_y;
-  const int nb = rows >= 32 ? 4 : 1;
+  const int nb = std::max(1, std::min(LPA_HOST_BANDS, rows / 8));
+  const int nstreams = LPA_HOST_BAND_STREAMS;
   size_t have[HDR_MAX_SENSORS] = {};
   CUDA_TRY(cudaEventRecord(ctx->ev_done[0], stream));  // the copies start after earlier work on `stream`
   CUDA_TRY(cudaStreamWaitEvent(ctx->h2d, ctx->ev_done[0], 0));
+  if (nstreams > 1 && nb > 1) CUDA_TRY(cudaStreamWaitEvent(ctx->band2, ctx->ev_done[0], 0));
   for (int b = 0; b < nb; b++) {
+    cudaStream_t sb = (nstreams > 1 && (b & 1)) ? ctx->band2 : stream;
     const int r0 = rows * b / nb, r1 = rows * (b + 1) / nb;
     const int v0 = r0 * L.tile_h, v1 = std::min(r1 * L.tile_h, params->out_h);
     for (int s = 0; s < rig.n; s++) {
@@ -941,14 +958,14 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
       }
     }
     CUDA_TRY(cudaEventRecord(ctx->ev_in[b], ctx->h2d));
-    CUDA_TRY(cudaStreamWaitEvent(stream, ctx->ev_in[b], 0));
+    CUDA_TRY(cudaStreamWaitEvent(sb, ctx->ev_in[b], 0));
     L.tile0 = r0 * L.tiles_x;
     L.tile_count = (r1 - r0) * L.tiles_x;
     if (L.tile_count > 0) {
-      st = launch(L, params->accum, false, stream);
+      st = launch(L, params->accum, false, sb);
       if (st) return st;
     }
-    CUDA_TRY(cudaEventRecord(ctx->ev_done[b], stream));
+    CUDA_TRY(cudaEventRecord(ctx->ev_done[b], sb));
     CUDA_TRY(cudaStreamWaitEvent(ctx->d2h, ctx->ev_done[b], 0));
     if (v1 > v0) {
       const size_t off = (size_t)v0 * params->out_w, n = (size_t)(v1 - v0) * params->out_w;
@@ -962,6 +979,9 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
       }
     }
   }
+  // `stream` is ordered after every band and copy (the call returns when they are done)
+  CUDA_TRY(cudaEventRecord(ctx->ev_in[0], ctx->d2h));
+  CUDA_TRY(cudaStreamWaitEvent(stream, ctx->ev_in[0], 0));
   CUDA_TRY(cudaStreamSynchronize(ctx->d2h));
   CUDA_TRY(cudaStreamSynchronize(stream));
   return HDR_OK;
