@@ -357,8 +357,8 @@ def run_serving(ctx, frames, dev, seconds: float, step_tiles: int):
     offered = sum(px[m] for _, m in sched) / seconds / 1e6
     cfg = dict(max_frames=48, pool_bytes=6 << 30, step_tiles=step_tiles)
 
-    def serve(sched, clock=None):
-        srv = hdr.Server(ctx, **cfg)
+    def serve(sched, clock=None, order=0):
+        srv = hdr.Server(ctx, order=order, **cfg)
         slot = [[None] * R for _ in streams]
         cnt = [0] * len(streams)
         t0 = time.perf_counter()
@@ -389,6 +389,7 @@ def run_serving(ctx, frames, dev, seconds: float, step_tiles: int):
         ctx.reconstruct_host(8 + m, hp, raws, outs[0])
     with ClockSampler(dev.index or 0) as clk:
         st, wall = serve(sched)
+    st1, _ = serve(sched, order=1)
     burst = [(0.0, m) for m in range(len(streams)) for _ in range(4)]
     cap, cap_wall = serve(burst)
 
@@ -415,7 +416,9 @@ def run_serving(ctx, frames, dev, seconds: float, step_tiles: int):
                    "mean_queue_ms": round(st.mean_queue_ms, 3), "steps": int(st.steps), "completed": int(st.completed),
                    "gpu_step_ms_total": round(st.gpu_step_ms, 1), "gpu_gap_ms_total": round(st.gpu_gap_ms, 1),
                    "host_step_ms": {"mean": round(st.host_step_ms_mean, 3), "max": round(st.host_step_ms_max, 3)},
-                   "config": cfg},
+                   "config": dict(cfg, order="admission (first come, first served)")},
+        "served_least_remaining_work_first": {"p50_ms": round(st1.p50_ms, 2), "p99_ms": round(st1.p99_ms, 2),
+                                              "max_ms": round(st1.max_ms, 2), "config": dict(cfg, order=1)},
         "plain_per_frame": {"mpx_s": round(sum(px[m] for _, m in sched) / pwall / 1e6, 1),
                             "p50_ms": round(_pct(lat, 50), 2), "p99_ms": round(_pct(lat, 99), 2),
                             "max_ms": round(max(lat), 2), "api": "hdr_reconstruct_host, one frame at a time"},

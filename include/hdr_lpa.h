@@ -230,15 +230,17 @@ hdr_status hdr_tune_batch(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frame
 
 /* ---------------------------------------------------------------- serving
  * A request loop over one context. The paper overlaps the transfer of one frame with the
- * reconstruction of the previous one on two streams (Section 7); this loop generalises that to
+ * reconstruction of the previous one on two streams (Section 8); this loop generalises that to
  * many concurrent video streams. Frames of any size, rig and order are submitted from any
  * thread. A scheduler thread admits them in arrival order while a slot and room in the server's
  * device-memory pool are free, copies their raw frames into the pool on a copy stream, and
  * repeatedly launches one batched step over the pending tiles of the admitted frames, oldest
  * frame first, at most step_tiles per step, with up to three steps queued on the device: frames that
- * arrive while a step runs join a later one (continuous batching at tile granularity). A frame
- * whose tiles are all done is copied back to its host buffers on a second copy stream and its
- * memory returns to the pool. Each pixel is computed as hdr_reconstruct (an adaptive request: as
+ * arrive while a step runs join a later one (continuous batching at tile granularity; with
+ * hdr_server_config.order 1 the frames with the least remaining work go first). When a step
+ * completes, the output rows of its frames whose tiles are all done are copied back to the host
+ * buffers on a second copy stream; a frame whose last rows have landed completes and its memory
+ * returns to the pool. Each pixel is computed as hdr_reconstruct (an adaptive request: as
  * hdr_reconstruct_adaptive) computes it, whatever else shares the step; an adaptive request runs
  * its gradient and steering-matrix passes in the step that takes its first tiles, into scratch in
  * its pool block (20 bytes per output pixel), and needs the default tile height (16). The server uses its context exclusively until hdr_server_destroy (no
@@ -251,6 +253,10 @@ typedef struct {
   uint64_t pool_bytes;          /* device pool for raw frames, outputs and level maps            */
   int32_t step_tiles;           /* tile budget of one step; 0 = every pending tile               */
   hdr_batch_config batch;       /* launch configuration of the steps (tile_h 0 = default)        */
+  int32_t order;                /* tiles of a step: 0 = frames in admission order (first come,
+                                   first served: the lowest worst-case latency at equal relative
+                                   deadlines); 1 = the least remaining work first (tiles x sensors:
+                                   a lower median, a longer tail for the largest frames)          */
 } hdr_server_config;
 
 typedef struct {

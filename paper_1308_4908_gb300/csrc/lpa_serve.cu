@@ -16,6 +16,10 @@
 #include "hdr_lpa.h"
 #include "lpa_internal.h"
 
+#ifndef LPA_SERVE_INFLIGHT
+#define LPA_SERVE_INFLIGHT 3  // batched steps queued on the device at most
+#endif
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -86,6 +90,8 @@ struct Job {
   float *scratch_dev = nullptr;     // adaptive requests: gradients and steering matrices
   size_t scratch_bytes = 0;
   int tiles = 0, next_tile = 0, steps = 0;
+  int tiles_x = 0, tile_h = 16;     // tile columns and rows per tile row of the frame's output
+  int rows_out = 0;                 // output rows whose copy back has been issued
   int inflight = 0;                 // launched steps holding tiles of this frame, not yet complete
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   hdr_status status = HDR_OK;       // final status (State::Done)
@@ -97,6 +103,7 @@ struct Step {
   cudaEvent_t ev = nullptr;        // recorded after the step's launch (its completion)
   cudaEvent_t ev_begin = nullptr;  // recorded before it (timing: the step's start on the device)
   std::vector<uint64_t> members;
+  std::vector<int> ends;           // per member: the end of its tile range in this step
 };
 
 }  // namespace
@@ -160,6 +167,9 @@ struct hdr_server {
 
 
   void finish(Job &j, hdr_status st) {
+    // a failed frame may have copies of its finished rows in flight: they land before its pool
+    // memory is reused and before the caller learns of the failure (the host buffer stays theirs)
+    if (st != HDR_OK && j.rows_out > 0) cudaStreamSynchronize(d2h);
     j.status = st;
     if (st != HDR_OK && j.message.empty()) j.message = hdr_last_error();
     j.state = State::Done;
@@ -254,7 +264,7 @@ struct hdr_server {
   // Up to kMaxInflight steps may be queued, so that the device never waits for the host to build
   // the next one. The lock is released while the step is planned and launched (submit and poll
   // stay responsive); only this thread changes the jobs a step holds.
-  static constexpr size_t kMaxInflight = 3;
+  static constexpr size_t kMaxInflight = LPA_SERVE_INFLIGHT;
   bool launch_step(std::unique_lock<std::mutex> &lock) {
     if (steps.size() >= kMaxInflight) return false;
     std::vector<hdr_frame> frames;
@@ -262,7 +272,12 @@ struct hdr_server {
     std::vector<float *> scratch;
     Step st;
     long budget = cfg.step_tiles > 0 ? cfg.step_tiles : (1L << 40);
-    for (uint64_t t : active) {
+    std::vector<uint64_t> order(active.begin(), active.end());
+    if (cfg.order == 1) {  // the least remaining work first (tiles x sensors), admission order on ties
+      auto left = [&](uint64_t t) { return (long)(jobs[t].tiles - jobs[t].next_tile) * jobs[t].n_sensors; };
+      std::stable_sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) { return left(a) < left(b); });
+    }
+    for (uint64_t t : order) {
       Job &j = jobs[t];
       if (j.state != State::Ready || j.error || j.next_tile >= j.tiles || budget <= 0) continue;
       const int take = (int)std::min<long>(budget, j.tiles - j.next_tile);
@@ -304,6 +319,7 @@ struct hdr_server {
     }
     for (size_t k = 0; k < st.members.size(); k++) {
       Job &j = jobs[st.members[k]];
+      st.ends.push_back(ranges[k].y);
       j.next_tile = ranges[k].y;
       j.steps++;
       j.inflight++;
@@ -334,24 +350,39 @@ struct hdr_server {
         for (const Step &q : steps)
           for (uint64_t t : q.members) fail_job(jobs[t], dev);
       }
-      for (uint64_t t : st.members) {
-        Job &j = jobs[t];
+      for (size_t k = 0; k < st.members.size(); k++) {
+        Job &j = jobs[st.members[k]];
         if (j.state == State::Done) continue;
         if (j.error) {
           if (j.inflight == 0) finish(j, j.error);
           continue;
         }
-        if (j.next_tile < j.tiles || j.inflight > 0) continue;
-        j.ev_out = event();
-        cudaError_t e = j.ev_out ? cudaStreamWaitEvent(d2h, st.ev, 0) : cudaErrorMemoryAllocation;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(j.req.out_host, j.out_dev, j.out_bytes, cudaMemcpyDeviceToHost, d2h);
-        if (e == cudaSuccess && j.choice_dev)
-          e = cudaMemcpyAsync(j.req.choice_host, j.choice_dev, j.choice_bytes, cudaMemcpyDeviceToHost, d2h);
-        if (e == cudaSuccess) e = cudaEventRecord(j.ev_out, d2h);
+        // the output rows whose tiles are all done (steps complete in launch order, and each
+        // frame's tiles go out in order) are copied back now, behind this step
+        const bool last = j.next_tile >= j.tiles && j.inflight == 0 && st.ends[k] >= j.tiles;
+        const int rows = last ? j.req.params.out_h : std::min(j.req.params.out_h, st.ends[k] / j.tiles_x * j.tile_h);
+        cudaError_t e = cudaSuccess;
+        if (rows > j.rows_out) {
+          e = cudaStreamWaitEvent(d2h, st.ev, 0);
+          const size_t w = (size_t)j.req.params.out_w, plane = w * j.req.params.out_h;
+          const size_t es = j.req.params.out_dtype ? 2 : 4, off = (size_t)j.rows_out * w, n = (size_t)(rows - j.rows_out) * w;
+          for (int c = 0; c < 3 && e == cudaSuccess; c++) {
+            e = cudaMemcpyAsync(static_cast<char *>(j.req.out_host) + (c * plane + off) * es,
+                                static_cast<char *>(j.out_dev) + (c * plane + off) * es, n * es, cudaMemcpyDeviceToHost, d2h);
+            if (e == cudaSuccess && j.choice_dev)
+              e = cudaMemcpyAsync(j.req.choice_host + c * plane + off, j.choice_dev + c * plane + off, n,
+                                  cudaMemcpyDeviceToHost, d2h);
+          }
+          if (e == cudaSuccess) j.rows_out = rows;
+        }
+        if (e == cudaSuccess && last) {
+          j.ev_out = event();
+          e = j.ev_out ? cudaEventRecord(j.ev_out, d2h) : cudaErrorMemoryAllocation;
+        }
         if (e != cudaSuccess) {
           lpa_fail(HDR_E_CUDA, cudaGetErrorString(e));
           fail_job(j, HDR_E_CUDA);
-        } else {
+        } else if (last) {
           j.state = State::CopyOut;
         }
       }
@@ -397,6 +428,7 @@ hdr_status hdr_server_create(hdr_ctx *ctx, const hdr_server_config *cfg, hdr_ser
   if (cfg->max_frames < 1) return lpa_fail(HDR_E_INVALID, "max_frames must be >= 1");
   if (cfg->pool_bytes < 4096) return lpa_fail(HDR_E_INVALID, "pool_bytes too small");
   if (cfg->step_tiles < 0) return lpa_fail(HDR_E_INVALID, "step_tiles must be >= 0");
+  if (cfg->order != 0 && cfg->order != 1) return lpa_fail(HDR_E_INVALID, "order must be 0 or 1");
   if (cfg->batch.tile_h != 0 && cfg->batch.tile_h != 8 && cfg->batch.tile_h != 16)
     return lpa_fail(HDR_E_INVALID, "batch.tile_h must be 0, 8 or 16");
   if (cfg->batch.ctas_per_sm < 0 || cfg->batch.ctas_per_sm > 8)
@@ -470,7 +502,9 @@ hdr_status hdr_submit(hdr_server *srv, const hdr_request *req, uint64_t *ticket)
   j.bytes = std::max<size_t>(bytes, 256);
   if (j.bytes > srv->cfg.pool_bytes) return lpa_fail(HDR_E_UNSUPPORTED, "the frame needs more memory than the pool holds");
   const int th = srv->cfg.batch.tile_h;
-  j.tiles = ((req->params.out_w + 15) / 16) * ((req->params.out_h + th - 1) / th);
+  j.tiles_x = (req->params.out_w + 15) / 16;
+  j.tile_h = th;
+  j.tiles = j.tiles_x * ((req->params.out_h + th - 1) / th);
   {
     std::lock_guard<std::mutex> lock(srv->mu);
     if (srv->stop) return lpa_fail(HDR_E_BUSY, "the server is stopping");

@@ -62,7 +62,7 @@ class hdr_batch_config(ctypes.Structure):
 
 class hdr_server_config(ctypes.Structure):
     _fields_ = [("max_frames", ctypes.c_int32), ("pool_bytes", ctypes.c_uint64), ("step_tiles", ctypes.c_int32),
-                ("batch", hdr_batch_config)]
+                ("batch", hdr_batch_config), ("order", ctypes.c_int32)]
 
 
 class hdr_request(ctypes.Structure):
@@ -580,10 +580,11 @@ class Server:
     alive here until their result has been polled."""
 
     def __init__(self, ctx: Context, max_frames: int = 16, pool_bytes: int = 4 << 30, step_tiles: int = 0,
-                 batch: Optional[hdr_batch_config] = None):
+                 batch: Optional[hdr_batch_config] = None, order: int = 0):
         cfg = hdr_server_config()
         cfg.max_frames, cfg.pool_bytes, cfg.step_tiles = int(max_frames), int(pool_bytes), int(step_tiles)
         cfg.batch = batch if batch is not None else hdr_batch_config(0, 0, 1, 0)
+        cfg.order = int(order)
         self.ctx = ctx
         self.handle = hdr_server_create(ctx.handle, cfg)
         self._held = {}

@@ -88,6 +88,19 @@ def test_alone_and_in_the_mix_are_identical(ctx, streams):
         np.testing.assert_array_equal(ch, ref[1])
 
 
+@pytest.mark.parametrize("step_tiles", [96, 0])
+def test_least_remaining_work_order(ctx, streams, step_tiles):
+    """order 1 (the least remaining work first) changes which tiles share a step, not what a pixel
+    computes: every frame of a mix equals its plain reconstruction."""
+    items = [(m, streams[m][k]) for k in range(2) for m in streams]
+    mixed, stats = _serve(ctx, items, step_tiles=step_tiles, order=1)
+    for (rig, fr), (out, ch, r) in zip(items, mixed):
+        assert r.status == 0
+        ref = _plain(ctx, rig, fr)
+        np.testing.assert_array_equal(out, ref[0])
+        np.testing.assert_array_equal(ch, ref[1])
+
+
 def test_served_frame_against_oracle(ctx, streams):
     fr = streams[7][0]                     # the upsampled stream
     (out, ch, _), = _serve(ctx, [(7, fr)])[0]
@@ -139,6 +152,10 @@ def test_poll_and_rejections(ctx, streams):
             srv.submit(6, bad, raws, out, ch)
     finally:
         srv.close()
+    for order in (-1, 2):
+        with pytest.raises(hdr.HdrError) as e:
+            hdr.Server(ctx, pool_bytes=64 << 20, order=order)
+        assert e.value.status == hdr.HDR_E_INVALID
     small = hdr.Server(ctx, pool_bytes=1 << 16)
     try:
         with pytest.raises(hdr.HdrError) as e:
