@@ -112,7 +112,7 @@ struct PlanCache {
   // KB) and kept until the context is destroyed, at most max_tables of them: the next one evicts
   // them all (after the device has finished the work that may use them).
   std::map<uint64_t, void *> dev;
-  // the inputs a table is built from (sensor count, scales, window constants, each sensor's
+  // the inputs a table is built from (sensor count, scales, window constants, scales per pass, each sensor's
   // translation) -> the device table, so that a repeated configuration skips the host build
   std::map<std::vector<double>, void *> by_inputs;
   uint64_t epoch = 0;  // bumped at each eviction (plans holding evicted tables are stale)
