@@ -264,6 +264,30 @@ def paper_scale(seed: int = 1002, size: int = 2048, out_size: Optional[int] = No
                         f"paper-3x{size}x{size}-M2-ICI4")
 
 
+PAPER_CAMERA_SIZE = (2336, 1752)
+
+
+def paper_camera(seed: int = 1009, translational: bool = True, sigma: float = 0.7) -> Frame:
+    """The four-sensor camera of Section 8 as a synthetic rig: 4 x 2336x1752 RGGB 12-bit sensors
+    whose exposure scalings span 1 : 2^12 (ND 1, 1/16, 1/256, 1/4096), gain 0.27 DN/e- and read
+    noise 72 e- (Section 8), exposure time 2 / 0.27 (the raw levels of the other workloads, whose
+    sensors have 2 DN/e-); misaligned by translations of up to 3 px and, unless `translational`,
+    rotations of up to 0.3 degrees; order 0, one scale `sigma`, output 2336x1752 at 1x."""
+    w, h = PAPER_CAMERA_SIZE
+    r = _rng(seed, 0, 0 if translational else 1)
+    scene = make_scene(seed, w, h)
+    sensors = []
+    for s, nd in enumerate((1.0, 1 / 16, 1 / 256, 1 / 4096)):
+        tx, ty = r.uniform(-3.0, 3.0, 2)
+        rot = 0.0 if translational else r.uniform(-0.3, 0.3)
+        sen = Sensor(w, h, nd, affine_about_center(w, h, tx, ty, rot), gain=0.27, exposure=2.0 / 0.27,
+                     read_var=(72.0 * 0.27) ** 2)
+        sen.raw = simulate_raw(scene, sen, seed, s)
+        sensors.append(sen)
+    p = Params(order=0, sigmas=(sigma,), out_w=w, out_h=h)
+    return Frame(sensors, p, scene, f"paper-camera-4x{w}x{h}-M0-{'translational' if translational else 'rotated'}")
+
+
 def precision(seed: int = 1003, size: int = 2048, order: int = 0) -> Frame:
     """Tiny recipe (2 sensors, ND 1 and 1/8, U(-1,1) translation, sigma 0.7) at size^2 raw -> 2x upsampled output."""
     o = 2 * size

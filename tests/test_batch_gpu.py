@@ -216,11 +216,12 @@ def test_batch_with_empty_and_one_pixel_frames(ctx, form):
     _check(items, _batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form)), refs, form)
 
 
-@pytest.mark.parametrize("form,stages", [(0, 1), (0, 2), (1, 1)])
-def test_batch_with_translational_frames(ctx, form, stages):
-    """Frames whose rigs are pure translations use tabulated weights in form 0 (and the searched
-    window in the persistent form): each equals its single-frame result within the parity
-    tolerance and is bit-identical to it in form 0."""
+@pytest.mark.parametrize("form,stages,px", [(0, 1, 1), (0, 2, 1), (0, 1, 2), (1, 1, 1)])
+def test_batch_with_translational_frames(ctx, form, stages, px):
+    """Frames whose rigs are pure translations use tabulated weights in form 0 (one or two staging
+    buffers, one or two pixels per thread) and the searched window in the persistent form: each
+    equals its single-frame result within the parity tolerance and is bit-identical to it in
+    form 0."""
     import dataclasses
     from paper_1308_4908_gb300 import hdr
     frames = synth.batching(n_frames=3, size_cap=96, seed=2007)
@@ -233,7 +234,7 @@ def test_batch_with_translational_frames(ctx, form, stages):
                                                                         out_affine=synth.output_affine(w, h, w, h)))
     items = _prepare(ctx, frames, base_rig=60 - 3)
     refs = _single(ctx, items)
-    got = _batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form, 1, stages))
+    got = _batch(ctx, items, hdr.hdr_batch_config(16, 0, 1, form, px, stages))
     if form == 0:
         _same(got, refs)
     else:
