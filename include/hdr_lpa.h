@@ -133,7 +133,12 @@ hdr_status hdr_set_rig(hdr_ctx *ctx, int32_t rig_id, int32_t n_sensors, const hd
  *   choice_dev  optional device pointer [3][out_h][out_w] uint8: per channel the level
  *               used - 0..J-1 = order M at scale j, J+i = order M-1-i at the largest scale,
  *               255 = no sample (NaN output). NULL = not written.
- * Asynchronous: returns after queueing one kernel launch. */
+ * Outputs of at least 152 x 256 pixels (one wave of 16 x 16 tiles) are reconstructed in two
+ * launches: every raw sample is first converted once (Eq. 18, inverse of Eq. 20) into a buffer the
+ * context owns (grown on demand, which waits for the device; calls on any stream are ordered
+ * through it by an event), then the reconstruction copies converted footprints; smaller outputs
+ * convert each footprint inside one launch. The results are the same either way.
+ * Asynchronous: returns after queueing the launches. */
 hdr_status hdr_reconstruct(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,
                            const uint16_t *const *raw_dev, void *out_dev, uint8_t *choice_dev,
                            void *cuda_stream);

@@ -63,6 +63,10 @@ inline const void *lpa_kernel(int order, bool comp, bool diag, int mode, int til
                       : lpa_kernel_order2(comp, diag, mode, tile_h, px, stages);
 }
 
+// Conversion of rows R of every sensor of L into its planes (LpaSensorK::conv), for a plan with
+// conv = 1; lit: the printed noise weight (square root of the inverse variance).
+cudaError_t lpa_launch_convert(const LpaLaunch &L, const LpaRows &R, bool lit, cudaStream_t st);
+
 // Persistent launch of order M over its segment of a many-frame tile list (tile height 8 or 16).
 cudaError_t lpa_launch_batch_order0(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st);
 cudaError_t lpa_launch_batch_order1(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st);

@@ -138,6 +138,9 @@ struct TableHold {
 #ifndef LPA_FRAME_STAGES
 #define LPA_FRAME_STAGES 1   // staging buffers per CTA of single-frame launches
 #endif
+#ifndef LPA_FRAME_CONV
+#define LPA_FRAME_CONV 1     // single-frame calls convert the frame in one pass before the reconstruction
+#endif
 #ifndef LPA_HOST_BANDS
 #define LPA_HOST_BANDS 16    // most row bands of hdr_reconstruct_host (each of at least 8 tile rows)
 #endif
@@ -165,6 +168,11 @@ struct hdr_ctx {
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_in[kMaxBands] = {}, ev_done[kMaxBands] = {};
   cudaStream_t band2 = nullptr;  // host-buffer path: the second stream the row bands alternate on
+  // frames converted ahead of single-frame reconstructions: one buffer, and the event after its
+  // last use (a call on any stream waits for it before converting into the buffer again)
+  float2 *conv_buf = nullptr;
+  size_t conv_cap = 0;  // float2 elements
+  cudaEvent_t conv_ev = nullptr;
   // gradient and steering-matrix planes of the adaptive reconstruction
   void *calpa = nullptr;
   size_t calpa_cap = 0;
@@ -289,6 +297,16 @@ int floor_div2_parity(long long v) { return (int)(((v % 2) + 2) % 2); }
 // (bxe + ox + 2 qx, bye + oy + 2 qy), bxe = even part of u + floor(G2) - ox, at offsets
 // d = (2 qx - rx, 2 qy - ry) with rx = parity(u + floor(G2) - ox) + frac(G2): the same for every
 // pixel of one parity class. The window cells (|d| < k sigma), offsets and weights are listed once.
+// Layout of a frame converted ahead of the reconstruction: per sensor float2 [4][(h + 1) / 2][pitch],
+// the pitch (x >> 1 columns) even so that rows are 16-byte multiples, sensors 256-byte aligned.
+int conv_pitch_of(int w) { return ((w + 1) / 2 + 1) & ~1; }
+size_t conv_elems_of(int w, int h) { return ((size_t)4 * ((h + 1) / 2) * conv_pitch_of(w) + 31) / 32 * 32; }
+size_t conv_elems(const Rig &rig) {
+  size_t n = 0;
+  for (int s = 0; s < rig.n; s++) n += conv_elems_of(rig.s[s].d.width, rig.s[s].d.height);
+  return n;
+}
+
 hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p, bool f64_possible, LpaLaunch &L) {
   L.tab_hdr = nullptr;
   L.tab_cells = nullptr;
@@ -458,8 +476,10 @@ hdr_status build_tables(const PlanEnv &env, const Rig &rig, const hdr_params *p,
 // 1 / sqrt(smallest eigenvalue of C) times the isotropic radius).
 // stages: 2 = the two-buffer kernel (each CTA copies its next tile while computing the current one)
 // where it is built (plain sums, the searched or tabulated window), else 1.
+// conv: a buffer of conv_elems(rig) float2 to convert the frames into ahead of the launch (the
+// kernel then copies converted footprints and does no conversion), or nullptr.
 hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, const uint16_t *const *raw,
-                    LpaLaunch &L, int tile_h = 16, double reach = 1.0, int stages = 1) {
+                    LpaLaunch &L, int tile_h = 16, double reach = 1.0, int stages = 1, float2 *conv = nullptr) {
   memset(&L, 0, sizeof(L));
   L.n_sensors = rig.n;
   L.order = p->order;
@@ -481,6 +501,8 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
   L.status = env.status;
   const double rmax = reach * p->trunc_k * p->sigma[p->n_scales - 1] * std::fmax(1.0, p->green_ratio);
   uint32_t off = 0, tx = 0;
+  size_t conv_off = 0;
+  L.conv = conv ? 1 : 0;
   for (int s = 0; s < rig.n; s++) {
     const hdr_sensor_desc &d = rig.s[s].d;
     LpaSensorK &K = L.s[s];
@@ -526,6 +548,41 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
       return fail(HDR_E_UNSUPPORTED, "sensor %d staging box %dx%d exceeds 256 (window or output scale too large)", s, bw, bh);
     K.box_w = bw;
     K.box_h = bh;
+    K.raw = raw[s];
+    K.raw_pitch = d.pitch_elems;
+    if (conv) {
+      // the converted frame's colour-phase planes, copied straight into the staged planes
+      K.conv_pitch = conv_pitch_of(d.width);
+      K.conv_h = (d.height + 1) / 2;
+      K.conv = conv + conv_off;
+      conv_off += conv_elems_of(d.width, d.height);
+      off = (off + 127) / 128 * 128;
+      K.off_raw = K.off_planes = off;
+      off += (uint32_t)(bw * bh * 8);
+      tx += (uint32_t)(bw * bh * 8);
+      const std::array<uint64_t, 4> ckey = {reinterpret_cast<uint64_t>(K.conv),
+                                            ((uint64_t)K.conv_pitch << 32) | (uint32_t)K.conv_h, (1ull << 63) | 4u,
+                                            ((uint64_t)bw << 32) | (uint32_t)bh};
+      auto hit = env.tabs ? env.tabs->tmaps.find(ckey) : std::map<std::array<uint64_t, 4>, CUtensorMap>::iterator();
+      if (env.tabs && hit != env.tabs->tmaps.end()) {
+        K.tmap = hit->second;
+      } else {
+        cuuint64_t cdim[3] = {(cuuint64_t)K.conv_pitch, (cuuint64_t)K.conv_h, 4};
+        cuuint64_t cstride[2] = {(cuuint64_t)K.conv_pitch * 8, (cuuint64_t)K.conv_pitch * K.conv_h * 8};
+        cuuint32_t cbox[3] = {(cuuint32_t)(bw / 2), (cuuint32_t)(bh / 2), 4};
+        cuuint32_t cestr[3] = {1, 1, 1};
+        CUresult cr = env.encode(&K.tmap, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, K.conv, cdim, cstride, cbox, cestr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS)
+          return fail(HDR_E_CUDA, "cuTensorMapEncodeTiled failed for the converted planes of sensor %d (code %d)", s, (int)cr);
+        if (env.tabs) {
+          if (env.tabs->tmaps.size() >= 4096) env.tabs->tmaps.clear();
+          env.tabs->tmaps.emplace(ckey, K.tmap);
+        }
+      }
+      continue;
+    }
     off = (off + 127) / 128 * 128;
     K.off_raw = off;
     off += (uint32_t)(bw * bh * 2);
@@ -575,7 +632,7 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
   CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, env.device));
   L.stages = 1;
   for (int s = 0; s < rig.n; s++) L.s[s].off_raw2 = L.s[s].off_raw;
-  if (stages == 2 && lpa_stages2_built(L.mode, p->accum != 0)) {
+  if (stages == 2 && !conv && lpa_stages2_built(L.mode, p->accum != 0)) {
     // the second buffer's raw boxes, where they fit beside the rest (else one buffer)
     uint32_t off2 = off, at[LPA_MAX_SENSORS];
     for (int s = 0; s < rig.n; s++) {
@@ -596,16 +653,49 @@ hdr_status plan_env(const PlanEnv &env, const Rig &rig, const hdr_params *p, con
 }
 
 hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
-                double reach = 1.0, bool tabulate = true, int stages = 1) {
+                double reach = 1.0, bool tabulate = true, int stages = 1, float2 *conv = nullptr) {
   return plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, tabulate}, rig, p, raw, L,
-                  LPA_FRAME_TILE_H, reach, stages);
+                  LPA_FRAME_TILE_H, reach, stages, conv);
+}
+
+// The context's conversion buffer for this rig, or nullptr when the frame is converted in the
+// kernel: frames smaller than one wave of 16x16 tiles on the GPU's 152 SMs, whose cost is their
+// launch rather than the repeated conversion of overlapping footprints. Growing the buffer waits
+// for the work that used it.
+hdr_status conv_buffer(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, float2 **buf) {
+  *buf = nullptr;
+  if (!LPA_FRAME_CONV || (long long)p->out_w * p->out_h < 152LL * 256) return HDR_OK;
+  const size_t need = conv_elems(rig);
+  if (need > ctx->conv_cap) {
+    if (ctx->conv_ev) CUDA_TRY(cudaEventSynchronize(ctx->conv_ev));
+    cudaFree(ctx->conv_buf);
+    ctx->conv_buf = nullptr;
+    ctx->conv_cap = 0;
+    CUDA_TRY(cudaMalloc(&ctx->conv_buf, need * sizeof(float2)));
+    ctx->conv_cap = need;
+  }
+  if (!ctx->conv_ev) CUDA_TRY(cudaEventCreateWithFlags(&ctx->conv_ev, cudaEventDisableTiming));
+  *buf = ctx->conv_buf;
+  return HDR_OK;
+}
+
+// Convert rows [r0[s], r1[s]) of every sensor of L into its planes on `st`, after the last use of
+// the buffer (the first call of a reconstruction passes first = true).
+hdr_status convert_rows(hdr_ctx *ctx, const LpaLaunch &L, const LpaRows &rows, bool first, cudaStream_t st) {
+  if (first) CUDA_TRY(cudaStreamWaitEvent(st, ctx->conv_ev, 0));
+  LpaRows R = rows;
+  for (int s = 0; s < L.n_sensors; s++)  // an odd height's last plane row pairs with a row outside
+    if (R.r1[s] == L.s[s].height && (L.s[s].height & 1)) R.r1[s]++;
+  cudaError_t e = lpa_launch_convert(L, R, L.mode == LPA_LITERAL, st);
+  if (e != cudaSuccess) return fail(HDR_E_CUDA, "conversion launch failed: %s", cudaGetErrorString(e));
+  return HDR_OK;
 }
 
 // plan() of a single-frame call through the context's plan cache.
 hdr_status cached_plan(hdr_ctx *ctx, int32_t rig_id, const hdr_params *p, const uint16_t *const *raw, LpaLaunch &L,
-                       bool tabulate, int stages) {
+                       bool tabulate, int stages, float2 *conv) {
   const Rig &rig = ctx->rigs[rig_id];
-  std::vector<uint8_t> key(sizeof(int32_t) + 2 * sizeof(uint64_t) + sizeof(hdr_params) + 2 + rig.n * sizeof(void *));
+  std::vector<uint8_t> key(sizeof(int32_t) + 2 * sizeof(uint64_t) + sizeof(hdr_params) + 2 + (rig.n + 1) * sizeof(void *));
   uint8_t *k = key.data();
   memcpy(k, &rig_id, sizeof(int32_t));
   k += sizeof(int32_t);
@@ -617,13 +707,15 @@ hdr_status cached_plan(hdr_ctx *ctx, int32_t rig_id, const hdr_params *p, const 
   k += sizeof(hdr_params);
   *k++ = tabulate ? 1 : 0;
   *k++ = (uint8_t)stages;
+  memcpy(k, &conv, sizeof(void *));
+  k += sizeof(void *);
   memcpy(k, raw, rig.n * sizeof(void *));
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) {
     L = it->second;
     return HDR_OK;
   }
-  hdr_status st = plan(ctx, rig, p, raw, L, 1.0, tabulate, stages);
+  hdr_status st = plan(ctx, rig, p, raw, L, 1.0, tabulate, stages, conv);
   if (st) return st;
   if (ctx->plans.size() >= 256) ctx->plans.clear();
   ctx->plans.emplace(std::move(key), L);
@@ -661,13 +753,25 @@ hdr_status reconstruct_impl(hdr_ctx *ctx, int32_t rig_id, const hdr_params *para
   if (levels_dev && params->weight_mode != 0)
     return fail(HDR_E_UNSUPPORTED, "the level maps are computed with the inverse-variance weight (weight_mode 0)");
   LpaLaunch L;
+  float2 *conv = nullptr;
+  st = conv_buffer(ctx, ctx->rigs[rig_id], params, &conv);
+  if (st) return st;
   // the diagnostic (level maps) kernel searches every window
-  st = cached_plan(ctx, rig_id, params, raw_dev, L, levels_dev == nullptr, levels_dev ? 1 : LPA_FRAME_STAGES);
+  st = cached_plan(ctx, rig_id, params, raw_dev, L, levels_dev == nullptr, levels_dev ? 1 : LPA_FRAME_STAGES, conv);
   if (st) return st;
   L.out = out_dev;
   L.choice = choice_dev;
   L.levels = levels_dev;
-  return launch(L, params->accum, levels_dev != nullptr, (cudaStream_t)stream);
+  const cudaStream_t cs = (cudaStream_t)stream;
+  if (L.conv) {  // the whole frame converted once, then the reconstruction
+    LpaRows R{};
+    for (int s = 0; s < L.n_sensors; s++) R.r1[s] = L.s[s].height;
+    st = convert_rows(ctx, L, R, true, cs);
+    if (st) return st;
+  }
+  st = launch(L, params->accum, levels_dev != nullptr, cs);
+  if (st == HDR_OK && L.conv) CUDA_TRY(cudaEventRecord(ctx->conv_ev, cs));
+  return st;
 }
 
 }  // namespace
@@ -744,6 +848,8 @@ void hdr_destroy(hdr_ctx *ctx) {
   if (ctx->h2d) cudaStreamDestroy(ctx->h2d);
   if (ctx->d2h) cudaStreamDestroy(ctx->d2h);
   if (ctx->band2) cudaStreamDestroy(ctx->band2);
+  if (ctx->conv_ev) cudaEventDestroy(ctx->conv_ev);
+  cudaFree(ctx->conv_buf);
   for (int b = 0; b < kMaxBands; b++) {
     if (ctx->ev_in[b]) cudaEventDestroy(ctx->ev_in[b]);
     if (ctx->ev_done[b]) cudaEventDestroy(ctx->ev_done[b]);
@@ -905,7 +1011,10 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
   const size_t plane = (size_t)params->out_w * params->out_h;
   const size_t esize = params->out_dtype ? 2 : 4;
   LpaLaunch L;
-  st = cached_plan(ctx, rig_id, params, raw_dev, L, true, LPA_FRAME_STAGES);
+  float2 *conv = nullptr;
+  st = conv_buffer(ctx, rig, params, &conv);
+  if (st) return st;
+  st = cached_plan(ctx, rig_id, params, raw_dev, L, true, LPA_FRAME_STAGES, conv);
   if (st) return st;
   L.out = ctx->out_stage;
   L.choice = choice_host ? ctx->choice_stage : nullptr;
@@ -931,10 +1040,13 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
   CUDA_TRY(cudaEventRecord(ctx->ev_done[0], stream));  // the copies start after earlier work on `stream`
   CUDA_TRY(cudaStreamWaitEvent(ctx->h2d, ctx->ev_done[0], 0));
   if (nstreams > 1 && nb > 1) CUDA_TRY(cudaStreamWaitEvent(ctx->band2, ctx->ev_done[0], 0));
+  bool converted = false;
   for (int b = 0; b < nb; b++) {
     cudaStream_t sb = (nstreams > 1 && (b & 1)) ? ctx->band2 : stream;
     const int r0 = rows * b / nb, r1 = rows * (b + 1) / nb;
     const int v0 = r0 * L.tile_h, v1 = std::min(r1 * L.tile_h, params->out_h);
+    LpaRows R{};  // the rows this band copies in, converted behind their copy on the copy stream
+    bool fresh = false;
     for (int s = 0; s < rig.n; s++) {
       const LpaSensorK &Sk = L.s[s];
       const int H = rig.s[s].d.height;
@@ -954,8 +1066,16 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
         CUDA_TRY(cudaMemcpyAsync(ctx->raw_stage[s] + have[s] * rig.s[s].d.pitch_elems,
                                  raw_host[s] + have[s] * rig.s[s].d.pitch_elems, (need - have[s]) * row_bytes,
                                  cudaMemcpyHostToDevice, ctx->h2d));
+        R.r0[s] = (int)have[s];
+        R.r1[s] = (int)need;
+        fresh = true;
         have[s] = need;
       }
+    }
+    if (L.conv && fresh) {
+      st = convert_rows(ctx, L, R, !converted, ctx->h2d);
+      if (st) return st;
+      converted = true;
     }
     CUDA_TRY(cudaEventRecord(ctx->ev_in[b], ctx->h2d));
     CUDA_TRY(cudaStreamWaitEvent(sb, ctx->ev_in[b], 0));
@@ -982,6 +1102,7 @@ hdr_status hdr_reconstruct_host(hdr_ctx *ctx, int32_t rig_id, const hdr_params *
   // `stream` is ordered after every band and copy (the call returns when they are done)
   CUDA_TRY(cudaEventRecord(ctx->ev_in[0], ctx->d2h));
   CUDA_TRY(cudaStreamWaitEvent(stream, ctx->ev_in[0], 0));
+  if (converted) CUDA_TRY(cudaEventRecord(ctx->conv_ev, stream));
   CUDA_TRY(cudaStreamSynchronize(ctx->d2h));
   CUDA_TRY(cudaStreamSynchronize(stream));
   return HDR_OK;

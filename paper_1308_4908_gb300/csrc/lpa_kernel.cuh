@@ -442,6 +442,35 @@ struct Anchor {
 // Staged sample layout: (f, 1/s2) (1/s for the printed weight); 1/s2 = 0 excludes the sample.
 __device__ __forceinline__ float2 stage_pair(float f, float iv) { return make_float2(f, iv); }
 __device__ __forceinline__ bool sample_ok(float2 fv) { return fv.y > 0.f; }
+// The staged value of raw sample y at sensor pixel (X, Y), inside the frame: Eq. 18 and the inverse
+// of Eq. 20 (its square root for the printed weight K / s); (0, 0) when saturated. `scalar`: the
+// sensor has no per-pixel calibration frames.
+template <bool LIT>
+__device__ __forceinline__ float2 convert_sample(const LpaSensorK &Sk, bool scalar, int X, int Y, float y) {
+  float f = 0.f, iv = 0.f;
+  if (scalar) {
+    if (y < Sk.sat) {
+      const float e0 = y - Sk.black;
+      f = e0 * Sk.inv_gtn;
+      iv = __fdividef(Sk.gtn2, fmaf(Sk.gain, fmaxf(e0, 0.f), Sk.read_var));
+      if (LIT) iv = sqrtf(iv);
+    }
+  } else {
+    const long px = (long)Y * Sk.width + X;
+    const float b = Sk.bias ? Sk.bias[px] : Sk.black;
+    const float rv = Sk.rvar ? Sk.rvar[px] : Sk.read_var;
+    const float sat = Sk.satf ? (float)Sk.satf[px] : Sk.sat;
+    if (y < sat) {
+      const float a = Sk.prnu ? Sk.prnu[px] : 1.f;
+      const float e0 = y - b;
+      f = __fdividef(e0 * Sk.inv_gtn, a);
+      iv = __fdividef(Sk.gtn2 * a * a, fmaf(Sk.gain, fmaxf(e0, 0.f), rv));
+      if (LIT) iv = sqrtf(iv);
+    }
+  }
+  return stage_pair(f, iv);
+}
+
 // (w, w f) of a staged sample for window value K: w = K / s2
 __device__ __forceinline__ float2 weights(float K, float2 fv) {
   const float w = K * fv.y;
@@ -738,8 +767,12 @@ __device__ __forceinline__ void stage_issue(const LpaLaunch &L, const LpaLaunch 
   if (GLOBAL_MAPS)
     for (int s = 0; s < S; s++) tensormap_acquire(&maps->s[s].tmap);
   mbar_arrive_expect_tx(mbar, L.tx_bytes);
-  for (int s = 0; s < S; s++)
-    tma_load_2d(smem + (stage ? L.s[s].off_raw2 : L.s[s].off_raw), &maps->s[s].tmap, fp_x0[s], fp_y0[s], mbar);
+  for (int s = 0; s < S; s++) {
+    if (L.conv)  // the four colour-phase planes of the footprint, converted: [4][box_h / 2][box_w / 2]
+      tma_load_3d(smem + L.s[s].off_planes, &maps->s[s].tmap, fp_x0[s] >> 1, fp_y0[s] >> 1, 0, mbar);
+    else
+      tma_load_2d(smem + (stage ? L.s[s].off_raw2 : L.s[s].off_raw), &maps->s[s].tmap, fp_x0[s], fp_y0[s], mbar);
+  }
 }
 
 // STAGED: the footprint (fp_x0, fp_y0) and the copies of this tile into buffer `stage` were issued
@@ -786,47 +819,24 @@ __device__ __forceinline__ bool process_tile(const LpaLaunch &L, const LpaLaunch
   }
 
   // convert the staged raw values once per sample: Eq. 18 and the inverse of Eq. 20 (its square
-  // root for the printed weight K / s)
+  // root for the printed weight K / s); frames converted ahead of the launch arrive as such
   constexpr bool LIT = MODE == LPA_LITERAL;
-  for (int s = 0; s < S; s++) {
+  const int n_conv = L.conv ? 0 : S;
+  for (int s = 0; s < n_conv; s++) {
     const LpaSensorK &Sk = L.s[s];
     const uint16_t *raw = reinterpret_cast<const uint16_t *>(smem + (stage ? Sk.off_raw2 : Sk.off_raw));
     float2 *planes = reinterpret_cast<float2 *>(smem + Sk.off_planes);
     const int bw = Sk.box_w, n = bw * Sk.box_h, PW = bw >> 1, PP = (bw >> 1) * (Sk.box_h >> 1);
     const int x0 = fp_x0[s], y0 = fp_y0[s];
     const bool scalar = !Sk.bias && !Sk.rvar && !Sk.satf && !Sk.prnu;
-    const float inv_gtn = Sk.inv_gtn, gtn2 = Sk.gtn2, gain = Sk.gain, rv0 = Sk.read_var, b0 = Sk.black;
-    const float sat0 = Sk.sat;
     const int W = Sk.width, H = Sk.height;
     const int step_y = NT / bw, step_x = NT - step_y * bw;
     int lx = tid % bw, ly = tid / bw;
     for (int e = tid; e < n; e += NT) {
       const int X = x0 + lx, Y = y0 + ly;
-      float f = 0.f, iv = 0.f;
-      if (X >= 0 && X < W && Y >= 0 && Y < H) {
-        const float y = (float)raw[e];
-        if (scalar) {
-          if (y < sat0) {
-            const float e0 = y - b0;
-            f = e0 * inv_gtn;
-            iv = __fdividef(gtn2, fmaf(gain, fmaxf(e0, 0.f), rv0));
-            if (LIT) iv = sqrtf(iv);
-          }
-        } else {
-          const long px = (long)Y * W + X;
-          const float b = Sk.bias ? Sk.bias[px] : b0;
-          const float rv = Sk.rvar ? Sk.rvar[px] : rv0;
-          const float sat = Sk.satf ? (float)Sk.satf[px] : sat0;
-          if (y < sat) {
-            const float a = Sk.prnu ? Sk.prnu[px] : 1.f;
-            const float e0 = y - b;
-            f = __fdividef(e0 * inv_gtn, a);
-            iv = __fdividef(gtn2 * a * a, fmaf(gain, fmaxf(e0, 0.f), rv));
-            if (LIT) iv = sqrtf(iv);
-          }
-        }
-      }
-      planes[((lx & 1) + 2 * (ly & 1)) * PP + (ly >> 1) * PW + (lx >> 1)] = stage_pair(f, iv);
+      const float2 v = (X >= 0 && X < W && Y >= 0 && Y < H) ? convert_sample<LIT>(Sk, scalar, X, Y, (float)raw[e])
+                                                          : stage_pair(0.f, 0.f);
+      planes[((lx & 1) + 2 * (ly & 1)) * PP + (ly >> 1) * PW + (lx >> 1)] = v;
       lx += step_x;
       ly += step_y;
       if (lx >= bw) {
@@ -1085,6 +1095,36 @@ __global__ void __launch_bounds__(LPA_TILE *TH, (FrameOccupancy<ORDER, COMP, TH,
         return;
       }
     }
+  }
+}
+
+// Conversion ahead of the reconstruction (LpaLaunch::conv): rows [R.r0[s], R.r1[s]) of sensor s =
+// blockIdx.y into its colour-phase planes (r1 may be the height + 1 of an odd height: that row is
+// outside the frame and writes zeros), with the arithmetic the reconstruction kernels use when
+// they convert staged footprints themselves (convert_sample), so the staged values are the same.
+// Each thread takes the two samples of a row that share a phase column, so that a warp writes
+// contiguous float2 runs in both planes of the row's phase.
+template <bool LIT>
+__global__ void __launch_bounds__(256) lpa_convert(const __grid_constant__ LpaLaunch L, const LpaRows R) {
+  const int s = blockIdx.y;
+  const LpaSensorK &Sk = L.s[s];
+  const int r0 = R.r0[s], r1 = R.r1[s];
+  if (r1 <= r0) return;
+  const int CP = Sk.conv_pitch, W = Sk.width;
+  const bool scalar = !Sk.bias && !Sk.rvar && !Sk.satf && !Sk.prnu;
+  const long n = (long)(r1 - r0) * CP;
+  const size_t plane = (size_t)Sk.conv_h * CP;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int Y = r0 + (int)(i / CP), c = (int)(i % CP);
+    const int X = 2 * c;
+    const bool in_row = Y < Sk.height;  // the padding row of an odd height converts to zeros
+    const uint16_t *row = Sk.raw + (size_t)(in_row ? Y : 0) * Sk.raw_pitch;
+    const float2 v0 = in_row && X < W ? convert_sample<LIT>(Sk, scalar, X, Y, (float)row[X]) : stage_pair(0.f, 0.f);
+    const float2 v1 =
+        in_row && X + 1 < W ? convert_sample<LIT>(Sk, scalar, X + 1, Y, (float)row[X + 1]) : stage_pair(0.f, 0.f);
+    float2 *dst = Sk.conv + (size_t)(2 * (Y & 1)) * plane + (size_t)(Y >> 1) * CP + c;
+    dst[0] = v0;      // colour phase (0, Y & 1)
+    dst[plane] = v1;  // colour phase (1, Y & 1)
   }
 }
 

@@ -35,6 +35,12 @@ struct alignas(64) LpaSensorK {
   const float *prnu;
   const float *rvar;
   const uint16_t *satf;
+  // Frames converted ahead of the reconstruction (LpaLaunch::conv): the raw frame (pitch in
+  // elements) and its staged values in global memory, float2 [4][conv_h][conv_pitch]: colour phase
+  // ox + 2 oy, row y >> 1, column x >> 1, (0, 0) outside the frame; tmap then maps these planes.
+  const uint16_t *raw;
+  float2 *conv;
+  int raw_pitch, conv_pitch, conv_h;
 };
 
 struct LpaLaunch {
@@ -68,6 +74,10 @@ struct LpaLaunch {
   // LPA_STAGED_TILES tiles (tile0 + b + k grid) and copies the next tile's raw boxes into the
   // second buffer while it reconstructs the current one.
   int stages;
+  // 1: the staged values come converted from global memory (LpaSensorK::conv, one 3-D bulk copy
+  // of the four colour-phase planes per sensor) and the kernel does no conversion; 0: it copies
+  // the raw footprints and converts them itself.
+  int conv;
   // Tabulated window weights (NULL = the window is searched and evaluated per pixel), in passes of
   // tab_nsp scales as the kernel walks them (lpa_scale_passes). Entry
   // ((((s * 2 + pu) * 2 + pv) * 4 + phase) * n_pass + pass) of tab_hdr, two int4, describes the
@@ -140,6 +150,11 @@ __host__ __device__ constexpr int lpa_scales_per_walk(int order, bool comp, int 
 // j0 .. j0 + nj - 1 in slots lead .. nsp - 1 (lead = nsp - nj).
 __host__ __device__ constexpr int lpa_n_passes(int J, int nsp) { return (J + nsp - 1) / nsp; }
 __host__ __device__ constexpr int lpa_first_pass_scales(int J, int nsp) { return J - nsp * (lpa_n_passes(J, nsp) - 1); }
+
+// Rows [r0[s], r1[s]) of sensor s to convert (lpa_convert).
+struct LpaRows {
+  int r0[LPA_MAX_SENSORS], r1[LPA_MAX_SENSORS];
+};
 
 // The two-buffer single-frame kernel is built for plain sums with the searched or tabulated window.
 __host__ __device__ constexpr bool lpa_stages2_built(int mode, bool comp) {
