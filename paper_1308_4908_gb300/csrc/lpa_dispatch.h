@@ -66,6 +66,9 @@ inline const void *lpa_kernel(int order, bool comp, bool diag, int mode, int til
 // Conversion of rows R of every sensor of L into its planes (LpaSensorK::conv), for a plan with
 // conv = 1; lit: the printed noise weight (square root of the inverse variance).
 cudaError_t lpa_launch_convert(const LpaLaunch &L, const LpaRows &R, bool lit, cudaStream_t st);
+// The conversion kernel (parameters: LpaLaunch, LpaRows; 256 threads) and its grid, for graph nodes.
+const void *lpa_convert_kernel(bool lit);
+dim3 lpa_convert_grid(const LpaLaunch &L, const LpaRows &R);
 
 // Persistent launch of order M over its segment of a many-frame tile list (tile height 8 or 16).
 cudaError_t lpa_launch_batch_order0(const LpaBatch &B, bool comp, int tile_h, int grid, cudaStream_t st);

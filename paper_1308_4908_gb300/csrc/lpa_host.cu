@@ -297,6 +297,17 @@ int floor_div2_parity(long long v) { return (int)(((v % 2) + 2) % 2); }
 // (bxe + ox + 2 qx, bye + oy + 2 qy), bxe = even part of u + floor(G2) - ox, at offsets
 // d = (2 qx - rx, 2 qy - ry) with rx = parity(u + floor(G2) - ox) + frac(G2): the same for every
 // pixel of one parity class. The window cells (|d| < k sigma), offsets and weights are listed once.
+}  // namespace
+
+// Frames converted in a pass of their own before the reconstruction: at least one wave of 16x16
+// tiles on the GPU's 152 SMs (smaller frames cost their launches, not the repeated conversion of
+// overlapping footprints), outside the adaptive passes (their kernels convert footprints).
+bool lpa_conv_eligible(const hdr_params *p, bool adaptive) {
+  return LPA_FRAME_CONV && !adaptive && (long long)p->out_w * p->out_h >= 152LL * 256;
+}
+
+namespace {
+
 // Layout of a frame converted ahead of the reconstruction: per sensor float2 [4][(h + 1) / 2][pitch],
 // the pitch (x >> 1 columns) even so that rows are 16-byte multiples, sensors 256-byte aligned.
 int conv_pitch_of(int w) { return ((w + 1) / 2 + 1) & ~1; }
@@ -658,14 +669,9 @@ hdr_status plan(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, const uint16_
                   LPA_FRAME_TILE_H, reach, stages, conv);
 }
 
-// The context's conversion buffer for this rig, or nullptr when the frame is converted in the
-// kernel: frames smaller than one wave of 16x16 tiles on the GPU's 152 SMs, whose cost is their
-// launch rather than the repeated conversion of overlapping footprints. Growing the buffer waits
-// for the work that used it.
-hdr_status conv_buffer(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, float2 **buf) {
-  *buf = nullptr;
-  if (!LPA_FRAME_CONV || (long long)p->out_w * p->out_h < 152LL * 256) return HDR_OK;
-  const size_t need = conv_elems(rig);
+// The context's conversion buffer, at least `need` float2; growing it waits for the work that
+// used it.
+hdr_status conv_capacity(hdr_ctx *ctx, size_t need) {
   if (need > ctx->conv_cap) {
     if (ctx->conv_ev) CUDA_TRY(cudaEventSynchronize(ctx->conv_ev));
     cudaFree(ctx->conv_buf);
@@ -675,18 +681,38 @@ hdr_status conv_buffer(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, float2
     ctx->conv_cap = need;
   }
   if (!ctx->conv_ev) CUDA_TRY(cudaEventCreateWithFlags(&ctx->conv_ev, cudaEventDisableTiming));
+  return HDR_OK;
+}
+
+// The conversion buffer of a single-frame call for this rig, or nullptr when the frame is
+// converted in the kernel (lpa_conv_eligible).
+hdr_status conv_buffer(hdr_ctx *ctx, const Rig &rig, const hdr_params *p, float2 **buf) {
+  *buf = nullptr;
+  if (!lpa_conv_eligible(p, false)) return HDR_OK;
+  hdr_status st = conv_capacity(ctx, conv_elems(rig));
+  if (st) return st;
   *buf = ctx->conv_buf;
   return HDR_OK;
 }
 
 // Convert rows [r0[s], r1[s]) of every sensor of L into its planes on `st`, after the last use of
 // the buffer (the first call of a reconstruction passes first = true).
+// Rows to convert, with the row past an odd height (its last plane row pairs with a row outside
+// the frame, which converts to zeros) when the range reaches the height.
+LpaRows rows_with_padding(const LpaLaunch &L, LpaRows R) {
+  for (int s = 0; s < L.n_sensors; s++)
+    if (R.r1[s] == L.s[s].height && (L.s[s].height & 1)) R.r1[s]++;
+  return R;
+}
+LpaRows all_rows(const LpaLaunch &L) {
+  LpaRows R{};
+  for (int s = 0; s < L.n_sensors; s++) R.r1[s] = L.s[s].height;
+  return rows_with_padding(L, R);
+}
+
 hdr_status convert_rows(hdr_ctx *ctx, const LpaLaunch &L, const LpaRows &rows, bool first, cudaStream_t st) {
   if (first) CUDA_TRY(cudaStreamWaitEvent(st, ctx->conv_ev, 0));
-  LpaRows R = rows;
-  for (int s = 0; s < L.n_sensors; s++)  // an odd height's last plane row pairs with a row outside
-    if (R.r1[s] == L.s[s].height && (L.s[s].height & 1)) R.r1[s]++;
-  cudaError_t e = lpa_launch_convert(L, R, L.mode == LPA_LITERAL, st);
+  cudaError_t e = lpa_launch_convert(L, rows_with_padding(L, rows), L.mode == LPA_LITERAL, st);
   if (e != cudaSuccess) return fail(HDR_E_CUDA, "conversion launch failed: %s", cudaGetErrorString(e));
   return HDR_OK;
 }
@@ -764,9 +790,7 @@ hdr_status reconstruct_impl(hdr_ctx *ctx, int32_t rig_id, const hdr_params *para
   L.levels = levels_dev;
   const cudaStream_t cs = (cudaStream_t)stream;
   if (L.conv) {  // the whole frame converted once, then the reconstruction
-    LpaRows R{};
-    for (int s = 0; s < L.n_sensors; s++) R.r1[s] = L.s[s].height;
-    st = convert_rows(ctx, L, R, true, cs);
+    st = convert_rows(ctx, L, all_rows(L), true, cs);
     if (st) return st;
   }
   st = launch(L, params->accum, levels_dev != nullptr, cs);
@@ -1298,11 +1322,36 @@ hdr_status batch_plan(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *
 // all of them) as independent kernel nodes of one graph, recorded once per shape; a replay only
 // updates the nodes' parameters.
 hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const int2 *ranges,
-                            const hdr_batch_config &cfg, cudaStream_t stream, float *const *scratch) {
+                            const hdr_batch_config &cfg, cudaStream_t stream, float *const *scratch,
+                            float2 *const *conv_in, bool conv_done) {
   BatchState &B = ctx->batch;
   TableHold hold(ctx->tabs);  // the plans of every frame stay valid until the launch
   std::vector<LpaLaunch> plans(n);
   std::vector<int> grid(n, 0);
+  // frames converted ahead (lpa_conv_eligible; not with two staging buffers) into the caller's
+  // buffers, else into the context's buffer, one slice per frame
+  std::vector<float2 *> cv(n, nullptr);
+  bool ctx_conv = false;
+  if (cfg.stages != 2) {
+    if (conv_in) {
+      for (int f = 0; f < n; f++) cv[f] = conv_in[f];
+    } else {
+      size_t total = 0;
+      for (int f = 0; f < n; f++)
+        if (lpa_conv_eligible(frames[f].params, frames[f].calpa != nullptr)) total += conv_elems(ctx->rigs[frames[f].rig_id]);
+      if (total) {
+        hdr_status st = conv_capacity(ctx, total);
+        if (st) return st;
+        float2 *p = ctx->conv_buf;
+        for (int f = 0; f < n; f++)
+          if (lpa_conv_eligible(frames[f].params, frames[f].calpa != nullptr)) {
+            cv[f] = p;
+            p += conv_elems(ctx->rigs[frames[f].rig_id]);
+          }
+        ctx_conv = true;
+      }
+    }
+  }
   // adaptive frames: gradients and steering matrices (5 floats per output pixel) in the caller's
   // scratch, else in one context buffer shared by the batch
   std::vector<float *> aux(n, nullptr);
@@ -1343,7 +1392,8 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
     const int px = (cfg.px_per_thread == 2 && !F.calpa) ? 2 : 1;
     hdr_status st = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, !F.calpa}, ctx->rigs[F.rig_id],
                              pp, F.raw_dev, plans[f], F.calpa ? 16 : cfg.tile_h,
-                             F.calpa ? lpa_calpa_reach(F.calpa) : 1.0, (F.calpa || px != 1) ? 1 : cfg.stages);
+                             F.calpa ? lpa_calpa_reach(F.calpa) : 1.0, (F.calpa || px != 1) ? 1 : cfg.stages,
+                             F.calpa ? nullptr : cv[f]);
     if (st) return fail(st, "frame %d: %s", f, g_err.c_str());
     if (F.calpa) {
       plans[f].mode = lpa_mode_f32(plans[f].mode) ? LPA_STEERED_F32 : LPA_STEERED;
@@ -1370,30 +1420,53 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
   }
   if (order.empty()) return HDR_OK;
   const bool comp = frames[0].params->accum != 0;
+  // graph nodes: each frame's reconstruction grid, behind its conversion where the frame is
+  // converted ahead and this launch takes its first tile
   std::vector<std::array<int64_t, 5>> key;
-  std::vector<cudaKernelNodeParams> kp(order.size());
-  std::vector<void *> args(order.size());
+  std::vector<cudaKernelNodeParams> kp;
+  std::vector<int> dep;
+  std::vector<LpaRows> rows(n);
+  std::vector<std::array<void *, 2>> args;
+  args.reserve(2 * order.size());
   for (size_t k = 0; k < order.size(); k++) {
-    const LpaLaunch &L = plans[order[k]];
+    const int f = order[k];
+    const LpaLaunch &L = plans[f];
+    int d = -1;
+    if (L.conv && !conv_done && (!ranges || ranges[f].x == 0)) {
+      rows[f] = all_rows(L);
+      args.push_back({&plans[f], &rows[f]});
+      cudaKernelNodeParams c{};
+      c.func = const_cast<void *>(lpa_convert_kernel(L.mode == LPA_LITERAL));
+      c.gridDim = lpa_convert_grid(L, rows[f]);
+      c.blockDim = dim3(256);
+      c.sharedMemBytes = 0;
+      c.kernelParams = args.back().data();
+      key.push_back({-1, L.mode == LPA_LITERAL ? 1 : 0, 0, 0, 0});
+      d = (int)kp.size();
+      kp.push_back(c);
+      dep.push_back(-1);
+    }
     const void *fn = lpa_kernel(L.order, comp, false, L.mode, L.tile_h, L.px, L.stages);
     if (!fn)
       return fail(HDR_E_INTERNAL, "no kernel for order %d, mode %d, tile height %d, %d pixels per thread, %d stages",
                   L.order, L.mode, L.tile_h, L.px, L.stages);
     CUDA_TRY(lpa_opt_in(fn));
     // grid size and shared memory are set on each replay: graphs are kept per sequence of kernels
-    key.push_back({L.order * 8 + L.mode, comp ? 1 : 0, L.tile_h, L.px, L.stages});
-    args[k] = &plans[order[k]];
-    kp[k] = cudaKernelNodeParams{};
-    kp[k].func = const_cast<void *>(fn);
-    kp[k].gridDim = dim3((unsigned)lpa_grid_ctas(grid[order[k]], L.stages));
-    kp[k].blockDim = dim3((unsigned)(LPA_TILE * L.tile_h / L.px));
-    kp[k].sharedMemBytes = L.smem_bytes;
-    kp[k].kernelParams = &args[k];
+    key.push_back({L.order * 8 + L.mode, comp ? 1 : 0, L.tile_h, L.px, L.stages + 4 * (d >= 0 ? 1 : 0)});
+    args.push_back({&plans[f], nullptr});
+    cudaKernelNodeParams r{};
+    r.func = const_cast<void *>(fn);
+    r.gridDim = dim3((unsigned)lpa_grid_ctas(grid[f], L.stages));
+    r.blockDim = dim3((unsigned)(LPA_TILE * L.tile_h / L.px));
+    r.sharedMemBytes = L.smem_bytes;
+    r.kernelParams = args.back().data();
+    kp.push_back(r);
+    dep.push_back(d);
   }
   auto it = B.frame_graphs.find(key);
   if (it != B.frame_graphs.end()) {
     cudaError_t e = cudaSuccess;
-    for (size_t k = 0; k < order.size() && e == cudaSuccess; k++)
+    for (size_t k = 0; k < kp.size() && e == cudaSuccess; k++)
       e = cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.nodes[k], &kp[k]);
     if (e != cudaSuccess) {  // an update the driver refuses: record the graph again
       cudaGetLastError();
@@ -1413,9 +1486,10 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
     }
     BatchState::FrameGraph fg;
     cudaError_t e = cudaGraphCreate(&fg.graph, 0);
-    fg.nodes.resize(order.size());
-    for (size_t k = 0; k < order.size() && e == cudaSuccess; k++)
-      e = cudaGraphAddKernelNode(&fg.nodes[k], fg.graph, nullptr, 0, &kp[k]);
+    fg.nodes.resize(kp.size());
+    for (size_t k = 0; k < kp.size() && e == cudaSuccess; k++)
+      e = cudaGraphAddKernelNode(&fg.nodes[k], fg.graph, dep[k] >= 0 ? &fg.nodes[dep[k]] : nullptr, dep[k] >= 0 ? 1 : 0,
+                                 &kp[k]);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&fg.exec, fg.graph, 0);
     if (e != cudaSuccess) {
       if (fg.graph) cudaGraphDestroy(fg.graph);
@@ -1423,7 +1497,10 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
     }
     it = B.frame_graphs.emplace(key, fg).first;
   }
+  // the context's conversion buffer: after its previous users, and before its next ones
+  if (ctx_conv) CUDA_TRY(cudaStreamWaitEvent(stream, ctx->conv_ev, 0));
   CUDA_TRY(cudaGraphLaunch(it->second.exec, stream));
+  if (ctx_conv) CUDA_TRY(cudaEventRecord(ctx->conv_ev, stream));
   return HDR_OK;
 }
 
@@ -1431,7 +1508,8 @@ hdr_status batch_run_frames(hdr_ctx *ctx, int n, const hdr_frame *frames, const 
 
 // One batched launch over the listed tiles of several frames (see hdr_reconstruct_batch).
 hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, const int2 *ranges,
-                         const hdr_batch_config *cfg_in, cudaStream_t stream, float *const *scratch) {
+                         const hdr_batch_config *cfg_in, cudaStream_t stream, float *const *scratch,
+                         float2 *const *conv, bool conv_done) {
   hdr_status st = check_batch(ctx, n_frames, frames);
   if (st) return st;
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -1453,7 +1531,7 @@ hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames
     return fail(HDR_E_INVALID, "two staging buffers need one pixel per thread and form 0");
   for (int f = 0; f < n_frames; f++)
     if (frames[f].calpa) cfg.form = 0;  // the persistent kernels have no steered window
-  if (cfg.form == 0) return batch_run_frames(ctx, n_frames, frames, ranges, cfg, stream, scratch);
+  if (cfg.form == 0) return batch_run_frames(ctx, n_frames, frames, ranges, cfg, stream, scratch, conv, conv_done);
   uint32_t smem[3];
   int n_tiles[3];
   st = batch_plan(ctx, n_frames, frames, ranges, cfg, smem, n_tiles);
@@ -1555,6 +1633,17 @@ void lpa_ctx_rig_sizes(const hdr_ctx *ctx, int rig_id, int *pitch, int *height) 
   }
 }
 hdr_status lpa_fail(hdr_status st, const char *msg) { return fail(st, "%s", msg); }
+size_t lpa_conv_elems(const hdr_ctx *ctx, int rig_id) { return conv_elems(ctx->rigs[rig_id]); }
+hdr_status lpa_convert_frame(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_dev,
+                             float2 *conv, cudaStream_t st) {
+  LpaLaunch L;
+  hdr_status s = plan_env(PlanEnv{ctx->encode, ctx->status, ctx->device, &ctx->tabs, true}, ctx->rigs[rig_id], params,
+                          raw_dev, L, 16, 1.0, 1, conv);
+  if (s) return s;
+  cudaError_t e = lpa_launch_convert(L, all_rows(L), L.mode == LPA_LITERAL, st);
+  if (e != cudaSuccess) return fail(HDR_E_CUDA, "conversion launch failed: %s", cudaGetErrorString(e));
+  return HDR_OK;
+}
 hdr_status lpa_ctx_calpa_scratch(hdr_ctx *ctx, size_t bytes, void **ptr) {
   if (bytes > ctx->calpa_cap) {
     CUDA_TRY(cudaSetDevice(ctx->device));

@@ -8,9 +8,21 @@
 // is NULL); the implementation behind hdr_reconstruct_batch. Adaptive frames (calpa set) keep
 // their gradients and steering matrices in scratch[f] (5 floats per output pixel), or, when
 // scratch is NULL, in scratch the context owns; their first two passes run in the launch that
-// takes their first tile.
+// takes their first tile. Frames converted ahead of the reconstruction (lpa_conv_eligible) read
+// their converted planes from conv[f] (lpa_conv_elems float2), which lpa_convert_frame has filled
+// when conv_done, else which the launch that takes their first tile fills; with conv NULL, the
+// context's conversion buffer. With two staging buffers, or in form 1, every frame converts its
+// footprints in the kernel.
 hdr_status lpa_batch_run(hdr_ctx *ctx, int32_t n_frames, const hdr_frame *frames, const int2 *ranges,
-                         const hdr_batch_config *cfg, cudaStream_t stream, float *const *scratch = nullptr);
+                         const hdr_batch_config *cfg, cudaStream_t stream, float *const *scratch = nullptr,
+                         float2 *const *conv = nullptr, bool conv_done = false);
+// Convert one frame into conv (lpa_conv_elems float2) on `st`.
+hdr_status lpa_convert_frame(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_dev,
+                             float2 *conv, cudaStream_t st);
+// Whether a frame with these parameters is converted in a pass of its own before its
+// reconstruction, and the float2 elements of its converted planes for a rig.
+bool lpa_conv_eligible(const hdr_params *p, bool adaptive);
+size_t lpa_conv_elems(const hdr_ctx *ctx, int rig_id);
 // Validate adaptive-reconstruction parameters.
 hdr_status lpa_check_calpa(const hdr_calpa_params *c);
 // Passes 1 and 2 of the adaptive reconstruction of one frame into scratch (gradients [2 npx],

@@ -1102,8 +1102,9 @@ __global__ void __launch_bounds__(LPA_TILE *TH, (FrameOccupancy<ORDER, COMP, TH,
 // blockIdx.y into its colour-phase planes (r1 may be the height + 1 of an odd height: that row is
 // outside the frame and writes zeros), with the arithmetic the reconstruction kernels use when
 // they convert staged footprints themselves (convert_sample), so the staged values are the same.
-// Each thread takes the two samples of a row that share a phase column, so that a warp writes
-// contiguous float2 runs in both planes of the row's phase.
+// Each thread takes eight samples of a row per step (one 16-byte load; the rows of the raw frame
+// are 16-byte aligned and padded to a multiple of 8 samples) and writes the four of each phase
+// column as two 16-byte stores, so that a warp's loads and stores are contiguous.
 template <bool LIT>
 __global__ void __launch_bounds__(256) lpa_convert(const __grid_constant__ LpaLaunch L, const LpaRows R) {
   const int s = blockIdx.y;
@@ -1111,20 +1112,46 @@ __global__ void __launch_bounds__(256) lpa_convert(const __grid_constant__ LpaLa
   const int r0 = R.r0[s], r1 = R.r1[s];
   if (r1 <= r0) return;
   const int CP = Sk.conv_pitch, W = Sk.width;
+  const int G = (CP + 3) >> 2;  // groups of four phase columns (eight samples) per row
   const bool scalar = !Sk.bias && !Sk.rvar && !Sk.satf && !Sk.prnu;
-  const long n = (long)(r1 - r0) * CP;
+  const long n = (long)(r1 - r0) * G;
   const size_t plane = (size_t)Sk.conv_h * CP;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const int Y = r0 + (int)(i / CP), c = (int)(i % CP);
-    const int X = 2 * c;
+    const int Y = r0 + (int)(i / G), c0 = 4 * (int)(i % G);
+    const int X0 = 2 * c0;
     const bool in_row = Y < Sk.height;  // the padding row of an odd height converts to zeros
-    const uint16_t *row = Sk.raw + (size_t)(in_row ? Y : 0) * Sk.raw_pitch;
-    const float2 v0 = in_row && X < W ? convert_sample<LIT>(Sk, scalar, X, Y, (float)row[X]) : stage_pair(0.f, 0.f);
-    const float2 v1 =
-        in_row && X + 1 < W ? convert_sample<LIT>(Sk, scalar, X + 1, Y, (float)row[X + 1]) : stage_pair(0.f, 0.f);
-    float2 *dst = Sk.conv + (size_t)(2 * (Y & 1)) * plane + (size_t)(Y >> 1) * CP + c;
-    dst[0] = v0;      // colour phase (0, Y & 1)
-    dst[plane] = v1;  // colour phase (1, Y & 1)
+    uint16_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (in_row && X0 < W) {
+      const uint4 q = *reinterpret_cast<const uint4 *>(Sk.raw + (size_t)Y * Sk.raw_pitch + X0);
+      const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        v[2 * k] = (uint16_t)(w4[k] & 0xffffu);
+        v[2 * k + 1] = (uint16_t)(w4[k] >> 16);
+      }
+    }
+    float2 e[4], o[4];  // columns c0 .. c0 + 3 of the even-x and the odd-x phase
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int X = X0 + 2 * k;
+      e[k] = in_row && X < W ? convert_sample<LIT>(Sk, scalar, X, Y, (float)v[2 * k]) : stage_pair(0.f, 0.f);
+      o[k] = in_row && X + 1 < W ? convert_sample<LIT>(Sk, scalar, X + 1, Y, (float)v[2 * k + 1]) : stage_pair(0.f, 0.f);
+    }
+    float2 *de = Sk.conv + (size_t)(2 * (Y & 1)) * plane + (size_t)(Y >> 1) * CP + c0;  // colour phase (0, Y & 1)
+    float2 *dodd = de + plane;                                                         // colour phase (1, Y & 1)
+    if (c0 + 4 <= CP) {
+      reinterpret_cast<float4 *>(de)[0] = make_float4(e[0].x, e[0].y, e[1].x, e[1].y);
+      reinterpret_cast<float4 *>(de)[1] = make_float4(e[2].x, e[2].y, e[3].x, e[3].y);
+      reinterpret_cast<float4 *>(dodd)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+      reinterpret_cast<float4 *>(dodd)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (c0 + k < CP) {
+          de[k] = e[k];
+          dodd[k] = o[k];
+        }
+    }
   }
 }
 

@@ -89,6 +89,8 @@ struct Job {
   size_t choice_bytes = 0;
   float *scratch_dev = nullptr;     // adaptive requests: gradients and steering matrices
   size_t scratch_bytes = 0;
+  float2 *conv_dev = nullptr;       // the frame converted ahead of its reconstruction (lpa_conv_eligible)
+  size_t conv_bytes = 0;
   int tiles = 0, next_tile = 0, steps = 0;
   int tiles_x = 0, tile_h = 16;     // tile columns and rows per tile row of the frame's output
   int rows_out = 0;                 // output rows whose copy back has been issued
@@ -217,6 +219,8 @@ struct hdr_server {
       j.choice_dev = j.req.choice_host ? reinterpret_cast<uint8_t *>(p + o) : nullptr;
       o += align256(j.choice_bytes);
       j.scratch_dev = j.scratch_bytes ? reinterpret_cast<float *>(p + o) : nullptr;
+      o += align256(j.scratch_bytes);
+      j.conv_dev = j.conv_bytes ? reinterpret_cast<float2 *>(p + o) : nullptr;
       j.t_admit = Clock::now();
       if (!have_first) {
         have_first = true;
@@ -227,9 +231,16 @@ struct hdr_server {
       for (int s = 0; s < j.n_sensors && e == cudaSuccess; s++)
         e = cudaMemcpyAsync(const_cast<uint16_t *>(j.raw_dev[s]), j.req.raw_host[s], j.raw_bytes[s],
                             cudaMemcpyHostToDevice, h2d);
-      if (e == cudaSuccess) e = cudaEventRecord(j.ev_in, h2d);
+      // a frame converted ahead of its reconstruction is converted behind its copy, on the copy
+      // stream: its steps then copy converted footprints and hold only reconstruction launches
+      hdr_status cs = HDR_OK;
+      if (e == cudaSuccess && j.conv_dev) cs = lpa_convert_frame(ctx, j.req.rig_id, &j.req.params, j.raw_dev, j.conv_dev, h2d);
+      if (e == cudaSuccess && cs == HDR_OK) e = cudaEventRecord(j.ev_in, h2d);
       active.push_back(j.ticket);
-      if (e != cudaSuccess) {
+      if (cs != HDR_OK) {  // the copies already queued land before the block returns to the pool
+        cudaStreamSynchronize(h2d);
+        finish(j, cs);
+      } else if (e != cudaSuccess) {
         lpa_fail(HDR_E_CUDA, cudaGetErrorString(e));
         finish(j, HDR_E_CUDA);
       } else {
@@ -270,6 +281,7 @@ struct hdr_server {
     std::vector<hdr_frame> frames;
     std::vector<int2> ranges;
     std::vector<float *> scratch;
+    std::vector<float2 *> conv;
     Step st;
     long budget = cfg.step_tiles > 0 ? cfg.step_tiles : (1L << 40);
     std::vector<uint64_t> order(active.begin(), active.end());
@@ -290,6 +302,7 @@ struct hdr_server {
       f.calpa = j.req.adaptive ? &j.req.calpa : nullptr;
       frames.push_back(f);
       scratch.push_back(j.scratch_dev);
+      conv.push_back(j.conv_dev);
       ranges.push_back(make_int2(j.next_tile, j.next_tile + take));
       budget -= take;
       st.members.push_back(t);
@@ -301,7 +314,7 @@ struct hdr_server {
     lock.unlock();
     if (st.ev_begin) cudaEventRecord(st.ev_begin, compute);
     hdr_status s = lpa_batch_run(ctx, (int)frames.size(), frames.data(), ranges.data(), &cfg.batch, compute,
-                                 scratch.data());
+                                 scratch.data(), conv.data(), true);
     lock.lock();
     if (s == HDR_OK && !st.ev) s = lpa_fail(HDR_E_CUDA, "cudaEventCreate failed");
     if (s == HDR_OK) {
@@ -498,7 +511,11 @@ hdr_status hdr_submit(hdr_server *srv, const hdr_request *req, uint64_t *ticket)
   j.out_bytes = px * (req->params.out_dtype ? 2 : 4);
   j.choice_bytes = req->choice_host ? px : 0;
   j.scratch_bytes = req->adaptive ? px / 3 * 5 * sizeof(float) : 0;  // 5 floats per output pixel
-  bytes += align256(j.out_bytes) + align256(j.choice_bytes) + align256(j.scratch_bytes);
+  // the frame's converted planes, where its steps copy converted footprints
+  const bool conv = lpa_conv_eligible(&req->params, req->adaptive != 0) && srv->cfg.batch.stages != 2 &&
+                    srv->cfg.batch.form == 0;
+  j.conv_bytes = conv ? lpa_conv_elems(srv->ctx, req->rig_id) * sizeof(float2) : 0;
+  bytes += align256(j.out_bytes) + align256(j.choice_bytes) + align256(j.scratch_bytes) + align256(j.conv_bytes);
   j.bytes = std::max<size_t>(bytes, 256);
   if (j.bytes > srv->cfg.pool_bytes) return lpa_fail(HDR_E_UNSUPPORTED, "the frame needs more memory than the pool holds");
   const int th = srv->cfg.batch.tile_h;

@@ -119,6 +119,8 @@ def test_admission_by_memory(ctx, streams):
     for _, fr in items:
         p = fr.params
         need = sum(s.raw.nbytes for s in fr.sensors) + p.out_w * p.out_h * 3 * 5 + 4096
+        if p.out_w * p.out_h >= 152 * 256:     # converted ahead: four colour-phase planes of float2
+            need += sum(4 * ((s.height + 1) // 2) * ((((s.width + 1) // 2) + 1) & ~1) * 8 + 256 for s in fr.sensors)
         biggest = max(biggest, need)
     res, stats = _serve(ctx, items, max_frames=8, pool_bytes=int(biggest * 1.2))
     for (rig, fr), (out, ch, r) in zip(items, res):
