@@ -16,6 +16,12 @@
 #include "hdr_lpa.h"
 #include "lpa_internal.h"
 
+#ifndef LPA_SERVE_CONV_STREAM
+#define LPA_SERVE_CONV_STREAM 1  // conversions on a stream of their own (0: on the copy stream)
+#endif
+#ifndef LPA_SERVE_CONV_PRIORITY
+#define LPA_SERVE_CONV_PRIORITY 1  // conversions at the highest stream priority
+#endif
 #ifndef LPA_SERVE_INFLIGHT
 #define LPA_SERVE_INFLIGHT 3  // batched steps queued on the device at most
 #endif
@@ -117,6 +123,7 @@ struct hdr_server {
   void *pool_mem = nullptr;
   Pool pool;
   cudaStream_t compute = nullptr, h2d = nullptr, d2h = nullptr;
+  cudaStream_t conv_st = nullptr;  // conversions of admitted frames, behind their copies
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   bool stop = false;
@@ -231,14 +238,21 @@ struct hdr_server {
       for (int s = 0; s < j.n_sensors && e == cudaSuccess; s++)
         e = cudaMemcpyAsync(const_cast<uint16_t *>(j.raw_dev[s]), j.req.raw_host[s], j.raw_bytes[s],
                             cudaMemcpyHostToDevice, h2d);
-      // a frame converted ahead of its reconstruction is converted behind its copy, on the copy
-      // stream: its steps then copy converted footprints and hold only reconstruction launches
+      // a frame converted ahead of its reconstruction is converted behind its copy, on a stream of
+      // its own (a conversion waiting for SMs does not hold up the copies queued behind it): its
+      // steps then copy converted footprints and hold only reconstruction launches
       hdr_status cs = HDR_OK;
-      if (e == cudaSuccess && j.conv_dev) cs = lpa_convert_frame(ctx, j.req.rig_id, &j.req.params, j.raw_dev, j.conv_dev, h2d);
-      if (e == cudaSuccess && cs == HDR_OK) e = cudaEventRecord(j.ev_in, h2d);
+      if (e == cudaSuccess) e = cudaEventRecord(j.ev_in, h2d);
+      if (e == cudaSuccess && j.conv_dev) {
+        cudaStream_t cst = LPA_SERVE_CONV_STREAM ? conv_st : h2d;
+        if (cst != h2d) e = cudaStreamWaitEvent(cst, j.ev_in, 0);
+        if (e == cudaSuccess) cs = lpa_convert_frame(ctx, j.req.rig_id, &j.req.params, j.raw_dev, j.conv_dev, cst);
+        if (e == cudaSuccess && cs == HDR_OK) e = cudaEventRecord(j.ev_in, cst);  // ready once converted
+      }
       active.push_back(j.ticket);
       if (cs != HDR_OK) {  // the copies already queued land before the block returns to the pool
         cudaStreamSynchronize(h2d);
+        cudaStreamSynchronize(conv_st);
         finish(j, cs);
       } else if (e != cudaSuccess) {
         lpa_fail(HDR_E_CUDA, cudaGetErrorString(e));
@@ -461,12 +475,21 @@ hdr_status hdr_server_create(hdr_ctx *ctx, const hdr_server_config *cfg, hdr_ser
   cudaError_t e = cudaSetDevice(s->device);
   if (e == cudaSuccess) e = cudaMalloc(&s->pool_mem, cfg->pool_bytes);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    // conversions take the highest stream priority: their blocks go ahead of the queued blocks of
+    // running steps, so that a new frame is ready for the next step without waiting for them
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess)
+      e = cudaStreamCreateWithPriority(&s->conv_st, cudaStreamNonBlocking, LPA_SERVE_CONV_PRIORITY ? greatest : least);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     hdr_status st = e == cudaErrorMemoryAllocation ? HDR_E_NOMEM : HDR_E_CUDA;
     cudaFree(s->pool_mem);
     if (s->compute) cudaStreamDestroy(s->compute);
+    if (s->conv_st) cudaStreamDestroy(s->conv_st);
     if (s->h2d) cudaStreamDestroy(s->h2d);
     if (s->d2h) cudaStreamDestroy(s->d2h);
     delete s;
@@ -598,6 +621,7 @@ void hdr_server_destroy(hdr_server *srv) {
   if (srv->worker.joinable()) srv->worker.join();
   cudaSetDevice(srv->device);
   cudaStreamSynchronize(srv->compute);
+  cudaStreamSynchronize(srv->conv_st);
   cudaStreamSynchronize(srv->h2d);
   cudaStreamSynchronize(srv->d2h);
   for (auto &kv : srv->jobs) {
@@ -612,6 +636,7 @@ void hdr_server_destroy(hdr_server *srv) {
     if (st.ev_begin) cudaEventDestroy(st.ev_begin);
   }
   cudaStreamDestroy(srv->compute);
+  cudaStreamDestroy(srv->conv_st);
   cudaStreamDestroy(srv->h2d);
   cudaStreamDestroy(srv->d2h);
   cudaFree(srv->pool_mem);
