@@ -125,12 +125,29 @@ hdr_status lpa_check_calpa(const hdr_calpa_params *c) { return check_calpa(c); }
 
 double lpa_calpa_reach(const hdr_calpa_params *calpa) { return 1.0 / std::sqrt(calpa->min_eig); }
 
+namespace {
+// Pass 1: one isotropic order-1 fit at grad_sigma (ahead: see lpa_launch_mode).
+hdr_status gradients(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const hdr_calpa_params *calpa,
+                     const uint16_t *const *raw_dev, float *grad_dev, cudaStream_t st, bool ahead) {
+  hdr_status s = check_calpa(calpa);
+  if (s) return s;
+  if (!params) return lpa_fail(HDR_E_INVALID, "params is NULL");
+  hdr_params p = *params;
+  p.order = 1;
+  p.n_scales = 1;
+  p.sigma[0] = calpa->grad_sigma;
+  return lpa_launch_mode(ctx, rig_id, &p, raw_dev, LPA_GRADIENTS, grad_dev, 1.0, nullptr, nullptr, st, ahead);
+}
+}  // namespace
+
 hdr_status lpa_calpa_prepare(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const hdr_calpa_params *calpa,
                              const uint16_t *const *raw_dev, float *scratch, cudaStream_t st) {
   const size_t npx = (size_t)params->out_w * params->out_h;
   if (npx == 0) return HDR_OK;
   float *grad = scratch, *metric = scratch + npx * 2;
-  hdr_status s = hdr_calpa_gradients(ctx, rig_id, params, calpa, raw_dev, grad, st);
+  // inside a batch, whose plans may point into the context's conversion buffer: the pass converts
+  // its footprints itself
+  hdr_status s = gradients(ctx, rig_id, params, calpa, raw_dev, grad, st, false);
   if (s) return s;
   return hdr_calpa_metric(ctx, params->out_w, params->out_h, calpa, grad, metric, st);
 }
@@ -151,15 +168,7 @@ void hdr_calpa_params_default(hdr_calpa_params *c) {
 
 hdr_status hdr_calpa_gradients(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const hdr_calpa_params *calpa,
                                const uint16_t *const *raw_dev, float *grad_dev, void *cuda_stream) {
-  hdr_status st = check_calpa(calpa);
-  if (st) return st;
-  if (!params) return lpa_fail(HDR_E_INVALID, "params is NULL");
-  hdr_params p = *params;  // one isotropic order-1 fit at grad_sigma
-  p.order = 1;
-  p.n_scales = 1;
-  p.sigma[0] = calpa->grad_sigma;
-  return lpa_launch_mode(ctx, rig_id, &p, raw_dev, LPA_GRADIENTS, grad_dev, 1.0, nullptr, nullptr,
-                         (cudaStream_t)cuda_stream);
+  return gradients(ctx, rig_id, params, calpa, raw_dev, grad_dev, (cudaStream_t)cuda_stream, true);
 }
 
 hdr_status hdr_calpa_metric(hdr_ctx *ctx, int32_t out_w, int32_t out_h, const hdr_calpa_params *calpa,
@@ -208,7 +217,7 @@ hdr_status hdr_reconstruct_steered(hdr_ctx *ctx, int32_t rig_id, const hdr_param
   if (!params) return lpa_fail(HDR_E_INVALID, "params is NULL");
   if (!metric_dev && (long long)params->out_w * params->out_h > 0) return lpa_fail(HDR_E_INVALID, "metric_dev is NULL");
   return lpa_launch_mode(ctx, rig_id, params, raw_dev, LPA_STEERED, const_cast<float *>(metric_dev),
-                         lpa_calpa_reach(calpa), out_dev, choice_dev, (cudaStream_t)cuda_stream);
+                         lpa_calpa_reach(calpa), out_dev, choice_dev, (cudaStream_t)cuda_stream, true);
 }
 
 hdr_status hdr_reconstruct_adaptive(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params,

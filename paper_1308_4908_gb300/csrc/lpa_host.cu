@@ -1658,22 +1658,34 @@ hdr_status lpa_ctx_calpa_scratch(hdr_ctx *ctx, size_t bytes, void **ptr) {
   return HDR_OK;
 }
 hdr_status lpa_launch_mode(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_dev,
-                           int mode, float *aux, double reach, void *out_dev, uint8_t *choice_dev, cudaStream_t st) {
+                           int mode, float *aux, double reach, void *out_dev, uint8_t *choice_dev, cudaStream_t st,
+                           bool ahead) {
   hdr_status s = common_checks(ctx, rig_id, params, raw_dev, mode == LPA_GRADIENTS ? aux : out_dev);
   if (s) return s;
   if (params->weight_mode != 0)
     return fail(HDR_E_UNSUPPORTED, "the adaptive passes use the inverse-variance weight (weight_mode 0)");
   hdr_params p = *params;
   p.tab_weights = 0;  // the window is searched: offsets or weights differ per pixel
+  float2 *conv = nullptr;
+  if (ahead) {
+    s = conv_buffer(ctx, ctx->rigs[rig_id], &p, &conv);
+    if (s) return s;
+  }
   LpaLaunch L;
-  s = plan(ctx, ctx->rigs[rig_id], &p, raw_dev, L, reach);
+  s = plan(ctx, ctx->rigs[rig_id], &p, raw_dev, L, reach, true, 1, conv);
   if (s) return s;
+  if (L.conv) {  // the frame converted once, then the pass
+    s = convert_rows(ctx, L, all_rows(L), true, st);
+    if (s) return s;
+  }
   // the plan picked the FP32-only variant when these parameters cannot trigger the FP64 re-solve
   L.mode = lpa_mode_f32(L.mode) ? lpa_mode_to_f32(mode) : mode;
   L.aux = aux;
   L.out = out_dev;
   L.choice = choice_dev;
-  return launch(L, p.accum, false, st);
+  s = launch(L, p.accum, false, st);
+  if (s == HDR_OK && L.conv) CUDA_TRY(cudaEventRecord(ctx->conv_ev, st));
+  return s;
 }
 hdr_status lpa_check_params(const hdr_params *p) { return check_params(p); }
 hdr_status lpa_take_status(hdr_ctx *ctx) {

@@ -41,9 +41,11 @@ hdr_status lpa_check_params(const hdr_params *p);
 hdr_status lpa_take_status(hdr_ctx *ctx);
 // Plan and launch one frame with the kernel of `mode` (LPA_STEERED: aux = the steering matrices,
 // the window's reach grown by `reach`; LPA_GRADIENTS: aux receives the gradients and no output
-// is written). The window is always searched.
+// is written). The window is always searched. ahead: the frame is converted into the context's
+// conversion buffer first where lpa_conv_eligible (not while a batch holds plans into it).
 hdr_status lpa_launch_mode(hdr_ctx *ctx, int32_t rig_id, const hdr_params *params, const uint16_t *const *raw_dev,
-                           int mode, float *aux, double reach, void *out_dev, uint8_t *choice_dev, cudaStream_t st);
+                           int mode, float *aux, double reach, void *out_dev, uint8_t *choice_dev, cudaStream_t st,
+                           bool ahead);
 // Staging reach of the steered window for these adaptive parameters (1 / sqrt(min_eig)).
 double lpa_calpa_reach(const hdr_calpa_params *calpa);
 // Device scratch of at least `bytes` owned by the context for the adaptive reconstruction
