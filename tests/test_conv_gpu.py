@@ -31,18 +31,18 @@ def ctx():
     c.close()
 
 
-def _odd_frame(seed=1201, order=2):
-    """3 sensors of 225 x 209 (odd sizes), small rotations, 224 x 208 output (46592 pixels: more
-    than one wave of 16 x 16 tiles), 4 scales; sensor 1 with per-pixel calibration frames whose
-    saturation level is low in a band of rows."""
-    p = synth.Params(order=order, sigmas=synth.PAPER_SCALES, out_w=224, out_h=208)
-    fr = synth._build_frame(seed, 3, 225, 209, (1.0, 1 / 8, 1 / 64), 1.0, 0.3, 0.0, p, "odd-3x225x209")
+def _odd_frame(seed=1201, order=2, w=225, h=209):
+    """3 sensors of w x h (odd sizes), small rotations, (w - 1) x (h - 1) output (224 x 208 =
+    46592 pixels by default: more than one wave of 16 x 16 tiles), 4 scales; sensor 1 with per-pixel
+    calibration frames whose saturation level is low in a band of rows."""
+    p = synth.Params(order=order, sigmas=synth.PAPER_SCALES, out_w=w - 1, out_h=h - 1)
+    fr = synth._build_frame(seed, 3, w, h, (1.0, 1 / 8, 1 / 64), 1.0, 0.3, 0.0, p, f"odd-3x{w}x{h}")
     r = np.random.default_rng(seed)
     s = fr.sensors[1]
-    s.bias_frame = (s.black + r.uniform(-2, 2, (209, 225))).astype(np.float32)
-    s.prnu_frame = r.uniform(0.95, 1.05, (209, 225)).astype(np.float32)
-    s.read_var_frame = r.uniform(6, 12, (209, 225)).astype(np.float32)
-    sat = np.full((209, 225), 4095, np.uint16)
+    s.bias_frame = (s.black + r.uniform(-2, 2, (h, w))).astype(np.float32)
+    s.prnu_frame = r.uniform(0.95, 1.05, (h, w)).astype(np.float32)
+    s.read_var_frame = r.uniform(6, 12, (h, w)).astype(np.float32)
+    sat = np.full((h, w), 4095, np.uint16)
     sat[60:90] = 300
     s.sat_frame = sat
     return fr
@@ -111,6 +111,22 @@ def test_host_buffers_convert_band_by_band(ctx):
     out = np.full((3, p.out_h, p.out_w), -7.0, np.float32)
     ch = np.zeros((3, p.out_h, p.out_w), np.uint8)
     ctx.reconstruct_host(2, p, raws, out, ch)
+    np.testing.assert_array_equal(ch, ref[1])
+    np.testing.assert_array_equal(out, ref[0])
+
+
+def test_host_buffers_odd_sizes_and_calibration_frames(ctx):
+    """The host-buffer path on 3 sensors of 513 x 387 (odd sizes; 25 tile rows: three bands, whose
+    row ranges end inside the frame and, for the last, at the padding row of the odd height) with
+    per-pixel calibration frames: identical to the device-buffer call."""
+    fr = _odd_frame(seed=1206, order=1, w=513, h=387)
+    ctx.set_rig(5, fr.sensors)
+    p = fr.params
+    ref = _single(ctx, 5, fr)
+    raws = [np.ascontiguousarray(s.raw) for s in fr.sensors]
+    out = np.full((3, p.out_h, p.out_w), -7.0, np.float32)
+    ch = np.zeros((3, p.out_h, p.out_w), np.uint8)
+    ctx.reconstruct_host(5, p, raws, out, ch)
     np.testing.assert_array_equal(ch, ref[1])
     np.testing.assert_array_equal(out, ref[0])
 
